@@ -1,0 +1,180 @@
+/*
+ * modal.h -- C ABI of the GB300 (sm_103a) modal bispectrum library.
+ *
+ * The library computes the data-parallel hot path of the optimal modal
+ * bispectrum estimator of Fergusson & Shellard, "Optimal Polyspectra
+ * Estimation" (arXiv:1105.2791):
+ *
+ *   filtered maps   M_p(x) = sum_lm q_p(l) a_lm / sqrt(C_l) Y_lm(x)
+ *                   (whitening of Eq. legoestimator, separable isotropic basis
+ *                   of Eq. isobasisbi with v_l = 1, Sec. III.A);
+ *   modal coeffs    beta_prs = sum_x W_x [M_p M_r M_s - (<M_p M_r>_x M_s
+ *                   + <M_p M_s>_x M_r + <M_r M_s>_x M_p)],  p <= r <= s
+ *                   (Eq. bbispect with the linear term of Eq. bispectrumest);
+ *   covariance      zeta = <beta beta^T> / 6          (Eq. linearterm, Sec. II);
+ *   estimator       fNL = alpha^T zeta^-1 beta / alpha^T zeta^-1 alpha,
+ *                   sigma^2 = 6 / alpha^T zeta^-1 alpha
+ *                   (Eq. modalest, Eq. modalvariance, via Eq. Cholrot).
+ *
+ * Conventions
+ *  - Sums over the sphere are quadratures on a Gauss-Legendre grid of
+ *    `nrings` rings (north first) x `nphi` equally spaced longitudes;
+ *    W_x = w_j (2 pi / nphi) mask_x.
+ *  - a_lm: complex64 (interleaved float re, im), m >= 0 only, m-major:
+ *    idx(l, m) = m (2 lmax + 3 - m) / 2 + (l - m); n_alm = (lmax+1)(lmax+2)/2.
+ *    Real field: a_{l,-m} = (-1)^m conj(a_lm); Im a_l0 is ignored.
+ *  - Maps: float32 [B][P][nrings][nphi].
+ *  - Modes n <-> (p, r, s), p <= r <= s, lexicographic; n_max = C(P+2, 3).
+ *    Pairs (p, r), p <= r, lexicographic; n_pair = P (P + 1) / 2.
+ *  - beta and the covariance sums are float64.
+ *  - Every data pointer is caller-owned.  "dev" pointers are device memory of
+ *    the current device, "host" pointers are host memory.  The plan owns its
+ *    tables, workspace and Monte Carlo accumulators.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream except modal_init, modal_solve, modal_sync,
+ *    the getters and state I/O, which synchronise.
+ *  - A plan is not thread-safe; concurrent calls on one plan race.
+ *  - Errors are returned as status codes and never abort; modal_last_error()
+ *    gives a message for the calling thread's last failure.  Kernel faults
+ *    surface as MODAL_ECUDA at the next synchronising call; a bounded device
+ *    wait that gave up surfaces as MODAL_ETIMEOUT at modal_sync.
+ */
+#ifndef MODAL_H
+#define MODAL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct modal_plan* modal_h;
+
+typedef enum {
+    MODAL_OK = 0,
+    MODAL_EINVAL = 1,    /* bad argument (size, pointer, unsupported option) */
+    MODAL_ENOMEM = 2,    /* device or host allocation failed */
+    MODAL_ECUDA = 3,     /* CUDA runtime error (launch or asynchronous fault) */
+    MODAL_ENOTPD = 4,    /* zeta is not positive definite (Cholesky pivot <= 0) */
+    MODAL_ETIMEOUT = 5,  /* a bounded device-side wait hit its limit */
+    MODAL_ESTATE = 6     /* call out of order (e.g. solve before 2 covariance sims) */
+} modal_status;
+
+/* Arithmetic of the Legendre contraction (the dominant step).  FP32 is the plain
+ * SIMT path; the others run on tcgen05 tensor cores with FP32 accumulation:
+ * 3XTF32 and FP16X3 split each operand into two parts and sum three products,
+ * BF16X3 does the same with bf16 parts, BF16 uses one bf16 product. */
+typedef enum {
+    MODAL_FP32 = 0,
+    MODAL_3XTF32 = 1,
+    MODAL_BF16X3 = 2,
+    MODAL_BF16 = 3,
+    MODAL_FP16X3 = 4
+} modal_prec;
+
+typedef struct {
+    int nrings;              /* Gauss-Legendre rings, >= lmax + 1                          */
+    int nphi;                /* longitudes: a power of two, >= 2 lmax + 2, <= 8192          */
+    const float* ring_mask;  /* host [nrings] multiplying W_x, or NULL (all ones)           */
+    const float* pix_mask;   /* host [nrings*nphi] multiplying W_x, or NULL (all ones)      */
+} modal_grid;
+
+typedef struct {
+    int lmax, P, nrings, nphi, prec;
+    int n_alm, n_max, n_pair;
+    long long npix;
+    long long n_lin;         /* simulations accumulated into <M_p M_r>_x      */
+    long long n_cov;         /* beta vectors accumulated into the covariance  */
+    int lin_final;           /* 1 once the linear-term mean has been formed   */
+    int chunk;               /* maps per internal pass                        */
+    size_t device_bytes;     /* device memory held by the plan                */
+} modal_info;
+
+/* Build a plan: Gauss-Legendre nodes and weights (FP64 Newton on the host), the
+ * normalised associated Legendre table lambda_lm(theta_j) (FP64 recurrence with
+ * exponent rescaling on the GPU, stored FP32; plus the pre-split tensor-core
+ * tables for the tensor-core precisions), the filter q_p(l)/sqrt(C_l) (zero where
+ * C_l <= 0) and the pixel weights.  Sec. III.A (basis), Eq. legoestimator (filter).
+ *   basis: host [P][lmax+1];  C_l: host [lmax+1];  1 <= P <= 16;  2 <= lmax <= 4000.
+ * Synchronises.  On failure *out is NULL. */
+modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
+                        const modal_grid* grid, int prec, modal_h* out);
+
+/* Filtered maps M_p for B maps: dev alm [B][n_alm] -> dev maps [B][P][nrings][nphi]. */
+modal_status modal_synthesize(modal_h h, const void* alm, int B, float* maps, void* stream);
+
+/* Quadrature analysis a_lm = sum_x w_j (2 pi / nphi) T(x) conj(Y_lm(x)) of B maps
+ * (no mask, no filter): dev maps [B][nrings][nphi] -> dev alm [B][n_alm] (complex64).
+ * The inverse of synthesis with a unit filter for band-limited maps. */
+modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void* stream);
+
+/* Linear-term simulations (Sec. II: the mean <M_p M_r>_x "calculated from Monte Carlo
+ * simulations of Gaussian maps"): synthesise B sims, add M_p M_r of each to the FP64
+ * pair sums.  finalize != 0 then forms <M_p M_r>_x = sums / n_lin (used by modal_cubic
+ * and modal_backward with use_linear != 0).  B may be 0 with finalize set. */
+modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int finalize, void* stream);
+
+/* Modal coefficients (Eq. bbispect): dev alm [B][n_alm] -> dev beta [B][n_max] (float64).
+ * use_linear != 0 subtracts the linear term (needs a finalised mean, else MODAL_ESTATE). */
+modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, double* beta,
+                         void* stream);
+
+/* Covariance sums over simulations (Eq. linearterm): S1 += sum_b beta_b,
+ * S2 += sum_b beta_b beta_b^T (FP64).  dev beta [B][n_max]. */
+modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* stream);
+
+/* Estimator (Eq. modalest, Eq. modalvariance, Eq. Cholrot): zeta = sample covariance
+ * of the accumulated beta / 6; FP64 Cholesky zeta = L L^T on the GPU;
+ * alpha' = L^-1 alpha, beta'_b = L^-1 beta_b; fnl[b] = alpha'.beta'_b / |alpha'|^2,
+ * sigma = sqrt(6 / |alpha'|^2).  alpha: host [n_max]; beta: dev [B][n_max] (B >= 0);
+ * fnl: host [B] (may be NULL when B == 0); sigma: host [1] or NULL.
+ * MODAL_ESTATE if fewer than 2 covariance sims; MODAL_ENOTPD if a pivot is <= 0.
+ * Synchronises. */
+modal_status modal_solve(modal_h h, const double* alpha, const double* beta, int B,
+                         double* fnl, double* sigma, void* stream);
+
+/* Adjoint (not in the paper): for L = sum_n g_n beta_n, grad_lm = dL/dRe a_lm
+ * + i dL/dIm a_lm for the stored m >= 0 entries (Im part of m = 0 is zero).
+ * Maps are recomputed, not stored.  dev alm [B][n_alm]; dev g [B][n_max] (float64);
+ * dev grad_alm [B][n_alm] complex64. */
+modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, int use_linear,
+                            void* grad_alm, void* stream);
+
+/* alpha_prs per unit fNL for the local shape b = 2 (C1 C2 + C2 C3 + C3 C1) (Eq. abispect
+ * with the first-order bispectrum of T = G + f (G^2 - <G^2>)), by exact Gauss-Legendre
+ * integration of Legendre series (FP64, host).  C_signal: host [lmax+1] (the signal
+ * part of C_l; NULL = the C_l given to modal_init); alpha: host [n_max]. */
+modal_status modal_alpha_local(modal_h h, const double* C_signal, double* alpha);
+
+modal_status modal_get_info(modal_h h, modal_info* info);
+/* Ring nodes mu_j = cos(theta_j) and weights w_j: host [nrings] each (either may be NULL). */
+modal_status modal_get_rings(modal_h h, double* mu, double* w);
+/* Copy <M_p M_r>_x (after finalize) to dev out [n_pair][nrings*nphi] float32. */
+modal_status modal_get_pair_mean(modal_h h, float* out, void* stream);
+/* zeta = covariance / 6 of the accumulated beta: host [n_max][n_max]. Synchronises. */
+modal_status modal_get_zeta(modal_h h, double* zeta);
+/* Clear accumulators: what & 1 -> linear-term sums, what & 2 -> covariance sums. */
+modal_status modal_reset(modal_h h, int what);
+/* Maps per internal pass (workspace is sized by it); reallocates.  Synchronises. */
+modal_status modal_set_chunk(modal_h h, int chunk);
+/* Synchronise `stream`, then report asynchronous faults (MODAL_ECUDA) or a device
+ * wait that gave up (MODAL_ETIMEOUT, with the flag cleared). */
+modal_status modal_sync(modal_h h, void* stream);
+
+/* Checkpoint / resume of the Monte Carlo accumulators (pair sums, n_lin, S1, S2,
+ * n_cov) in a binary file tagged with the plan's sizes.  Synchronise. */
+modal_status modal_save_state(modal_h h, const char* path);
+modal_status modal_load_state(modal_h h, const char* path);
+
+/* Device wait self-test: one thread waits on a device flag that nothing sets, giving
+ * up after `spin_limit` polls; the next modal_sync returns MODAL_ETIMEOUT.  Exercises
+ * the bounded-wait error path without faulting the GPU. */
+modal_status modal_selftest_wait(modal_h h, int spin_limit, void* stream);
+
+void modal_destroy(modal_h h);
+const char* modal_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MODAL_H */

@@ -1,0 +1,249 @@
+"""Thin ctypes binding of the modal C ABI (include/modal.h).
+
+Each function has the name of the C entry point and only marshals arguments:
+host arrays are numpy float64/float32 arrays, device buffers are CUDA torch
+tensors (or raw integer device addresses), `stream` defaults to torch's
+current stream.  Every computation runs in the CUDA library; there is no CPU
+fallback, and importing this module raises if the library is not built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_float, c_int, c_longlong, c_size_t, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+MODAL_OK, MODAL_EINVAL, MODAL_ENOMEM, MODAL_ECUDA, MODAL_ENOTPD, MODAL_ETIMEOUT, MODAL_ESTATE = range(7)
+MODAL_FP32, MODAL_3XTF32, MODAL_BF16X3, MODAL_BF16, MODAL_FP16X3 = range(5)
+PREC = {"fp32": MODAL_FP32, "3xtf32": MODAL_3XTF32, "bf16x3": MODAL_BF16X3, "bf16": MODAL_BF16,
+        "fp16x3": MODAL_FP16X3}
+STATUS_NAMES = ["MODAL_OK", "MODAL_EINVAL", "MODAL_ENOMEM", "MODAL_ECUDA", "MODAL_ENOTPD",
+                "MODAL_ETIMEOUT", "MODAL_ESTATE"]
+
+# Every symbol include/modal.h declares.
+EXPORTS = [
+    "modal_init", "modal_synthesize", "modal_analyze", "modal_linear_term", "modal_cubic",
+    "modal_cov_accumulate", "modal_solve", "modal_backward", "modal_alpha_local", "modal_get_info",
+    "modal_get_rings", "modal_get_pair_mean", "modal_get_zeta", "modal_reset", "modal_set_chunk",
+    "modal_sync", "modal_save_state", "modal_load_state", "modal_selftest_wait", "modal_destroy",
+    "modal_last_error",
+]
+
+
+class ModalError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s: %s" % (name, message))
+
+
+class modal_grid(ctypes.Structure):
+    _fields_ = [("nrings", c_int), ("nphi", c_int), ("ring_mask", c_void_p), ("pix_mask", c_void_p)]
+
+
+class modal_info(ctypes.Structure):
+    _fields_ = [("lmax", c_int), ("P", c_int), ("nrings", c_int), ("nphi", c_int), ("prec", c_int),
+                ("n_alm", c_int), ("n_max", c_int), ("n_pair", c_int), ("npix", c_longlong),
+                ("n_lin", c_longlong), ("n_cov", c_longlong), ("lin_final", c_int), ("chunk", c_int),
+                ("device_bytes", c_size_t)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Load the in-tree libmodal.so (raises ImportError if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError("modal CUDA library not built (%s); run paper_1105_2791_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    H = c_void_p
+    sig = {
+        "modal_init": [c_int, c_int, c_void_p, c_void_p, POINTER(modal_grid), c_int, POINTER(H)],
+        "modal_synthesize": [H, c_void_p, c_int, c_void_p, c_void_p],
+        "modal_analyze": [H, c_void_p, c_int, c_void_p, c_void_p],
+        "modal_linear_term": [H, c_void_p, c_int, c_int, c_void_p],
+        "modal_cubic": [H, c_void_p, c_int, c_int, c_void_p, c_void_p],
+        "modal_cov_accumulate": [H, c_void_p, c_int, c_void_p],
+        "modal_solve": [H, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
+        "modal_backward": [H, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p],
+        "modal_alpha_local": [H, c_void_p, c_void_p],
+        "modal_get_info": [H, POINTER(modal_info)],
+        "modal_get_rings": [H, c_void_p, c_void_p],
+        "modal_get_pair_mean": [H, c_void_p, c_void_p],
+        "modal_get_zeta": [H, c_void_p],
+        "modal_reset": [H, c_int],
+        "modal_set_chunk": [H, c_int],
+        "modal_sync": [H, c_void_p],
+        "modal_save_state": [H, c_char_p],
+        "modal_load_state": [H, c_char_p],
+        "modal_selftest_wait": [H, c_int, c_void_p],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = c_int
+    lib.modal_destroy.argtypes = [H]
+    lib.modal_destroy.restype = None
+    lib.modal_last_error.argtypes = []
+    lib.modal_last_error.restype = c_char_p
+    _LIB = lib
+    return lib
+
+
+def _check(status: int):
+    if status != MODAL_OK:
+        msg = load_library().modal_last_error()
+        raise ModalError(status, msg.decode() if msg else "")
+
+
+def _dev(t):
+    """Device address of a CUDA tensor (must be contiguous) or a raw integer address."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _host(a, dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(c_void_p)
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ------------------------------------------------------------------ entry points
+
+def modal_init(lmax, P, basis, C_l, nrings, nphi, prec=MODAL_FP32, ring_mask=None, pix_mask=None):
+    lib = load_library()
+    b_arr, b_ptr = _host(basis, np.float64)
+    c_arr, c_ptr = _host(C_l, np.float64)
+    rm_arr, rm_ptr = _host(ring_mask, np.float32)
+    pm_arr, pm_ptr = _host(pix_mask, np.float32)
+    grid = modal_grid(int(nrings), int(nphi), rm_ptr, pm_ptr)
+    h = c_void_p()
+    _check(lib.modal_init(int(lmax), int(P), b_ptr, c_ptr, byref(grid), int(PREC.get(prec, prec)), byref(h)))
+    return h
+
+
+def modal_synthesize(h, alm, B, maps, stream=None):
+    _check(load_library().modal_synthesize(h, _dev(alm), int(B), _dev(maps), _stream(stream)))
+
+
+def modal_analyze(h, maps, B, alm, stream=None):
+    _check(load_library().modal_analyze(h, _dev(maps), int(B), _dev(alm), _stream(stream)))
+
+
+def modal_linear_term(h, alm_sims, B, finalize, stream=None):
+    _check(load_library().modal_linear_term(h, _dev(alm_sims), int(B), int(bool(finalize)), _stream(stream)))
+
+
+def modal_cubic(h, alm, B, use_linear, beta, stream=None):
+    _check(load_library().modal_cubic(h, _dev(alm), int(B), int(bool(use_linear)), _dev(beta), _stream(stream)))
+
+
+def modal_cov_accumulate(h, beta, B, stream=None):
+    _check(load_library().modal_cov_accumulate(h, _dev(beta), int(B), _stream(stream)))
+
+
+def modal_solve(h, alpha, beta, B, stream=None):
+    """Returns (fnl [B] numpy, sigma)."""
+    a_arr, a_ptr = _host(alpha, np.float64)
+    fnl = np.zeros(max(int(B), 1))
+    sigma = c_double(0.0)
+    _check(load_library().modal_solve(h, a_ptr, _dev(beta), int(B), fnl.ctypes.data_as(c_void_p), byref(sigma),
+                                      _stream(stream)))
+    return fnl[: int(B)], sigma.value
+
+
+def modal_backward(h, alm, B, g, use_linear, grad_alm, stream=None):
+    _check(load_library().modal_backward(h, _dev(alm), int(B), _dev(g), int(bool(use_linear)), _dev(grad_alm),
+                                         _stream(stream)))
+
+
+def modal_alpha_local(h, C_signal=None):
+    info = modal_get_info(h)
+    out = np.zeros(info.n_max)
+    c_arr, c_ptr = _host(C_signal, np.float64)
+    _check(load_library().modal_alpha_local(h, c_ptr, out.ctypes.data_as(c_void_p)))
+    return out
+
+
+def modal_get_info(h) -> modal_info:
+    info = modal_info()
+    _check(load_library().modal_get_info(h, byref(info)))
+    return info
+
+
+def modal_get_rings(h):
+    n = modal_get_info(h).nrings
+    mu, w = np.zeros(n), np.zeros(n)
+    _check(load_library().modal_get_rings(h, mu.ctypes.data_as(c_void_p), w.ctypes.data_as(c_void_p)))
+    return mu, w
+
+
+def modal_get_pair_mean(h, out, stream=None):
+    _check(load_library().modal_get_pair_mean(h, _dev(out), _stream(stream)))
+
+
+def modal_get_zeta(h):
+    n = modal_get_info(h).n_max
+    z = np.zeros((n, n))
+    _check(load_library().modal_get_zeta(h, z.ctypes.data_as(c_void_p)))
+    return z
+
+
+def modal_reset(h, what):
+    _check(load_library().modal_reset(h, int(what)))
+
+
+def modal_set_chunk(h, chunk):
+    _check(load_library().modal_set_chunk(h, int(chunk)))
+
+
+def modal_sync(h, stream=None):
+    _check(load_library().modal_sync(h, _stream(stream)))
+
+
+def modal_save_state(h, path):
+    _check(load_library().modal_save_state(h, str(path).encode()))
+
+
+def modal_load_state(h, path):
+    _check(load_library().modal_load_state(h, str(path).encode()))
+
+
+def modal_selftest_wait(h, spin_limit, stream=None):
+    _check(load_library().modal_selftest_wait(h, int(spin_limit), _stream(stream)))
+
+
+def modal_destroy(h):
+    if h is not None and h.value:
+        load_library().modal_destroy(h)
+
+
+def modal_last_error() -> str:
+    msg = load_library().modal_last_error()
+    return msg.decode() if msg else ""

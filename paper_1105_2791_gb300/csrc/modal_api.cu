@@ -1,0 +1,728 @@
+// C ABI of the modal bispectrum library: plan construction, dispatch of the
+// per-map stages in chunks of maps, Monte Carlo accumulators, estimator solve,
+// checkpointing.  Argument meaning and error behaviour are documented in modal.h.
+#include "modal_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+using namespace modal;
+
+struct modal_plan : public Plan {};
+
+// Offsets inside the small integer table `modeidx` (one allocation).
+static constexpr int MI_MODEIDX = 0;      // [256][16]  colex pair c, s -> mode or -1
+static constexpr int MI_MP = 4096;        // [1024] mode -> p
+static constexpr int MI_MR = 5120;        // [1024] mode -> r
+static constexpr int MI_MS = 6144;        // [1024] mode -> s
+static constexpr int MI_MODEOF = 7168;    // [P][P][P] sorted triple -> mode
+static constexpr int MI_TOTAL = 11264;
+
+namespace modal {
+
+static thread_local std::string g_last_error;
+
+modal_status set_error(modal_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+modal_status cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return MODAL_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_error(MODAL_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    return set_error(MODAL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace modal
+
+#define CK(expr, what)                                        \
+    do {                                                      \
+        modal_status _s = cuda_check((expr), (what));         \
+        if (_s != MODAL_OK) return _s;                        \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(modal_plan* pl, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e == cudaSuccess) pl->device_bytes += count * sizeof(T);
+    return e;
+}
+
+static void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+// ------------------------------------------------------------------ host math
+// Gauss-Legendre nodes (north first) and weights by Newton's method on P_n.
+static void gauss_legendre(int n, std::vector<double>& mu, std::vector<double>& w) {
+    mu.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const int half = (n + 1) / 2;
+    for (int j = 0; j < half; ++j) {
+        double x = std::cos(M_PI * (j + 0.75) / (n + 0.5));
+        double p = 0, pm1 = 0, dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            p = (n == 0) ? 1.0 : p1;
+            pm1 = (n == 1) ? 1.0 : p0;
+            if (n == 1) { p = x; pm1 = 1.0; }
+            dp = n * (x * p - pm1) / (x * x - 1.0);
+            const double dx = p / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            p = p1;
+            pm1 = (n == 1) ? 1.0 : p0;
+            dp = n * (x * p - pm1) / (x * x - 1.0);
+        }
+        if ((n & 1) && j == half - 1) x = 0.0;
+        mu[j] = x;
+        w[j] = 2.0 / ((1.0 - x * x) * dp * dp);
+        mu[n - 1 - j] = -x;
+        w[n - 1 - j] = w[j];
+    }
+}
+
+static int n_modes_of(int P) { return P * (P + 1) * (P + 2) / 6; }
+
+static void build_mode_tables(modal_plan* pl, std::vector<int>& mi) {
+    const int P = pl->P;
+    mi.assign(MI_TOTAL, -1);
+    pl->mode_p.clear(); pl->mode_r.clear(); pl->mode_s.clear();
+    std::vector<int> mode_of(P * P * P, -1);
+    int n = 0;
+    for (int p = 0; p < P; ++p)
+        for (int r = p; r < P; ++r)
+            for (int s = r; s < P; ++s) {
+                pl->mode_p.push_back(p); pl->mode_r.push_back(r); pl->mode_s.push_back(s);
+                mi[MI_MP + n] = p; mi[MI_MR + n] = r; mi[MI_MS + n] = s;
+                mode_of[(p * P + r) * P + s] = n;
+                mi[MI_MODEOF + (p * P + r) * P + s] = n;
+                ++n;
+            }
+    // colex pairs (sorted by r then p), padded to a multiple of 8
+    std::vector<std::pair<int, int>> colex;
+    for (int r = 0; r < P; ++r)
+        for (int p = 0; p <= r; ++p) colex.push_back({p, r});
+    pl->n_pg = ((int)colex.size() + 7) / 8;
+    pl->n_sq = (P + 3) / 4;
+    std::vector<int> pair_ab(pl->n_pg * 8, -1);
+    for (size_t c = 0; c < colex.size(); ++c) pair_ab[c] = colex[c].first | (colex[c].second << 8);
+    for (size_t c = 0; c < colex.size(); ++c)
+        for (int s = 0; s < P; ++s)
+            if (s >= colex[c].second)
+                mi[MI_MODEIDX + c * 16 + s] = mode_of[(colex[c].first * P + colex[c].second) * P + s];
+    std::vector<int> tiles;
+    for (int pg = 0; pg < pl->n_pg; ++pg)
+        for (int sq = 0; sq < pl->n_sq; ++sq) {
+            bool any = false;
+            for (int c = pg * 8; c < pg * 8 + 8 && c < (int)colex.size(); ++c)
+                for (int s = sq * 4; s < sq * 4 + 4 && s < P; ++s)
+                    if (s >= colex[c].second) any = true;
+            if (any) tiles.push_back(pg | (sq << 8));
+        }
+    pl->n_tiles = (int)tiles.size();
+    pl->cubic_pair_ab_host = pair_ab;
+    pl->cubic_tiles_host = tiles;
+}
+
+// ------------------------------------------------------------------ workspace
+static size_t per_map_workspace(const modal_plan* pl) {
+    const size_t L1 = pl->lmax + 1;
+    const size_t delta = (size_t)pl->P * L1 * pl->nrings * sizeof(float2);
+    const size_t maps = (size_t)pl->P * pl->npix * sizeof(float);
+    const size_t ut = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
+    return delta + maps + ut;
+}
+
+static void free_workspace(modal_plan* pl) {
+    size_t freed = 0;
+    (void)freed;
+    dfree(pl->delta); pl->delta = nullptr;
+    dfree(pl->maps); pl->maps = nullptr;
+    dfree(pl->ut); pl->ut = nullptr;
+    dfree(pl->partial); pl->partial = nullptr;
+    dfree(pl->hk); pl->hk = nullptr;
+    pl->device_bytes -= pl->workspace_bytes;
+    pl->workspace_bytes = 0;
+}
+
+static modal_status alloc_workspace(modal_plan* pl, int chunk) {
+    free_workspace(pl);
+    pl->chunk = chunk;
+    const size_t before = pl->device_bytes;
+    const size_t L1 = pl->lmax + 1;
+    CK(dalloc(pl, &pl->delta, (size_t)chunk * pl->P * L1 * pl->nrings), "workspace delta");
+    CK(dalloc(pl, &pl->maps, (size_t)chunk * pl->P * pl->npix), "workspace maps");
+    CK(dalloc(pl, &pl->ut, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace ut");
+    CK(dalloc(pl, &pl->hk, (size_t)chunk * pl->P * pl->n_pair), "workspace hk");
+    // cubic partials: [chunk][cubic_ctas][n_max]; linear partials: [ksplit][n_pair][chunk*P]
+    const size_t cub = (size_t)chunk * pl->cubic_ctas * pl->n_max;
+    const size_t lin = (size_t)pl->lin_ksplit * pl->n_pair * chunk * pl->P;
+    pl->partial_elems = cub + lin;
+    CK(dalloc(pl, &pl->partial, pl->partial_elems), "workspace partial");
+    pl->workspace_bytes = pl->device_bytes - before;
+    return MODAL_OK;
+}
+
+static modal_status ensure_pair_buffers(modal_plan* pl) {
+    if (pl->pair_sum) return MODAL_OK;
+    const size_t n = (size_t)pl->n_pair * pl->npix;
+    CK(dalloc(pl, &pl->pair_sum, n), "pair sums");
+    CK(dalloc(pl, &pl->pair_mean, n), "pair mean");
+    CK(cudaMemset(pl->pair_sum, 0, n * sizeof(double)), "pair sums clear");
+    CK(cudaMemset(pl->pair_mean, 0, n * sizeof(float)), "pair mean clear");
+    return MODAL_OK;
+}
+
+static void destroy_plan(modal_plan* pl) {
+    if (!pl) return;
+    cudaDeviceSynchronize();
+    free_workspace(pl);
+    dfree(pl->lam); dfree(pl->filt); dfree(pl->W); dfree(pl->wring); dfree(pl->twiddle);
+    dfree(pl->modeidx); dfree(pl->tiles); dfree(pl->pair_ab);
+    dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->S1); dfree(pl->S2);
+    dfree(pl->solve_ws); dfree(pl->d_err);
+    free_tc_tables(*pl);
+    delete pl;
+}
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+static modal_status check_plan(modal_h h) {
+    if (!h) return set_error(MODAL_EINVAL, "null plan");
+    return MODAL_OK;
+}
+
+static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Legendre stage for one chunk: alm -> delta.
+static cudaError_t legendre_forward(modal_plan* pl, const float2* alm, int B, cudaStream_t st) {
+    if (pl->prec == MODAL_FP32) return launch_legendre_simt(*pl, alm, B, pl->delta, st);
+    return launch_legendre_tc(*pl, alm, B, pl->delta, st);
+}
+
+static cudaError_t synth_chunk(modal_plan* pl, const float2* alm, int B, float* maps_out, cudaStream_t st) {
+    cudaError_t e = legendre_forward(pl, alm, B, st);
+    if (e != cudaSuccess) return e;
+    return launch_ring_c2r(*pl, pl->delta, B * pl->P, maps_out, st);
+}
+
+extern "C" {
+
+const char* modal_last_error(void) { return g_last_error.c_str(); }
+
+modal_status modal_init(int lmax, int P, const double* basis, const double* C_l, const modal_grid* grid, int prec,
+                        modal_h* out) {
+    if (!out) return set_error(MODAL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (lmax < 2 || lmax > 4000) return set_error(MODAL_EINVAL, "lmax must be in [2, 4000]");
+    if (P < 1 || P > MODAL_MAXP) return set_error(MODAL_EINVAL, "P must be in [1, 16]");
+    if (!basis || !C_l || !grid) return set_error(MODAL_EINVAL, "basis, C_l and grid are required");
+    if (grid->nrings < lmax + 1) return set_error(MODAL_EINVAL, "nrings must be >= lmax + 1");
+    if (!is_pow2(grid->nphi) || grid->nphi < 2 * lmax + 2 || grid->nphi > 8192)
+        return set_error(MODAL_EINVAL, "nphi must be a power of two in [2 lmax + 2, 8192]");
+    if (prec < MODAL_FP32 || prec > MODAL_FP16X3) return set_error(MODAL_EINVAL, "unknown precision");
+    for (int l = 0; l <= lmax; ++l)
+        if (!std::isfinite(C_l[l])) return set_error(MODAL_EINVAL, "C_l must be finite");
+    for (int i = 0; i < P * (lmax + 1); ++i)
+        if (!std::isfinite(basis[i])) return set_error(MODAL_EINVAL, "basis must be finite");
+
+    modal_plan* pl = new modal_plan();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    pl->dev = dev;
+    pl->lmax = lmax; pl->P = P; pl->nrings = grid->nrings; pl->nphi = grid->nphi; pl->prec = prec;
+    pl->R_half = (grid->nrings + 1) / 2;
+    pl->RH = (pl->R_half + 31) / 32 * 32;
+    pl->n_alm = (lmax + 1) * (lmax + 2) / 2;
+    pl->n_max = n_modes_of(P);
+    pl->n_pair = P * (P + 1) / 2;
+    pl->npix = (int64_t)grid->nrings * grid->nphi;
+    pl->basis.assign(basis, basis + (size_t)P * (lmax + 1));
+    pl->cl.assign(C_l, C_l + lmax + 1);
+    gauss_legendre(grid->nrings, pl->mu, pl->w);
+
+    auto fail = [&](modal_status s) { destroy_plan(pl); return s; };
+#define CKI(expr, what)                                        \
+    do {                                                       \
+        modal_status _s = cuda_check((expr), (what));          \
+        if (_s != MODAL_OK) return fail(_s);                   \
+    } while (0)
+
+    // Legendre table (FP64 recurrence on the GPU)
+    {
+        std::vector<double> log2c(lmax + 1), ca(pl->n_alm, 0.0), cb(pl->n_alm, 0.0);
+        double lp = 0.0;
+        for (int m = 0; m <= lmax; ++m) {
+            if (m > 0) lp += std::log2((2.0 * m - 1.0) / (2.0 * m));
+            log2c[m] = 0.5 * (std::log2((2.0 * m + 1.0) / (4.0 * M_PI)) + lp);
+            for (int l = m + 1; l <= lmax; ++l) {
+                const int64_t i = alm_index(l, m, lmax);
+                const double L = l, M = m;
+                ca[i] = std::sqrt((4.0 * L * L - 1.0) / (L * L - M * M));
+                cb[i] = std::sqrt(((L - 1.0) * (L - 1.0) - M * M) / (4.0 * (L - 1.0) * (L - 1.0) - 1.0));
+            }
+        }
+        double *d_mu = nullptr, *d_log2c = nullptr, *d_a = nullptr, *d_b = nullptr;
+        CKI(cudaMalloc(&d_mu, pl->R_half * sizeof(double)), "table mu");
+        cudaMalloc(&d_log2c, (lmax + 1) * sizeof(double));
+        cudaMalloc(&d_a, pl->n_alm * sizeof(double));
+        cudaMalloc(&d_b, pl->n_alm * sizeof(double));
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(d_mu, pl->mu.data(), pl->R_half * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_log2c, log2c.data(), (lmax + 1) * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_a, ca.data(), pl->n_alm * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_b, cb.data(), pl->n_alm * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = dalloc(pl, &pl->lam, (size_t)pl->n_alm * pl->RH);
+        if (e == cudaSuccess) e = launch_lambda_table(*pl, d_mu, d_log2c, d_a, d_b, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(d_mu); cudaFree(d_log2c); cudaFree(d_a); cudaFree(d_b);
+        CKI(e, "legendre table");
+    }
+    // filter f_p(l) = q_p(l)/sqrt(C_l), zero where C_l <= 0
+    {
+        std::vector<float> f((size_t)P * (lmax + 1));
+        for (int p = 0; p < P; ++p)
+            for (int l = 0; l <= lmax; ++l)
+                f[(size_t)p * (lmax + 1) + l] =
+                    C_l[l] > 0 ? (float)(basis[(size_t)p * (lmax + 1) + l] / std::sqrt(C_l[l])) : 0.f;
+        CKI(dalloc(pl, &pl->filt, f.size()), "filter");
+        CKI(cudaMemcpy(pl->filt, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice), "filter copy");
+    }
+    // pixel weights W_x = w_j (2 pi / nphi) mask_x, ring weights, twiddles
+    {
+        std::vector<float> W((size_t)pl->npix), wr(pl->nrings);
+        for (int j = 0; j < pl->nrings; ++j) {
+            const double base = pl->w[j] * 2.0 * M_PI / pl->nphi;
+            wr[j] = (float)base;
+            const double rm = grid->ring_mask ? grid->ring_mask[j] : 1.0;
+            for (int k = 0; k < pl->nphi; ++k) {
+                const double pm = grid->pix_mask ? grid->pix_mask[(size_t)j * pl->nphi + k] : 1.0;
+                W[(size_t)j * pl->nphi + k] = (float)(base * rm * pm);
+            }
+        }
+        CKI(dalloc(pl, &pl->W, W.size()), "weights");
+        CKI(cudaMemcpy(pl->W, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice), "weights copy");
+        CKI(dalloc(pl, &pl->wring, wr.size()), "ring weights");
+        CKI(cudaMemcpy(pl->wring, wr.data(), wr.size() * sizeof(float), cudaMemcpyHostToDevice), "ring weights copy");
+        std::vector<float2> tw(pl->nphi);
+        for (int k = 0; k < pl->nphi; ++k) {
+            const double a = 2.0 * M_PI * k / pl->nphi;
+            tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        CKI(dalloc(pl, &pl->twiddle, tw.size()), "twiddles");
+        CKI(cudaMemcpy(pl->twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice), "twiddles copy");
+    }
+    // mode / pair / tile tables
+    {
+        std::vector<int> mi;
+        build_mode_tables(pl, mi);
+        CKI(dalloc(pl, &pl->modeidx, mi.size()), "mode tables");
+        CKI(cudaMemcpy(pl->modeidx, mi.data(), mi.size() * sizeof(int), cudaMemcpyHostToDevice), "mode tables copy");
+        CKI(dalloc(pl, &pl->tiles, pl->cubic_tiles_host.size()), "tiles");
+        CKI(cudaMemcpy(pl->tiles, pl->cubic_tiles_host.data(), pl->cubic_tiles_host.size() * sizeof(int),
+                       cudaMemcpyHostToDevice), "tiles copy");
+        CKI(dalloc(pl, &pl->pair_ab, pl->cubic_pair_ab_host.size()), "pairs");
+        CKI(cudaMemcpy(pl->pair_ab, pl->cubic_pair_ab_host.data(), pl->cubic_pair_ab_host.size() * sizeof(int),
+                       cudaMemcpyHostToDevice), "pairs copy");
+    }
+    // accumulators and solve workspace
+    CKI(dalloc(pl, &pl->S1, (size_t)pl->n_max), "S1");
+    CKI(dalloc(pl, &pl->S2, (size_t)pl->n_max * pl->n_max), "S2");
+    CKI(cudaMemset(pl->S1, 0, pl->n_max * sizeof(double)), "S1 clear");
+    CKI(cudaMemset(pl->S2, 0, (size_t)pl->n_max * pl->n_max * sizeof(double)), "S2 clear");
+    CKI(dalloc(pl, &pl->d_err, 1), "error word");
+    CKI(cudaMemset(pl->d_err, 0, sizeof(int)), "error word clear");
+    // kernel geometry
+    {
+        int64_t ctas = pl->npix / 8192;
+        pl->cubic_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, 512));
+        int64_t ks = pl->npix / 16384;
+        pl->lin_ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(ks, 128));
+    }
+    // tensor-core tables
+    if (prec != MODAL_FP32) CKI(build_tc_tables(*pl, 0), "tensor-core tables");
+    // workspace: as many maps per pass as fit a 24 GB budget (at least 1, at most 64)
+    {
+        const size_t per = per_map_workspace(pl);
+        int chunk = (int)std::max<size_t>(1, std::min<size_t>(64, (size_t)24e9 / std::max<size_t>(per, 1)));
+        modal_status s = alloc_workspace(pl, chunk);
+        if (s != MODAL_OK) return fail(s);
+    }
+    CKI(cudaDeviceSynchronize(), "init");
+#undef CKI
+    *out = pl;
+    return MODAL_OK;
+}
+
+void modal_destroy(modal_h h) { destroy_plan(h); }
+
+modal_status modal_set_chunk(modal_h h, int chunk) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (chunk < 1 || chunk > 4096) return set_error(MODAL_EINVAL, "chunk must be in [1, 4096]");
+    CK(cudaDeviceSynchronize(), "set_chunk sync");
+    return alloc_workspace(h, chunk);
+}
+
+modal_status modal_synthesize(modal_h h, const void* alm, int B, float* maps, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && (!alm || !maps)) return set_error(MODAL_EINVAL, "null pointer");
+    cudaStream_t st = as_stream(stream);
+    const float2* a = static_cast<const float2*>(alm);
+    for (int b0 = 0; b0 < B; b0 += h->chunk) {
+        const int nb = std::min(h->chunk, B - b0);
+        CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, maps + (size_t)b0 * h->P * h->npix, st), "synthesize");
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && (!alm || !maps)) return set_error(MODAL_EINVAL, "null pointer");
+    cudaStream_t st = as_stream(stream);
+    float2* out = static_cast<float2*>(alm);
+    const int step = h->chunk * h->P;   // ut holds chunk*P channels
+    for (int b0 = 0; b0 < B; b0 += step) {
+        const int nb = std::min(step, B - b0);
+        CK(launch_ring_r2c(*h, maps + (size_t)b0 * h->npix, nb, h->wring, h->ut, st), "analyze r2c");
+        CK(launch_legendre_adjoint_simt(*h, h->ut, nb, nullptr, 1, out + (size_t)b0 * h->n_alm, st), "analyze legendre");
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int finalize, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && !alm_sims) return set_error(MODAL_EINVAL, "null pointer");
+    modal_status s = ensure_pair_buffers(h);
+    if (s != MODAL_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    const float2* a = static_cast<const float2*>(alm_sims);
+    for (int b0 = 0; b0 < B; b0 += h->chunk) {
+        const int nb = std::min(h->chunk, B - b0);
+        CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "linear-term synthesis");
+        CK(launch_pair_accumulate(*h, h->maps, nb, st), "pair accumulate");
+    }
+    h->n_lin += B;
+    if (B > 0) h->lin_final = 0;
+    if (finalize) {
+        if (h->n_lin < 1) return set_error(MODAL_ESTATE, "finalize with no linear-term simulations");
+        CK(launch_pair_finalize(*h, st), "pair finalize");
+        h->lin_final = 1;
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, double* beta, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && (!alm || !beta)) return set_error(MODAL_EINVAL, "null pointer");
+    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+    cudaStream_t st = as_stream(stream);
+    const float2* a = static_cast<const float2*>(alm);
+    double* cub = h->partial;
+    double* lin = h->partial + (size_t)h->chunk * h->cubic_ctas * h->n_max;
+    for (int b0 = 0; b0 < B; b0 += h->chunk) {
+        const int nb = std::min(h->chunk, B - b0);
+        CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "cubic synthesis");
+        CK(launch_cubic(*h, h->maps, nb, cub, st), "cubic");
+        if (use_linear) CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm");
+        CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, beta + (size_t)b0 * h->n_max, st), "beta finalize");
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && !beta) return set_error(MODAL_EINVAL, "null pointer");
+    CK(launch_cov_accumulate(*h, beta, B, as_stream(stream)), "cov accumulate");
+    h->n_cov += B;
+    return MODAL_OK;
+}
+
+static modal_status read_device_error(modal_h h, cudaStream_t st) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word read");
+    CK(cudaStreamSynchronize(st), "sync");
+    if (e) {
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st), "error word clear");
+        CK(cudaStreamSynchronize(st), "sync");
+        if (e & MODAL_DEVERR_NOTPD) return set_error(MODAL_ENOTPD, "zeta is not positive definite");
+        if (e & MODAL_DEVERR_TIMEOUT) return set_error(MODAL_ETIMEOUT, "a device-side wait hit its spin limit");
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_solve(modal_h h, const double* alpha, const double* beta, int B, double* fnl, double* sigma,
+                         void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!alpha || B < 0 || (B > 0 && (!beta || !fnl))) return set_error(MODAL_EINVAL, "bad arguments");
+    if (h->n_cov < 2) return set_error(MODAL_ESTATE, "need at least 2 covariance simulations");
+    cudaStream_t st = as_stream(stream);
+    const int n = h->n_max;
+    double* ws = nullptr;
+    CK(cudaMallocAsync(&ws, ((size_t)n * n + (size_t)(B + 1) * n + (B + 1)) * sizeof(double), st), "solve workspace");
+    double* A = ws;
+    double* rhs = ws + (size_t)n * n;
+    double* est = rhs + (size_t)(B + 1) * n;
+    modal_status s = MODAL_OK;
+    auto run = [&]() -> modal_status {
+        CK(launch_zeta(*h, A, st), "zeta");
+        CK(launch_cholesky(*h, A, n, st), "cholesky");
+        CK(cudaMemcpyAsync(rhs, alpha, n * sizeof(double), cudaMemcpyHostToDevice, st), "alpha copy");
+        if (B > 0) CK(cudaMemcpyAsync(rhs + n, beta, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice, st), "beta copy");
+        modal_status es = read_device_error(h, st);
+        if (es != MODAL_OK) return es;
+        CK(launch_solve_rhs(*h, A, n, rhs, B + 1, st), "triangular solve");
+        CK(launch_estimates(*h, rhs, n, B, est, st), "estimates");
+        std::vector<double> out(B + 1);
+        CK(cudaMemcpyAsync(out.data(), est, (B + 1) * sizeof(double), cudaMemcpyDeviceToHost, st), "estimates copy");
+        CK(cudaStreamSynchronize(st), "solve sync");
+        if (!(out[0] > 0.0)) return set_error(MODAL_ENOTPD, "alpha^T zeta^-1 alpha is not positive");
+        if (sigma) *sigma = std::sqrt(6.0 / out[0]);
+        for (int b = 0; b < B; ++b) fnl[b] = out[1 + b];
+        return MODAL_OK;
+    };
+    s = run();
+    cudaFreeAsync(ws, st);
+    cudaStreamSynchronize(st);
+    return s;
+}
+
+modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, int use_linear, void* grad_alm,
+                            void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && (!alm || !g || !grad_alm)) return set_error(MODAL_EINVAL, "null pointer");
+    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+    cudaStream_t st = as_stream(stream);
+    const float2* a = static_cast<const float2*>(alm);
+    float2* out = static_cast<float2*>(grad_alm);
+    for (int b0 = 0; b0 < B; b0 += h->chunk) {
+        const int nb = std::min(h->chunk, B - b0);
+        CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "backward synthesis");
+        CK(launch_adjoint_weights(*h, g + (size_t)b0 * h->n_max, nb, h->hk, st), "adjoint weights");
+        CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear, h->maps, st), "adjoint pixel");
+        CK(launch_ring_r2c(*h, h->maps, nb * h->P, nullptr, h->ut, st), "adjoint r2c");
+        CK(launch_legendre_adjoint_simt(*h, h->ut, nb, h->filt, h->P, out + (size_t)b0 * h->n_alm, st), "adjoint legendre");
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_alpha_local(modal_h h, const double* C_signal, double* alpha) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!alpha) return set_error(MODAL_EINVAL, "alpha is NULL");
+    const int L = h->lmax, P = h->P;
+    const double* cs = C_signal ? C_signal : h->cl.data();
+    std::vector<double> x, wx;
+    gauss_legendre(3 * L / 2 + 2, x, wx);
+    const int nx = (int)x.size();
+    // A_p(x) = sum_l (2l+1)/4pi C_l f_p(l) P_l(x), D_p(x) = sum_l (2l+1)/4pi f_p(l) P_l(x)
+    std::vector<double> A((size_t)P * nx, 0.0), D((size_t)P * nx, 0.0);
+    for (int i = 0; i < nx; ++i) {
+        double p0 = 1.0, p1 = x[i];
+        for (int l = 0; l <= L; ++l) {
+            double pl;
+            if (l == 0) pl = 1.0;
+            else if (l == 1) pl = x[i];
+            else {
+                pl = ((2.0 * l - 1.0) * x[i] * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = pl;
+            }
+            if (h->cl[l] <= 0) continue;
+            const double c = (2.0 * l + 1.0) / (4.0 * M_PI) * pl / std::sqrt(h->cl[l]);
+            for (int p = 0; p < P; ++p) {
+                const double f = h->basis[(size_t)p * (L + 1) + l] * c;
+                D[(size_t)p * nx + i] += f;
+                A[(size_t)p * nx + i] += f * cs[l];
+            }
+        }
+    }
+    for (int n = 0; n < h->n_max; ++n) {
+        const int p = h->mode_p[n], r = h->mode_r[n], s = h->mode_s[n];
+        double acc = 0.0;
+        for (int i = 0; i < nx; ++i) {
+            const double* a = A.data();
+            const double* d = D.data();
+            acc += wx[i] * (a[p * nx + i] * a[r * nx + i] * d[s * nx + i] + a[p * nx + i] * d[r * nx + i] * a[s * nx + i]
+                            + d[p * nx + i] * a[r * nx + i] * a[s * nx + i]);
+        }
+        alpha[n] = 16.0 * M_PI * M_PI * acc;
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_get_info(modal_h h, modal_info* info) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!info) return set_error(MODAL_EINVAL, "info is NULL");
+    info->lmax = h->lmax; info->P = h->P; info->nrings = h->nrings; info->nphi = h->nphi; info->prec = h->prec;
+    info->n_alm = h->n_alm; info->n_max = h->n_max; info->n_pair = h->n_pair; info->npix = h->npix;
+    info->n_lin = h->n_lin; info->n_cov = h->n_cov; info->lin_final = h->lin_final; info->chunk = h->chunk;
+    info->device_bytes = h->device_bytes;
+    return MODAL_OK;
+}
+
+modal_status modal_get_rings(modal_h h, double* mu, double* w) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (mu) std::memcpy(mu, h->mu.data(), h->nrings * sizeof(double));
+    if (w) std::memcpy(w, h->w.data(), h->nrings * sizeof(double));
+    return MODAL_OK;
+}
+
+modal_status modal_get_pair_mean(modal_h h, float* out, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!out) return set_error(MODAL_EINVAL, "out is NULL");
+    if (!h->lin_final) return set_error(MODAL_ESTATE, "pair mean not finalised");
+    CK(cudaMemcpyAsync(out, h->pair_mean, (size_t)h->n_pair * h->npix * sizeof(float), cudaMemcpyDeviceToDevice,
+                       as_stream(stream)), "pair mean copy");
+    return MODAL_OK;
+}
+
+modal_status modal_get_zeta(modal_h h, double* zeta) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!zeta) return set_error(MODAL_EINVAL, "zeta is NULL");
+    if (h->n_cov < 2) return set_error(MODAL_ESTATE, "need at least 2 covariance simulations");
+    double* d = nullptr;
+    const size_t nn = (size_t)h->n_max * h->n_max;
+    CK(cudaMalloc(&d, nn * sizeof(double)), "zeta workspace");
+    cudaError_t e = launch_zeta(*h, d, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(zeta, d, nn * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    CK(e, "zeta");
+    return MODAL_OK;
+}
+
+modal_status modal_reset(modal_h h, int what) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    CK(cudaDeviceSynchronize(), "reset sync");
+    if ((what & 1) && h->pair_sum) {
+        CK(cudaMemset(h->pair_sum, 0, (size_t)h->n_pair * h->npix * sizeof(double)), "reset pair sums");
+        h->n_lin = 0;
+        h->lin_final = 0;
+    }
+    if (what & 2) {
+        CK(cudaMemset(h->S1, 0, h->n_max * sizeof(double)), "reset S1");
+        CK(cudaMemset(h->S2, 0, (size_t)h->n_max * h->n_max * sizeof(double)), "reset S2");
+        h->n_cov = 0;
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_sync(modal_h h, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    CK(cudaStreamSynchronize(st), "sync");
+    CK(cudaGetLastError(), "sync");
+    return read_device_error(h, st);
+}
+
+modal_status modal_selftest_wait(modal_h h, int spin_limit, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (spin_limit < 1) return set_error(MODAL_EINVAL, "spin_limit must be >= 1");
+    CK(launch_wait_selftest(h->d_err, spin_limit, as_stream(stream)), "wait selftest");
+    return MODAL_OK;
+}
+
+// State file: magic, sizes, n_lin, lin_final, n_cov, then pair sums (if present), S1, S2.
+struct StateHeader {
+    char magic[8];
+    int32_t lmax, P, nrings, nphi;
+    int64_t n_lin, n_cov;
+    int32_t lin_final, has_pairs;
+};
+
+modal_status modal_save_state(modal_h h, const char* path) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!path) return set_error(MODAL_EINVAL, "path is NULL");
+    CK(cudaDeviceSynchronize(), "save sync");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return set_error(MODAL_EINVAL, std::string("cannot open ") + path);
+    StateHeader hd{};
+    std::memcpy(hd.magic, "MODALST1", 8);
+    hd.lmax = h->lmax; hd.P = h->P; hd.nrings = h->nrings; hd.nphi = h->nphi;
+    hd.n_lin = h->n_lin; hd.n_cov = h->n_cov; hd.lin_final = h->lin_final; hd.has_pairs = h->pair_sum ? 1 : 0;
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+    auto dump = [&](const double* d, size_t n) {
+        std::vector<double> buf(std::min<size_t>(n, (size_t)1 << 24));
+        for (size_t off = 0; ok && off < n; off += buf.size()) {
+            const size_t m = std::min(buf.size(), n - off);
+            if (cudaMemcpy(buf.data(), d + off, m * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) ok = false;
+            else ok = std::fwrite(buf.data(), sizeof(double), m, f) == m;
+        }
+    };
+    if (hd.has_pairs) dump(h->pair_sum, (size_t)h->n_pair * h->npix);
+    dump(h->S1, h->n_max);
+    dump(h->S2, (size_t)h->n_max * h->n_max);
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return set_error(MODAL_ECUDA, "state write failed");
+    return MODAL_OK;
+}
+
+modal_status modal_load_state(modal_h h, const char* path) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!path) return set_error(MODAL_EINVAL, "path is NULL");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return set_error(MODAL_EINVAL, std::string("cannot open ") + path);
+    StateHeader hd{};
+    bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, "MODALST1", 8) == 0 &&
+              hd.lmax == h->lmax && hd.P == h->P && hd.nrings == h->nrings && hd.nphi == h->nphi;
+    if (!ok) {
+        std::fclose(f);
+        return set_error(MODAL_EINVAL, "state file does not match this plan");
+    }
+    CK(cudaDeviceSynchronize(), "load sync");
+    if (hd.has_pairs) {
+        modal_status s = ensure_pair_buffers(h);
+        if (s != MODAL_OK) { std::fclose(f); return s; }
+    }
+    auto load = [&](double* d, size_t n) {
+        std::vector<double> buf(std::min<size_t>(n, (size_t)1 << 24));
+        for (size_t off = 0; ok && off < n; off += buf.size()) {
+            const size_t m = std::min(buf.size(), n - off);
+            ok = std::fread(buf.data(), sizeof(double), m, f) == m &&
+                 cudaMemcpy(d + off, buf.data(), m * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+    };
+    if (hd.has_pairs) load(h->pair_sum, (size_t)h->n_pair * h->npix);
+    load(h->S1, h->n_max);
+    load(h->S2, (size_t)h->n_max * h->n_max);
+    std::fclose(f);
+    if (!ok) return set_error(MODAL_EINVAL, "state file truncated");
+    h->n_lin = hd.n_lin;
+    h->n_cov = hd.n_cov;
+    h->lin_final = 0;
+    if (hd.has_pairs && hd.lin_final && h->n_lin > 0) {
+        CK(launch_pair_finalize(*h, 0), "pair finalize");
+        CK(cudaDeviceSynchronize(), "load sync");
+        h->lin_final = 1;
+    }
+    return MODAL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Internal declarations shared by the translation units of the modal library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/modal.h"
+
+#define MODAL_MAXP 16
+#define MODAL_MAX_TILES 40
+
+// Device-side error word bits (set by kernels, read by modal_sync).
+#define MODAL_DEVERR_TIMEOUT 1
+#define MODAL_DEVERR_NOTPD 2
+
+namespace modal {
+
+inline int64_t alm_index(int64_t l, int64_t m, int64_t lmax) { return m * (2 * lmax + 3 - m) / 2 + (l - m); }
+__host__ __device__ inline int64_t d_alm_index(int64_t l, int64_t m, int64_t lmax) {
+    return m * (2 * lmax + 3 - m) / 2 + (l - m);
+}
+
+// Tensor-core operand tiles: 128 ring pairs x 32 l values of one parity per tile.
+constexpr int TC_BM = 128;
+
+// Layout of the pre-split tensor-core Legendre tables (hi and lo parts).
+struct TcTable {
+    void* hi = nullptr;                 // element type per precision (fp32 for tf32, 16-bit otherwise)
+    void* lo = nullptr;
+    int elem_bytes = 4;
+    int bk = 32;                        // l values per K block (one 128-byte swizzle row)
+    int n_rt = 0;                       // ring tiles of TC_BM ring pairs
+    std::vector<int64_t> kb_off;        // per (m, parity): first K block index (prefix sums)
+    int64_t n_kb = 0;                   // total K blocks over all (m, parity)
+    int64_t* d_kb_off = nullptr;        // device copy of kb_off ([2*(lmax+1)+1])
+    size_t bytes = 0;
+};
+
+struct Plan {
+    int lmax = 0, P = 0, nrings = 0, nphi = 0, prec = 0, dev = 0;
+    int R_half = 0;          // ring pairs (north rings incl. the equator)
+    int RH = 0;              // R_half padded to a multiple of 32 (SIMT table stride)
+    int n_alm = 0, n_max = 0, n_pair = 0;
+    int64_t npix = 0;
+    int chunk = 0;           // maps per internal pass
+    std::vector<double> mu, w;            // host ring nodes/weights (north first, all rings)
+    std::vector<double> basis, cl;        // host copies of the inputs
+    std::vector<int> mode_p, mode_r, mode_s;
+
+    // device tables
+    float* lam = nullptr;        // [n_alm][RH] lambda_lm(theta_j), j < R_half
+    float* filt = nullptr;       // [P][lmax+1]
+    float* W = nullptr;          // [nrings*nphi] pixel weights with mask
+    float* wring = nullptr;      // [nrings] w_j 2 pi / nphi (no mask)
+    float2* twiddle = nullptr;   // [nphi] exp(+2 pi i k / nphi)
+    int* modeidx = nullptr;      // [n_pair_colex_pad][16] -> mode index or -1 (cubic tiles)
+    int* tiles = nullptr;        // [n_tiles] packed (pair group, s quad)
+    int n_tiles = 0, n_pg = 0, n_sq = 0;
+    int* pair_ab = nullptr;      // colex pair c -> (p | r << 8), padded entries = -1
+    TcTable tc;
+
+    // Monte Carlo accumulators
+    double* pair_sum = nullptr;  // [n_pair][npix]
+    float* pair_mean = nullptr;  // [n_pair][npix]
+    long long n_lin = 0;
+    int lin_final = 0;
+    double* S1 = nullptr;        // [n_max]
+    double* S2 = nullptr;        // [n_max][n_max]
+    long long n_cov = 0;
+
+    // workspace (sized by chunk)
+    float2* delta = nullptr;     // [chunk][P][lmax+1][nrings]
+    float* maps = nullptr;       // [chunk][P][npix]
+    float2* ut = nullptr;        // [chunk][P][lmax+1][2][RH] (adjoint)
+    double* partial = nullptr;   // cubic / linear partial sums
+    size_t partial_elems = 0;
+    int cubic_ctas = 0;          // CTAs per map in the cubic kernel
+    int lin_ksplit = 0;          // K splits in the linear-term GEMM
+    float* hk = nullptr;         // [chunk][P][n_pair] adjoint weights
+    double* solve_ws = nullptr;  // [n_max][n_max] + vectors
+    int* d_err = nullptr;        // device error word
+    size_t device_bytes = 0;
+    size_t workspace_bytes = 0;
+    std::vector<int> cubic_pair_ab_host, cubic_tiles_host;
+};
+
+// ---- error reporting (modal_api.cu) ----
+modal_status set_error(modal_status s, const std::string& msg);
+modal_status cuda_check(cudaError_t e, const char* what);
+
+// ---- kernels launchers ----
+// k_tables.cu
+cudaError_t launch_lambda_table(const Plan& pl, const double* d_mu_north, const double* d_log2c,
+                                const double* d_a, const double* d_b, cudaStream_t st);
+cudaError_t build_tc_tables(Plan& pl, cudaStream_t st);      // allocates pl.tc
+void free_tc_tables(Plan& pl);
+// k_legendre_simt.cu
+cudaError_t launch_legendre_simt(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st);
+cudaError_t launch_legendre_adjoint_simt(const Plan& pl, const float2* ut, int B, const float* rowfilt,
+                                         int nfilt, float2* out, cudaStream_t st);
+// k_legendre_tc.cu
+cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st);
+// k_fft.cu
+cudaError_t launch_ring_c2r(const Plan& pl, const float2* delta, int nmaps_p, float* maps, cudaStream_t st);
+cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmaps_p, const float* ring_weight,
+                            float2* ut, cudaStream_t st);
+// k_cubic.cu
+cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
+cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
+cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* cub_partial,
+                                 const double* lin_partial, double* beta, cudaStream_t st);
+cudaError_t launch_pair_accumulate(Plan& pl, const float* maps, int B, cudaStream_t st);
+cudaError_t launch_pair_finalize(Plan& pl, cudaStream_t st);
+cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, cudaStream_t st);
+cudaError_t launch_adjoint_u(Plan& pl, const float* maps, int B, const float* hk, int use_linear,
+                             float* u, cudaStream_t st);
+// k_solve.cu
+cudaError_t launch_cov_accumulate(Plan& pl, const double* beta, int B, cudaStream_t st);
+cudaError_t launch_zeta(Plan& pl, double* zeta, cudaStream_t st);
+cudaError_t launch_cholesky(Plan& pl, double* A, int n, cudaStream_t st);
+cudaError_t launch_solve_rhs(Plan& pl, const double* Lc, int n, double* rhs, int nrhs, cudaStream_t st);
+cudaError_t launch_estimates(Plan& pl, const double* rhs, int n, int B, double* out, cudaStream_t st);
+cudaError_t launch_wait_selftest(int* d_err, int spin_limit, cudaStream_t st);
+
+}  // namespace modal

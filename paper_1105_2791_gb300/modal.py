@@ -1,0 +1,130 @@
+"""Tensor-level convenience over the C ABI: a Plan object and the autograd Function.
+
+Every method forwards to one entry point of include/modal.h (argument marshalling
+and output allocation only).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class Plan:
+    """Owns one modal plan (device tables, workspace, Monte Carlo accumulators)."""
+
+    def __init__(self, lmax, P, basis, C_l, nrings, nphi, prec="fp32", ring_mask=None, pix_mask=None):
+        self.h = B.modal_init(lmax, P, basis, C_l, nrings, nphi, prec, ring_mask, pix_mask)
+        info = B.modal_get_info(self.h)
+        self.lmax, self.P, self.nrings, self.nphi = info.lmax, info.P, info.nrings, info.nphi
+        self.n_alm, self.n_max, self.n_pair, self.npix = info.n_alm, info.n_max, info.n_pair, info.npix
+        self.prec = info.prec
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            B.modal_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return B.modal_get_info(self.h)
+
+    # -- per-map stages
+    def synthesize(self, alm, out=None):
+        nb = alm.shape[0]
+        if out is None:
+            out = torch.empty((nb, self.P, self.nrings, self.nphi), dtype=torch.float32, device=alm.device)
+        B.modal_synthesize(self.h, alm, nb, out)
+        return out
+
+    def analyze(self, maps, out=None):
+        nb = maps.shape[0]
+        if out is None:
+            out = torch.empty((nb, self.n_alm), dtype=torch.complex64, device=maps.device)
+        B.modal_analyze(self.h, maps, nb, out)
+        return out
+
+    def linear_term(self, alm_sims, finalize=False):
+        nb = 0 if alm_sims is None else alm_sims.shape[0]
+        B.modal_linear_term(self.h, alm_sims, nb, finalize)
+
+    def cubic(self, alm, use_linear=False, out=None):
+        nb = alm.shape[0]
+        if out is None:
+            out = torch.empty((nb, self.n_max), dtype=torch.float64, device=alm.device)
+        B.modal_cubic(self.h, alm, nb, use_linear, out)
+        return out
+
+    def cov_accumulate(self, beta):
+        B.modal_cov_accumulate(self.h, beta, beta.shape[0])
+
+    def solve(self, alpha, beta=None):
+        nb = 0 if beta is None else beta.shape[0]
+        return B.modal_solve(self.h, alpha, beta, nb)
+
+    def backward(self, alm, g, use_linear=False, out=None):
+        nb = alm.shape[0]
+        if out is None:
+            out = torch.empty((nb, self.n_alm), dtype=torch.complex64, device=alm.device)
+        B.modal_backward(self.h, alm, nb, g, use_linear, out)
+        return out
+
+    # -- host-side helpers and accumulators
+    def alpha_local(self, C_signal=None):
+        return B.modal_alpha_local(self.h, C_signal)
+
+    def rings(self):
+        return B.modal_get_rings(self.h)
+
+    def pair_mean(self, device="cuda"):
+        out = torch.empty((self.n_pair, self.npix), dtype=torch.float32, device=device)
+        B.modal_get_pair_mean(self.h, out)
+        return out
+
+    def zeta(self):
+        return B.modal_get_zeta(self.h)
+
+    def reset(self, what=3):
+        B.modal_reset(self.h, what)
+
+    def set_chunk(self, chunk):
+        B.modal_set_chunk(self.h, chunk)
+
+    def sync(self):
+        B.modal_sync(self.h)
+
+    def save_state(self, path):
+        B.modal_save_state(self.h, path)
+
+    def load_state(self, path):
+        B.modal_load_state(self.h, path)
+
+
+class ModalBeta(torch.autograd.Function):
+    """beta = modal coefficients of alm (complex64 [B][n_alm]); backward through the
+    library's adjoint (grad = dL/dRe a_lm + i dL/dIm a_lm, torch's convention for a
+    real loss of complex inputs)."""
+
+    @staticmethod
+    def forward(ctx, alm, plan, use_linear):
+        ctx.plan = plan
+        ctx.use_linear = bool(use_linear)
+        ctx.save_for_backward(alm)
+        return plan.cubic(alm.detach().contiguous(), use_linear)
+
+    @staticmethod
+    def backward(ctx, gbeta):
+        (alm,) = ctx.saved_tensors
+        g = gbeta.detach().to(torch.float64).contiguous()
+        return ctx.plan.backward(alm.detach().contiguous(), g, ctx.use_linear), None, None
+
+
+def modal_beta(alm, plan, use_linear=False):
+    return ModalBeta.apply(alm, plan, use_linear)

@@ -1,0 +1,298 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated by the estimator's accuracy target and the FP32 arithmetic):
+  maps       max |M_gpu - M_oracle| / max |M_oracle| <= 1e-5
+  beta       ||beta_gpu - beta_oracle||_2 / ||beta_oracle||_2 <= 1e-5 per map
+  zeta       ||zeta_gpu - zeta_oracle||_F / ||zeta_oracle||_F <= 1e-5
+  fnl        |fnl_gpu - fnl_oracle| <= 1e-4 sigma
+  gradient   ||g_gpu - g_oracle||_2 / ||g_oracle||_2 <= 1e-5
+Inputs come only from simgen; each side runs its own transforms.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import simgen
+from oracle import modal as om, sht as osh
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [p for p in os.environ.get("MODAL_TEST_PRECS", "fp32,fp16x3,3xtf32").split(",") if p]
+
+
+def _cuda_or_skip():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1105_2791_gb300 as M
+    return M
+
+
+def _plan(M, L, P, basis, cl, R, nphi, prec, **kw):
+    try:
+        return M.Plan(L, P, basis, cl, R, nphi, prec=prec, **kw)
+    except M.ModalError as e:
+        if prec != "fp32" and "not supported" in str(e):
+            pytest.skip("precision %s not built" % prec)
+        raise
+
+
+def _case(L, P, nmaps, seed, amplitude=1.0):
+    basis = simgen.shifted_legendre_basis(L, P)
+    cl = simgen.cl_model(L, amplitude)
+    alm = simgen.gaussian_alm(cl, nmaps, seed=seed).astype(np.complex64)
+    return basis, cl, alm
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+CASES = [
+    # (lmax, P, nrings, nphi, nmaps, chunk)
+    (32, 6, 33, 128, 2, None),       # the l_max = 32 workload (6 modes, 56 coefficients)
+    (45, 5, 50, 128, 3, 2),          # even ring count (no equator), chunk boundary
+    (47, 3, 51, 128, 1, None),       # odd l_max, equator ring
+    (20, 1, 21, 64, 2, 1),           # single basis function
+    (70, 16, 71, 256, 2, None),      # 16 modes (816 coefficients), several tiles
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("L,P,R,nphi,nb,chunk", CASES)
+def test_maps_and_beta_parity(prec, L, P, R, nphi, nb, chunk):
+    M = _cuda_or_skip()
+    basis, cl, alm = _case(L, P, nb, seed=100 + L)
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec)
+    if chunk:
+        plan.set_chunk(chunk)
+    a = torch.from_numpy(alm).cuda()
+    maps = plan.synthesize(a).cpu().numpy()
+    beta = plan.cubic(a).cpu().numpy()
+    plan.sync()
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    W = om.pixel_weights(w, nphi)
+    for b in range(nb):
+        ref = osh.synthesize(alm[b].astype(np.complex128), L, filt, mu, nphi)
+        assert np.max(np.abs(maps[b] - ref)) <= 1e-5 * np.max(np.abs(ref))
+        rb = om.cubic_beta(ref, W)
+        assert _rel(beta[b], rb) <= 1e-5
+    plan.close()
+
+
+def test_analysis_parity():
+    M = _cuda_or_skip()
+    L, R, nphi = 40, 45, 128
+    basis, cl, _ = _case(L, 1, 1, seed=3)
+    plan = _plan(M, L, 1, basis, cl, R, nphi, "fp32")
+    xi = simgen.pixel_normals(R, nphi, 3, seed=9)
+    got = plan.analyze(torch.from_numpy(xi.astype(np.float32)).cuda()).cpu().numpy()
+    mu, w = osh.gl_nodes(R)
+    for b in range(3):
+        ref = osh.analyze(xi[b].astype(np.float32).astype(np.float64), L, mu, w, nphi)
+        assert _rel(got[b], ref) <= 1e-5
+    plan.close()
+
+
+def _noise_alm_gpu(plan, xi, sigma_ring):
+    mu, w = plan.rings()
+    omega = w * 2 * math.pi / plan.nphi
+    nmap = (sigma_ring / np.sqrt(omega))[None, :, None] * xi
+    return plan.analyze(torch.from_numpy(nmap.astype(np.float32)).cuda())
+
+
+def _noise_alm_oracle(L, R, nphi, xi, sigma_ring):
+    mu, w = osh.gl_nodes(R)
+    omega = w * 2 * math.pi / nphi
+    nmap = (sigma_ring / np.sqrt(omega))[None, :, None] * xi
+    return np.stack([osh.analyze(m.astype(np.float32).astype(np.float64), L, mu, w, nphi) for m in nmap])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_linear_term_covariance_and_solve_parity(prec):
+    """Masked sky with anisotropic noise: pair means, beta with the linear term, zeta,
+    alpha and the fNL estimates against the oracle."""
+    M = _cuda_or_skip()
+    L, P, R, nphi = 24, 3, 25, 64
+    n_lin, n_cov, n_dat = 24, 40, 3
+    basis = simgen.shifted_legendre_basis(L, P)
+    cl = simgen.cl_model(L)
+    sig = simgen.noise_sigma_rings(R, 0.1 * cl[L])
+    cl_tot = cl + np.where(np.arange(L + 1) >= 2, 2 * 0.1 * cl[L], 0.0)
+    mask = simgen.band_mask(R, 20.0)
+    plan = _plan(M, L, P, basis, cl_tot, R, nphi, prec, ring_mask=mask)
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl_tot)
+    W = om.pixel_weights(w, nphi, mask)
+
+    def sims(n, seed, stream):
+        sa = simgen.gaussian_alm(cl, n, seed=seed, stream=stream).astype(np.complex64)
+        xi = simgen.pixel_normals(R, nphi, n, seed=seed, stream=simgen.STREAM_NOISE)
+        g = torch.from_numpy(sa).cuda() + _noise_alm_gpu(plan, xi, sig)
+        o = sa.astype(np.complex128) + _noise_alm_oracle(L, R, nphi, xi, sig)
+        return g.contiguous(), o
+
+    g_lin, o_lin = sims(n_lin, 7, simgen.STREAM_LINEAR)
+    plan.linear_term(g_lin[:10])
+    plan.linear_term(g_lin[10:], finalize=True)
+    o_maps_lin = [osh.synthesize(a, L, filt, mu, nphi) for a in o_lin]
+    pm_ref = om.pair_means(o_maps_lin)
+    pm = plan.pair_mean().cpu().numpy().reshape(pm_ref.shape)
+    assert _rel(pm, pm_ref) <= 1e-5
+
+    g_cov, o_cov = sims(n_cov, 8, simgen.STREAM_COV)
+    beta = plan.cubic(g_cov, use_linear=True)
+    plan.cov_accumulate(beta)
+    b_ref = np.stack([om.cubic_beta(osh.synthesize(a, L, filt, mu, nphi), W, pm_ref) for a in o_cov])
+    bg = beta.cpu().numpy()
+    for b in range(n_cov):
+        assert _rel(bg[b], b_ref[b]) <= 1e-5
+    z_ref = om.covariance_zeta(b_ref)
+    assert _rel(plan.zeta(), z_ref) <= 1e-5
+
+    alpha = plan.alpha_local(cl)
+    alpha_ref = om.alpha_local(filt, cl)
+    np.testing.assert_allclose(alpha, alpha_ref, rtol=1e-9, atol=1e-12 * np.abs(alpha_ref).max())
+
+    g_dat, o_dat = sims(n_dat, 9, simgen.STREAM_DATA)
+    bd = plan.cubic(g_dat, use_linear=True)
+    fnl, sigma = plan.solve(alpha, bd)
+    bd_ref = np.stack([om.cubic_beta(osh.synthesize(a, L, filt, mu, nphi), W, pm_ref) for a in o_dat])
+    fnl_ref, sigma_ref = om.solve_fnl(z_ref, alpha_ref, bd_ref)
+    assert sigma == pytest.approx(sigma_ref, rel=1e-5)
+    assert np.max(np.abs(fnl - fnl_ref)) <= 1e-4 * sigma_ref
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("use_linear", [False, True])
+def test_backward_parity(prec, use_linear):
+    M = _cuda_or_skip()
+    L, P, R, nphi = 20, 3, 21, 64
+    basis, cl, alm = _case(L, P, 2, seed=31)
+    mask = simgen.band_mask(R, 20.0)
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec, ring_mask=mask)
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    pm = None
+    if use_linear:
+        sims = simgen.gaussian_alm(cl, 8, seed=32, stream=simgen.STREAM_LINEAR).astype(np.complex64)
+        plan.linear_term(torch.from_numpy(sims).cuda(), finalize=True)
+        pm = om.pair_means([osh.synthesize(s.astype(np.complex128), L, filt, mu, nphi) for s in sims])
+    g = np.random.default_rng(5).standard_normal((2, plan.n_max))
+    grad = plan.backward(torch.from_numpy(alm).cuda(), torch.from_numpy(g).cuda(), use_linear).cpu().numpy()
+    for b in range(2):
+        ref = om.adjoint_grad(alm[b].astype(np.complex128), g[b], L, filt, mu, w, nphi, mask, pm)
+        assert _rel(grad[b], ref) <= 1e-5
+    plan.close()
+
+
+def test_autograd_function_matches_adjoint():
+    M = _cuda_or_skip()
+    L, P, R, nphi = 16, 2, 17, 64
+    basis, cl, alm = _case(L, P, 2, seed=41)
+    plan = _plan(M, L, P, basis, cl, R, nphi, "fp32")
+    a = torch.from_numpy(alm).cuda().requires_grad_(True)
+    g = torch.randn(2, plan.n_max, dtype=torch.float64, device="cuda")
+    beta = M.modal_beta(a, plan)
+    (beta * g).sum().backward()
+    direct = plan.backward(a.detach(), g)
+    torch.testing.assert_close(a.grad, direct)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_l2000_sampled_rings(prec):
+    """l_max = 2000, 2001 x 4096, 16 modes: maps on sampled rings from the pole to the
+    equator against the oracle, and beta restricted (through the ring mask) to them."""
+    M = _cuda_or_skip()
+    L, P, R, nphi = 2000, 16, 2001, 4096
+    basis, cl, alm = _case(L, P, 2, seed=2000)
+    rings = np.array([0, 3, 517, 1000, 1998])
+    mask = np.zeros(R)
+    mask[rings] = 1.0
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec, ring_mask=mask)
+    a = torch.from_numpy(alm).cuda()
+    maps = plan.synthesize(a)[:, :, torch.from_numpy(rings).cuda(), :].cpu().numpy()
+    beta = plan.cubic(a).cpu().numpy()
+    plan.sync()
+    plan.close()
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    W = om.pixel_weights(w[rings], nphi)
+    for b in range(2):
+        ref = osh.synthesize(alm[b].astype(np.complex128), L, filt, mu[rings], nphi)
+        assert np.max(np.abs(maps[b] - ref)) <= 1e-5 * np.max(np.abs(ref))
+        assert _rel(beta[b], om.cubic_beta(ref, W)) <= 1e-5
+
+
+def test_error_paths_and_edge_cases(tmp_path):
+    M = _cuda_or_skip()
+    L, P, R, nphi = 12, 2, 13, 32
+    basis, cl, alm = _case(L, P, 3, seed=51)
+    for bad in [dict(lmax=1), dict(P=17), dict(nphi=48), dict(nrings=L)]:
+        kw = dict(lmax=L, P=P, nrings=R, nphi=nphi)
+        kw.update(bad)
+        b2 = simgen.shifted_legendre_basis(kw["lmax"], kw["P"])
+        with pytest.raises(M.ModalError) as ei:
+            M.Plan(kw["lmax"], kw["P"], b2, simgen.cl_model(kw["lmax"]), kw["nrings"], kw["nphi"])
+        assert ei.value.status == M.MODAL_EINVAL
+    plan = _plan(M, L, P, basis, cl, R, nphi, "fp32")
+    a = torch.from_numpy(alm).cuda()
+    empty = torch.empty((0, plan.n_alm), dtype=torch.complex64, device="cuda")
+    assert plan.cubic(empty).shape == (0, plan.n_max)
+    assert plan.synthesize(empty).shape[0] == 0
+    with pytest.raises(M.ModalError) as ei:
+        plan.cubic(a, use_linear=True)
+    assert ei.value.status == M.MODAL_ESTATE
+    with pytest.raises(M.ModalError) as ei:
+        plan.solve(np.ones(plan.n_max))
+    assert ei.value.status == M.MODAL_ESTATE
+    # rank-deficient covariance: two identical beta vectors
+    beta = plan.cubic(a[:1])
+    plan.cov_accumulate(beta)
+    plan.cov_accumulate(beta)
+    with pytest.raises(M.ModalError) as ei:
+        plan.solve(np.ones(plan.n_max))
+    assert ei.value.status == M.MODAL_ENOTPD
+    plan.sync()
+    # bounded device wait gives up with a status, the context stays usable
+    M.modal_selftest_wait(plan.h, 1000)
+    with pytest.raises(M.ModalError) as ei:
+        plan.sync()
+    assert ei.value.status == M.MODAL_ETIMEOUT
+    plan.sync()
+    b1 = plan.cubic(a)
+    b2 = plan.cubic(a)
+    assert torch.equal(b1, b2)                        # deterministic reduction order
+    plan.close()
+
+
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    M = _cuda_or_skip()
+    L, P, R, nphi = 16, 3, 17, 64
+    basis, cl, alm = _case(L, P, 12, seed=61)
+    a = torch.from_numpy(alm).cuda()
+    one = _plan(M, L, P, basis, cl, R, nphi, "fp32")
+    one.linear_term(a[:6], finalize=True)
+    b = one.cubic(a[6:], use_linear=True)
+    one.cov_accumulate(b[:3])
+    one.cov_accumulate(b[3:])
+    z_one = one.zeta()
+    pm_one = one.pair_mean().cpu()
+    first = _plan(M, L, P, basis, cl, R, nphi, "fp32")
+    first.linear_term(a[:6], finalize=True)
+    first.cov_accumulate(b[:3])
+    first.save_state(tmp_path / "state.bin")
+    first.close()
+    second = _plan(M, L, P, basis, cl, R, nphi, "fp32")
+    second.load_state(tmp_path / "state.bin")
+    second.cov_accumulate(b[3:])
+    assert np.array_equal(second.zeta(), z_one)
+    assert torch.equal(second.pair_mean().cpu(), pm_one)
+    one.close()
+    second.close()
