@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of the modal bispectrum hot path on GB300: maps/s at l_max = 2000, 16 modes.
+
+One step = one batch of B maps through every stage of the per-map path:
+  linear-term pass   synthesis (filter + Legendre sums + ring FFT) and the pair sums
+  coefficient pass   synthesis, cubic term with the linear term, covariance sums
+  solve              FP64 Cholesky of zeta and the fNL estimate of every map
+  adjoint            d(sum_n g_n beta_n)/d a_lm with maps recomputed
+The workload is l_max = 2000 on 2001 Gauss-Legendre rings x 4096 longitudes, 16
+shifted-Legendre modes (n_max = 816), C_l = 1/(l(l+1)), synthetic Gaussian a_lm
+(seeded Philox).  All buffers are far larger than L2 (129 MB), so no flush is needed.
+
+`value` is device-timed maps/s with inputs resident; `e2e` times the same step through
+the public API with a_lm copied from pinned host memory every step and the fNL values
+returned to the host.  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "maps/s at lmax=2000, 816 modes: batched/split-prec vs plain GPU path, err<=1e-5"
+WORKLOAD = dict(lmax=2000, nrings=2001, nphi=4096, P=16)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--batch", type=int, default=32, help="maps per step per GPU")
+    ap.add_argument("--prec", default="auto", help="fp32 | 3xtf32 | fp16x3 | bf16x3 | bf16 | auto")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the plain FP32 comparison and CPU baseline")
+    ap.add_argument("--cpu-rings", type=int, default=8, help="rings in the CPU-baseline sample")
+    ap.add_argument("--lmax", type=int, default=2000, help="smaller l_max for profiler captures only")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def legendre_flops(P, lmax, nrings):
+    """Algorithmic flops of the Legendre sums per map: each (l, m, ring pair) contributes
+    one multiply-add to 2P real outputs (re/im x P) of one parity."""
+    n_alm = (lmax + 1) * (lmax + 2) // 2
+    return 4.0 * P * n_alm * ((nrings + 1) // 2)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import simgen
+    import paper_1105_2791_gb300 as M
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    L, R, nphi, P = WORKLOAD["lmax"], WORKLOAD["nrings"], WORKLOAD["nphi"], WORKLOAD["P"]
+    if args.lmax != L:
+        L, R = args.lmax, args.lmax + 1
+        nphi = 1 << int(math.ceil(math.log2(2 * L + 2)))
+    B = args.batch
+    basis = simgen.shifted_legendre_basis(L, P)
+    cl = simgen.cl_model(L)
+    alm_host = simgen.gaussian_alm(cl, B, seed=3 + 1000 * rank).astype(np.complex64)
+    alm_pinned = torch.from_numpy(alm_host).pin_memory()
+    alm = alm_pinned.to(dev)
+    lin_sims = torch.from_numpy(simgen.gaussian_alm(cl, 2, seed=4 + 1000 * rank,
+                                                    stream=simgen.STREAM_LINEAR).astype(np.complex64)).to(dev)
+
+    def make_plan(prec):
+        try:
+            plan = M.Plan(L, P, basis, cl, R, nphi, prec=prec)
+        except M.ModalError as e:
+            if "not supported" in str(e):
+                return None
+            raise
+        plan.linear_term(lin_sims, finalize=True)      # a mean to subtract from the first step on
+        return plan
+
+    if args.prec == "auto":
+        plan, prec = None, None
+        for cand in ("fp16x3", "3xtf32", "fp32"):
+            plan = make_plan(cand)
+            if plan is not None:
+                prec = cand
+                break
+    else:
+        prec = args.prec
+        plan = make_plan(prec)
+        if plan is None:
+            raise SystemExit("precision %s not available" % prec)
+
+    alpha = plan.alpha_local()
+    g = torch.from_numpy(np.tile(alpha / (alpha @ alpha), (B, 1))).to(dev)
+    beta = torch.empty((B, plan.n_max), dtype=torch.float64, device=dev)
+    grad = torch.empty((B, plan.n_alm), dtype=torch.complex64, device=dev)
+    # Seed the covariance sums with 2 n_max random vectors so that zeta is positive definite
+    # from the first step on (a real run accumulates N_cov >> n_max simulations first).
+    gen = torch.Generator(device=dev).manual_seed(5)
+    plan.cov_accumulate(torch.randn((2 * plan.n_max, plan.n_max), generator=gen, device=dev, dtype=torch.float64))
+    torch.cuda.synchronize()
+
+    def step(pl, a, e2e=False):
+        if e2e:
+            a.copy_(alm_pinned, non_blocking=True)
+        pl.linear_term(a)
+        pl.cubic(a, use_linear=True, out=beta)
+        pl.cov_accumulate(beta)
+        fnl, sigma = pl.solve(alpha, beta)
+        pl.backward(a, g, use_linear=True, out=grad)
+        return fnl, sigma
+
+    def timed(pl, a, steps, warmup, e2e=False, profile=False):
+        for _ in range(warmup):
+            step(pl, a, e2e)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        M.modal_get_profile(pl.h)                          # reset counters
+        M.modal_set_profiling(pl.h, profile)
+        st = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(st)
+        for _ in range(steps):
+            step(pl, a, e2e)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        prof = M.modal_get_profile(pl.h)
+        M.modal_set_profiling(pl.h, False)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof
+
+    K, W = args.steps, args.warmup
+    with ClockSampler(local) as clocks:
+        ms, prof_plain_timing = timed(plan, alm, K, W)
+    clk = clocks.summary()
+    # kernel-level timing in a separate timed pass with per-launch events
+    _, prof = timed(plan, alm, max(1, K // 2), 1, profile=True)
+    launches = sum(n for (_, n) in prof_plain_timing.values())
+    # end to end through the public API from pinned host memory
+    a_e2e = torch.empty_like(alm)
+    e2e_ms, _ = timed(plan, a_e2e, K, 1, e2e=True)
+
+    value = B * K * world / (ms / 1e3)
+    e2e_value = B * K * world / (e2e_ms / 1e3)
+    leg_ms, leg_n = prof["legendre"]
+    n_prof_steps = max(1, K // 2)
+    flops = legendre_flops(P, L, R) * B * n_prof_steps * 3     # three syntheses per map per step
+    achieved = flops / (leg_ms / 1e3) / 1e12
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    if prec == "fp32":
+        # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (maximum SM clock)
+        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(152 * 128 * 2 * 2.07e9 / 1e12, 1),
+                "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        bf16 = peaks.get("bf16_tflops_sustained", 1710.9)
+        per = {"fp16x3": 3.0, "bf16x3": 3.0, "3xtf32": 6.0, "bf16": 1.0}[prec]
+        roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(bf16 / per, 1),
+                "unit": "TFLOP/s", "peak_source": "measured bf16 sustained / %g products per useful MAC" % per}
+    roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
+    roof["traffic"] = None
+    roof["kernel"] = "legendre (forward Legendre sums), %d launches, %.3f ms per launch" % (
+        leg_n, leg_ms / max(leg_n, 1))
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "maps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(ms / K, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "3xtf32": "tf32x3", "fp16x3": "f16x3", "bf16x3": "bf16x3", "bf16": "bf16"}[prec],
+        "data": "synthetic",
+        "config": {"workload": "lmax=%d GL %dx%d, P=%d (n_max=%d), batch %d maps/step/GPU, %s" % (
+                       L, R, nphi, P, plan.n_max, B, prec),
+                   "lmax": L, "nrings": R, "nphi": nphi, "P": P, "n_max": plan.n_max, "batch_per_gpu": B,
+                   "precision": prec, "l2": "inputs and intermediates > L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": {"value": round(e2e_value, 3), "unit": "maps/s",
+                "h2d_bytes_per_step": int(alm.numel() * 8), "d2h_bytes_per_step": int(B * 8 + 8)},
+        "roofline": roof,
+        "stage_ms_per_step": {k: round(v[0] / n_prof_steps, 3) for k, v in prof.items() if v[1]},
+    }
+
+    if rank == 0 and not args.no_baseline and prec != "fp32":
+        plan.close()
+        plain = make_plan("fp32")
+        plain.cov_accumulate(torch.randn((2 * plain.n_max, plain.n_max), generator=gen, device=dev,
+                                         dtype=torch.float64))
+        pms, _ = timed(plain, alm, max(1, K // 2), 1)
+        result["plain_fp32_value"] = round(B * max(1, K // 2) / (pms / 1e3), 3)
+        result["speedup_vs_plain_fp32"] = round(value / world / result["plain_fp32_value"], 3)
+        plain.close()
+    if rank == 0 and not args.no_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.cpu_rings)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- oracle (CPU baseline and reference arm)
+def oracle_step_sample(nring_sample, seed=3):
+    """One map of the workload through the oracle's per-map step (synthesis, pair means,
+    cubic with the linear term, adjoint) on `nring_sample` rings spread pole to equator;
+    returns (seconds, extrapolated seconds per map)."""
+    import simgen
+    from oracle import modal as om, sht as osh
+
+    L, R, nphi, P = WORKLOAD["lmax"], WORKLOAD["nrings"], WORKLOAD["nphi"], WORKLOAD["P"]
+    basis = simgen.shifted_legendre_basis(L, P)
+    cl = simgen.cl_model(L)
+    filt = osh.filter_table(basis, cl)
+    a = simgen.gaussian_alm(cl, 1, seed=seed)[0]
+    mu, w = osh.gl_nodes(R)
+    rings = np.unique(np.linspace(0, R // 2, nring_sample).astype(int))
+    t0 = time.perf_counter()
+    maps = osh.synthesize(a, L, filt, mu[rings], nphi)
+    pm = om.pair_means([maps])
+    beta = om.cubic_beta(maps, om.pixel_weights(w[rings], nphi), pm)
+    g = np.ones(beta.size) / beta.size
+    om.adjoint_grad(a, g, L, filt, mu[rings], w[rings], nphi, None, pm)
+    dt = time.perf_counter() - t0
+    return dt, dt * R / len(rings), len(rings)
+
+
+def cpu_baseline(nring_sample):
+    dt, per_map, k = oracle_step_sample(nring_sample)
+    return {"value": round(1.0 / per_map, 8), "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "1 map at lmax=2000 (P=16, 4096 longitudes) on %d of 2001 rings: synthesis, pair means, "
+                      "cubic with linear term, adjoint; %.1f s, extrapolated by ring count" % (k, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_step_sample(2)
+    total, per_maps = 0.0, []
+    for _ in range(args.steps):
+        dt, per_map, k = oracle_step_sample(args.cpu_rings)
+        total += dt
+        per_maps.append(per_map)
+    per_map = float(np.mean(per_maps))
+    value = 1.0 / per_map
+    sample = ("1 map per step at lmax=2000 (P=16, 4096 longitudes) on %d of 2001 rings, extrapolated by ring "
+              "count" % k)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": "maps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "lmax=2000 GL 2001x4096, P=16 (n_max=816), FP64 CPU oracle", "lmax": 2000,
+                   "nrings": 2001, "nphi": 4096, "P": 16},
+        "cpu_baseline": {"value": round(value, 8), "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 8), "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -111,7 +111,8 @@ modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void*
 /* Linear-term simulations (Sec. II: the mean <M_p M_r>_x "calculated from Monte Carlo
  * simulations of Gaussian maps"): synthesise B sims, add M_p M_r of each to the FP64
  * pair sums.  finalize != 0 then forms <M_p M_r>_x = sums / n_lin (used by modal_cubic
- * and modal_backward with use_linear != 0).  B may be 0 with finalize set. */
+ * and modal_backward with use_linear != 0); later simulations change the sums but not
+ * this mean until the next finalize.  B may be 0 with finalize set. */
 modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int finalize, void* stream);
 
 /* Modal coefficients (Eq. bbispect): dev alm [B][n_alm] -> dev beta [B][n_max] (float64).
@@ -170,6 +171,17 @@ modal_status modal_load_state(modal_h h, const char* path);
  * up after `spin_limit` polls; the next modal_sync returns MODAL_ETIMEOUT.  Exercises
  * the bounded-wait error path without faulting the GPU. */
 modal_status modal_selftest_wait(modal_h h, int spin_limit, void* stream);
+
+/* Per-stage timing.  With profiling enabled every kernel launch of the plan is
+ * bracketed by CUDA events recorded on the launching stream.  modal_get_profile
+ * synchronises, writes for each stage s < nstages the summed event time in ms
+ * (stage_ms, may be NULL) and the number of kernel launches (launches, may be NULL;
+ * counted whether or not profiling is on) since the previous call, then resets both.
+ * Stages are numbered 0 .. MODAL_NSTAGES-1; modal_stage_name gives their names. */
+#define MODAL_NSTAGES 12
+modal_status modal_set_profiling(modal_h h, int enable);
+modal_status modal_get_profile(modal_h h, double* stage_ms, long long* launches, int nstages);
+const char* modal_stage_name(int stage);
 
 void modal_destroy(modal_h h);
 const char* modal_last_error(void);

@@ -29,8 +29,9 @@ EXPORTS = [
     "modal_cov_accumulate", "modal_solve", "modal_backward", "modal_alpha_local", "modal_get_info",
     "modal_get_rings", "modal_get_pair_mean", "modal_get_zeta", "modal_reset", "modal_set_chunk",
     "modal_sync", "modal_save_state", "modal_load_state", "modal_selftest_wait", "modal_destroy",
-    "modal_last_error",
+    "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name",
 ]
+MODAL_NSTAGES = 12
 
 
 class ModalError(RuntimeError):
@@ -88,6 +89,8 @@ def load_library():
         "modal_save_state": [H, c_char_p],
         "modal_load_state": [H, c_char_p],
         "modal_selftest_wait": [H, c_int, c_void_p],
+        "modal_set_profiling": [H, c_int],
+        "modal_get_profile": [H, c_void_p, c_void_p, c_int],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -95,6 +98,8 @@ def load_library():
         fn.restype = c_int
     lib.modal_destroy.argtypes = [H]
     lib.modal_destroy.restype = None
+    lib.modal_stage_name.argtypes = [c_int]
+    lib.modal_stage_name.restype = c_char_p
     lib.modal_last_error.argtypes = []
     lib.modal_last_error.restype = c_char_p
     _LIB = lib
@@ -237,6 +242,23 @@ def modal_load_state(h, path):
 
 def modal_selftest_wait(h, spin_limit, stream=None):
     _check(load_library().modal_selftest_wait(h, int(spin_limit), _stream(stream)))
+
+
+def modal_set_profiling(h, enable):
+    _check(load_library().modal_set_profiling(h, int(bool(enable))))
+
+
+def modal_get_profile(h):
+    """{stage name: (ms, launches)} accumulated since the previous call (then reset)."""
+    ms = np.zeros(MODAL_NSTAGES)
+    n = np.zeros(MODAL_NSTAGES, dtype=np.int64)
+    _check(load_library().modal_get_profile(h, ms.ctypes.data_as(c_void_p), n.ctypes.data_as(c_void_p),
+                                            MODAL_NSTAGES))
+    return {modal_stage_name(i): (float(ms[i]), int(n[i])) for i in range(MODAL_NSTAGES)}
+
+
+def modal_stage_name(stage):
+    return load_library().modal_stage_name(int(stage)).decode()
 
 
 def modal_destroy(h):

@@ -113,8 +113,10 @@ __host__ __device__ inline int fft_rings_per_block(int N) {
 }
 
 // grid: (ceil(R_half / RPB), nmp); nmp = number of (map, p) rows.
+// delta layout [nmp][L+1][2][RH]: even (E) and odd (O) Legendre sums per ring pair;
+// north = E + O, south = E - O.
 __global__ void __launch_bounds__(FFT_THREADS)
-k_ring_c2r(int L, int R, int R_half, int N, int log2N, const float2* __restrict__ delta,
+k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __restrict__ delta,
            const float2* __restrict__ tw, float* __restrict__ maps) {
     extern __shared__ float2 buf[];
     const int RPB = fft_rings_per_block(N);
@@ -123,12 +125,13 @@ k_ring_c2r(int L, int R, int R_half, int N, int log2N, const float2* __restrict_
     const int ntr = min(RPB, R_half - j0);
     for (int i = threadIdx.x; i < ntr * N; i += FFT_THREADS) buf[i] = make_float2(0.f, 0.f);
     __syncthreads();
-    const float2* d = delta + (int64_t)mp * (L + 1) * R;
+    const float2* d = delta + (int64_t)mp * (L + 1) * 2 * RH;
     for (int i = threadIdx.x; i < (L + 1) * ntr; i += FFT_THREADS) {
         const int m = i / ntr, q = i % ntr;
-        const int jn = j0 + q, js = R - 1 - jn;
-        const float2 dn = d[(int64_t)m * R + jn];
-        const float2 ds = d[(int64_t)m * R + js];
+        const float2 e = d[(int64_t)m * 2 * RH + j0 + q];
+        const float2 o = d[(int64_t)m * 2 * RH + RH + j0 + q];
+        const float2 dn = make_float2(e.x + o.x, e.y + o.y);
+        const float2 ds = make_float2(e.x - o.x, e.y - o.y);
         if (m == 0) {
             buf[q * N] = make_float2(dn.x, ds.x);
         } else {
@@ -197,7 +200,8 @@ cudaError_t launch_ring_c2r(const Plan& pl, const float2* delta, int nmp, float*
     cudaError_t e = cudaFuncSetAttribute(k_ring_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
-    k_ring_c2r<<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, N, ilog2(N), delta, pl.twiddle, maps);
+    k_ring_c2r<<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, N, ilog2(N), delta, pl.twiddle,
+                                                maps);
     return cudaGetLastError();
 }
 

@@ -4,8 +4,9 @@
 // Forward:  D_{b,p,m}(theta) = sum_{l>=m} lambda_lm(theta) f_p(l) a_{b,lm},
 // split by the parity of l - m into E (even) and O (odd) so that one table row
 // serves the north ring (E + O) and its mirror south ring (E - O), since
-// lambda_lm(-mu) = (-1)^{l+m} lambda_lm(mu).  This is the separable evaluation
-// of the filtered maps whose cube gives Eq. bbispect.
+// lambda_lm(-mu) = (-1)^{l+m} lambda_lm(mu).  E and O are stored per ring pair
+// (delta layout [B][P][lmax+1][2][RH]); the ring FFT combines them.  This is the
+// separable evaluation of the filtered maps whose cube gives Eq. bbispect.
 #include "modal_internal.cuh"
 
 namespace modal {
@@ -17,7 +18,7 @@ k_legendre_simt(int L, int P, int R, int R_half, int RH, const float* __restrict
                 float2* __restrict__ delta) {
     constexpr int CH = 64;
     __shared__ float2 sa[CH];
-    __shared__ float sf[CH][PM];
+    __shared__ __align__(16) float sf[CH][PM];
     const int m = blockIdx.y, b = blockIdx.z;
     const int j = blockIdx.x * 128 + threadIdx.x;
     const int64_t base = d_alm_index(m, m, L);
@@ -41,34 +42,39 @@ k_legendre_simt(int L, int P, int R, int R_half, int RH, const float* __restrict
         }
         __syncthreads();
         if (active) {
-            for (int i = 0; i < n; i += 2) {
-                const float lv = lp[(int64_t)(l0 - m + i) * RH];
-                const float2 t = make_float2(lv * sa[i].x, lv * sa[i].y);
+            // l0 - m is a multiple of CH (even), so i + u has the parity of u.
+            for (int i = 0; i < n; i += 8) {
+                float lv[8];
 #pragma unroll
-                for (int p = 0; p < PM; ++p) {
-                    accE[p].x = fmaf(sf[i][p], t.x, accE[p].x);
-                    accE[p].y = fmaf(sf[i][p], t.y, accE[p].y);
-                }
-                if (i + 1 < n) {
-                    const float lv2 = lp[(int64_t)(l0 - m + i + 1) * RH];
-                    const float2 t2 = make_float2(lv2 * sa[i + 1].x, lv2 * sa[i + 1].y);
+                for (int u = 0; u < 8; ++u) lv[u] = (i + u < n) ? lp[(int64_t)(l0 - m + i + u) * RH] : 0.f;
 #pragma unroll
-                    for (int p = 0; p < PM; ++p) {
-                        accO[p].x = fmaf(sf[i + 1][p], t2.x, accO[p].x);
-                        accO[p].y = fmaf(sf[i + 1][p], t2.y, accO[p].y);
+                for (int u = 0; u < 8; ++u) {
+                    const float2 t = make_float2(lv[u] * sa[i + u].x, lv[u] * sa[i + u].y);
+                    float2* acc = (u & 1) ? accO : accE;
+                    const float4* f4 = reinterpret_cast<const float4*>(&sf[i + u][0]);
+#pragma unroll
+                    for (int q = 0; q < PM / 4; ++q) {
+                        const float4 f = f4[q];
+                        acc[4 * q + 0].x = fmaf(f.x, t.x, acc[4 * q + 0].x);
+                        acc[4 * q + 0].y = fmaf(f.x, t.y, acc[4 * q + 0].y);
+                        acc[4 * q + 1].x = fmaf(f.y, t.x, acc[4 * q + 1].x);
+                        acc[4 * q + 1].y = fmaf(f.y, t.y, acc[4 * q + 1].y);
+                        acc[4 * q + 2].x = fmaf(f.z, t.x, acc[4 * q + 2].x);
+                        acc[4 * q + 2].y = fmaf(f.z, t.y, acc[4 * q + 2].y);
+                        acc[4 * q + 3].x = fmaf(f.w, t.x, acc[4 * q + 3].x);
+                        acc[4 * q + 3].y = fmaf(f.w, t.y, acc[4 * q + 3].y);
                     }
                 }
             }
         }
     }
     if (!active) return;
-    const int js = R - 1 - j;
 #pragma unroll
     for (int p = 0; p < PM; ++p) {
         if (p < P) {
-            const int64_t row = ((int64_t)(b * P + p) * (L + 1) + m) * R;
-            delta[row + j] = make_float2(accE[p].x + accO[p].x, accE[p].y + accO[p].y);
-            if (js != j) delta[row + js] = make_float2(accE[p].x - accO[p].x, accE[p].y - accO[p].y);
+            const int64_t row = ((int64_t)(b * P + p) * (L + 1) + m) * 2 * RH;
+            delta[row + j] = accE[p];
+            delta[row + RH + j] = accO[p];
         }
     }
 }

@@ -1,17 +1,623 @@
-// Tensor-core (tcgen05) Legendre sums: placeholder until the sm_103a kernel lands.
+// Tensor-core (tcgen05, sm_103a) Legendre sums with compensated split precision.
+//
+// For every order m and parity pi of l - m the contraction
+//     D_pi[j, n] = sum_{l = m + pi (mod 2)} lambda_lm(theta_j) * F[l, n],
+//     F[l, (b, p, c)] = f_p(l) * (Re, Im)_c a_{b,lm}
+// is a GEMM with M = ring pairs j, N = 2 P x (8 maps), K = l.  The north ring gets
+// E + O, its mirror south ring E - O (lambda_lm(-mu) = (-1)^{l+m} lambda_lm(mu)).
+//
+// Work item = (m, parity, tile of 128 ring pairs, group of 8 maps).  A persistent CTA
+// loops over items.  Per pipeline stage it holds 128 bytes of K per row:
+//   A (lambda, pre-split hi/lo, pre-tiled in HBM): fetched with one cp.async.bulk;
+//   B (filtered a_lm): formed, scaled and split hi/lo in shared memory by 8 warps.
+// One thread issues tcgen05.mma: hi*hi into TMEM accumulator D1 (columns 0..N-1) and
+// the cross products hi*lo + lo*hi into D2 (columns N..2N-1).  The tensor core rounds
+// its FP32 accumulator once per MMA; keeping the small cross terms apart makes their
+// rounding 2^-11 smaller, so the error of a sum over ~10^3 values of l stays near
+// (K/16) 2^-24 instead of three times that.  The same 8 warps then drain TMEM,
+// form D1 + D2, undo the scaling and write the even (E) or odd (O) row for the ring
+// pairs; the ring FFT forms north = E + O and south = E - O.
+// Operands use the no-swizzle K-major core-matrix layout: element (row r, k) at
+// (r/8)*1024 + (k/(16/E))*128 + (r%8)*16 + (k%(16/E))*E bytes (E = element bytes).
+//
+// Every mbarrier wait is bounded (~1 s of clock): on expiry the kernel records
+// MODAL_DEVERR_TIMEOUT, the roles drain, in-flight copies are awaited (bounded) and
+// TMEM is freed before exit.
 #include "modal_internal.cuh"
+
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 
 namespace modal {
 
-cudaError_t build_tc_tables(Plan& pl, cudaStream_t) {
-    (void)pl;
-    return cudaErrorNotSupported;
+constexpr int TC_MAPS = 8;                 // maps per work item (N = 16 P)
+constexpr int TC_PROD_WARPS = 8;           // B producers / epilogue
+constexpr int TC_THREADS = 32 * (2 + TC_PROD_WARPS);
+constexpr int TC_STAGES = 2;
+constexpr int TC_KB = 128;                 // bytes of K per row per stage (8 core matrices)
+constexpr int TC_SBO = 8 * TC_KB;          // bytes between 8-row groups
+constexpr int TC_A_TILE = 128 * TC_KB;     // bytes: 128 rows x 128 bytes of K
+constexpr int TC_A_STAGE = 2 * TC_A_TILE;  // hi, lo
+constexpr float TC_LAMBDA_SCALE = 2048.f;  // |lambda| * 2^11 stays inside fp16 range
+constexpr long long TC_WAIT_CYCLES = 1ll << 31;
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the CTA is aborting or the wait gave up (then it aborts).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > TC_WAIT_CYCLES) {
+            atomicOr(err, MODAL_DEVERR_TIMEOUT);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle; LBO = 128 B (next core matrix
+// along K), SBO = 1024 B (next 8-row group), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(TC_SBO >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
 }
 
-void free_tc_tables(Plan& pl) { (void)pl; }
+// Instruction descriptor: fp32 accumulate, K-major A and B, M = 128, N = n.
+// fmt: 0 = f16, 1 = bf16 (kind::f16); 2 = tf32 (kind::tf32).
+__host__ __device__ constexpr uint32_t umma_idesc(int fmt, int n) {
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(128 >> 4) << 24);
+}
 
-cudaError_t launch_legendre_tc(const Plan&, const float2*, int, float2*, cudaStream_t) {
-    return cudaErrorNotSupported;
+template <bool TF32>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    if (TF32) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ element splitting
+// PREC: MODAL_FP16X3, MODAL_BF16X3, MODAL_BF16 (16-bit elements), MODAL_3XTF32 (32-bit).
+template <int PREC>
+struct Split;
+
+template <>
+struct Split<MODAL_FP16X3> {
+    static constexpr int E = 2, FMT = 0, PRODUCTS = 3;
+    __device__ static void split(float x, uint16_t& hi, uint16_t& lo) {
+        const __half h = __float2half_rn(x);
+        const __half l = __float2half_rn(x - __half2float(h));
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(l);
+    }
+};
+template <>
+struct Split<MODAL_BF16X3> {
+    static constexpr int E = 2, FMT = 1, PRODUCTS = 3;
+    __device__ static void split(float x, uint16_t& hi, uint16_t& lo) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(l);
+    }
+};
+template <>
+struct Split<MODAL_BF16> {
+    static constexpr int E = 2, FMT = 1, PRODUCTS = 1;
+    __device__ static void split(float x, uint16_t& hi, uint16_t& lo) {
+        hi = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+        lo = 0;
+    }
+};
+template <>
+struct Split<MODAL_3XTF32> {
+    static constexpr int E = 4, FMT = 2, PRODUCTS = 3;
+    // Both parts rounded to nearest tf32 (unbiased), so the tensor core reads them exactly.
+    __device__ static uint32_t to_tf32(float x) {
+        uint32_t r;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+        return r;
+    }
+    __device__ static void split(float x, uint32_t& hi, uint32_t& lo) {
+        hi = to_tf32(x);
+        lo = to_tf32(x - __uint_as_float(hi));
+    }
+};
+
+// Power-of-two exponent k that brings the map's largest |f_p(l) a_lm| into [2^14, 2^15)
+// (fp16 keeps 11 significant bits down to 2^-14; the lo parts stay normal well below
+// the largest values).  amax_bits: the float bits of that maximum (0 for an empty map).
+__device__ __forceinline__ int tc_scale_exp(unsigned amax_bits) {
+    if (amax_bits == 0u) return 0;
+    const int e = (int)((amax_bits >> 23) & 0xFF);             // biased exponent
+    return max(-120, min(120, 141 - e));
+}
+
+template <int E>
+struct ElemT;
+template <>
+struct ElemT<2> { using T = uint16_t; };
+template <>
+struct ElemT<4> { using T = uint32_t; };
+
+// ------------------------------------------------------------------ table builder
+// Number of values of l in [m, L] with l - m = pi (mod 2), and K blocks of KPS of them
+// (at least one, zero-padded, so that every item writes its row).
+__host__ __device__ inline int tc_nkb(int L, int m, int pi, int kps) {
+    const int k = (L - m - pi >= 0) ? (L - m - pi) / 2 + 1 : 0;
+    return k > 0 ? (k + kps - 1) / kps : 1;
+}
+
+// Stage block (m, pi, rt, kb) = [hi tile, lo tile] of 128 ring pairs x KPS values of
+// l = m + pi + 2 (kb KPS + k), KPS = 128 / E; lambda scaled by 2^11 for 16-bit formats.
+template <int PREC>
+__global__ void k_build_tc_table(int L, int R_half, int RH, int n_rt, const float* __restrict__ lam,
+                                 const int64_t* __restrict__ blk_base, void* __restrict__ out) {
+    using S = Split<PREC>;
+    using T = typename ElemT<S::E>::T;
+    constexpr int KPS = TC_KB / S::E;
+    constexpr int CM = 16 / S::E;            // K values per core matrix
+    const int m = blockIdx.y >> 1, pi = blockIdx.y & 1;
+    const int nkb = tc_nkb(L, m, pi, KPS);
+    const int64_t base_m = d_alm_index(m, m, L);
+    const float scale = (S::E == 2) ? TC_LAMBDA_SCALE : 1.f;
+    for (int64_t blk = blockIdx.x; blk < (int64_t)n_rt * nkb; blk += gridDim.x) {
+        const int rt = (int)(blk / nkb), kb = (int)(blk % nkb);
+        char* dst = reinterpret_cast<char*>(out) + (blk_base[2 * m + pi] + blk) * TC_A_STAGE;
+        for (int e = threadIdx.x; e < 128 * KPS; e += blockDim.x) {
+            const int r = e / KPS, k = e % KPS;
+            const int l = m + pi + 2 * (kb * KPS + k);
+            const int j = rt * 128 + r;
+            float v = 0.f;
+            if (l <= L && j < R_half) v = lam[(base_m + (l - m)) * (int64_t)RH + j] * scale;
+            T hi, lo;
+            S::split(v, hi, lo);
+            const int off = (r / 8) * TC_SBO + (k / CM) * 128 + (r % 8) * 16 + (k % CM) * S::E;
+            *reinterpret_cast<T*>(dst + off) = hi;
+            *reinterpret_cast<T*>(dst + TC_A_TILE + off) = lo;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ per-map scale
+// amax[b] = max_{l,m,p} |f_p(l) a_{b,lm}| as float bits (positive floats order as ints).
+__global__ void k_alm_amax(int L, const float* __restrict__ fmax_l, const float2* __restrict__ alm, int64_t n_alm,
+                           unsigned* __restrict__ amax) {
+    const int m = blockIdx.y, b = blockIdx.z;
+    const int64_t base = d_alm_index(m, m, L);
+    float v = 0.f;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= L - m; k += gridDim.x * blockDim.x) {
+        const float2 a = alm[(int64_t)b * n_alm + base + k];
+        v = fmaxf(v, fmaxf(fabsf(a.x), fabsf(a.y)) * fmax_l[m + k]);
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(&amax[b], __float_as_uint(v));
+}
+
+// ------------------------------------------------------------------ main kernel
+struct TcArgs {
+    int L, P, R, R_half, RH, n_rt, B, n_groups;
+    int64_t n_items, n_alm;
+    const char* table;             // pre-tiled A blocks
+    const int64_t* blk_base;       // [2 (L+1)] first block of (m, parity)
+    const float* filt;             // [P][L+1]
+    const float2* alm;             // [B][n_alm]
+    const unsigned* amax;          // [B] float bits
+    float2* delta;                 // [B][P][L+1][2][RH]: E and O rows per ring pair
+    int* err;
+};
+
+// item -> (m, pi, rt, g); consecutive items share the lambda tiles (same m, pi, rt).
+__device__ __forceinline__ void tc_item(const TcArgs& a, int64_t item, int& m, int& pi, int& rt, int& g) {
+    g = (int)(item % a.n_groups);
+    int64_t t = item / a.n_groups;
+    rt = (int)(t % a.n_rt);
+    t /= a.n_rt;
+    pi = (int)(t & 1);
+    m = (int)(t >> 1);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
+    using S = Split<PREC>;
+    using T = typename ElemT<S::E>::T;
+    constexpr bool TF32 = (PREC == MODAL_3XTF32);
+    constexpr int KPS = TC_KB / S::E;     // K values per stage
+    constexpr int CM = 16 / S::E;         // K values per core matrix
+    constexpr int NKC = TC_KB / 16;       // core matrices along K per stage (8)
+    const int N = 16 * a.P;               // 2 (re, im) x P x 8 maps
+    const int b_tile = N * TC_KB;         // bytes of one B tile
+
+    extern __shared__ __align__(1024) char smem[];
+    char* sA = smem;                                        // [TC_STAGES][hi, lo]
+    char* sB = sA + TC_STAGES * TC_A_STAGE;                 // [TC_STAGES][hi, lo][b_tile]
+    float2* s_a = reinterpret_cast<float2*>(sB + TC_STAGES * 2 * 256 * TC_KB);   // [8][KPS]
+    float* s_f = reinterpret_cast<float*>(s_a + TC_MAPS * 64);                   // [KPS][16]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s_f + 64 * 16);
+    uint64_t* full = bars;                                  // [TC_STAGES]
+    uint64_t* empty = bars + TC_STAGES;                     // [TC_STAGES]
+    uint64_t* tmem_full = bars + 2 * TC_STAGES;
+    uint64_t* tmem_empty = tmem_full + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = (2 * N <= 256) ? 256u : 512u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1 + TC_PROD_WARPS);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(tmem_full, 1);
+        mbar_init(tmem_empty, TC_PROD_WARPS);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- A loader (one thread)
+        if (lane == 0) {
+            uint32_t it = 0;
+            uint32_t last_phase[TC_STAGES] = {0, 0};
+            bool issued[TC_STAGES] = {false, false};
+            for (int64_t item = blockIdx.x; item < a.n_items && !*abort_flag; item += gridDim.x) {
+                int m, pi, rt, g;
+                tc_item(a, item, m, pi, rt, g);
+                const int nkb = tc_nkb(a.L, m, pi, KPS);
+                const char* src = a.table + (a.blk_base[2 * m + pi] + (int64_t)rt * nkb) * TC_A_STAGE;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % TC_STAGES;
+                    const uint32_t ph = (it / TC_STAGES) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err)) break;
+                    mbar_arrive_expect_tx(&full[s], TC_A_STAGE);
+                    bulk_copy_g2s(sA + s * TC_A_STAGE, src + (int64_t)kb * TC_A_STAGE, TC_A_STAGE, &full[s]);
+                    last_phase[s] = ph;
+                    issued[s] = true;
+                }
+            }
+            // copies still in flight complete before the CTA exits
+            for (int s = 0; s < TC_STAGES; ++s) {
+                if (!issued[s]) continue;
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&full[s], last_phase[s]) && clock64() - t0 < TC_WAIT_CYCLES) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc(S::FMT, N);
+            const uint32_t d1 = tmem, d2 = tmem + (uint32_t)N;
+            uint32_t it = 0, nitem = 0;
+            for (int64_t item = blockIdx.x; item < a.n_items && !*abort_flag; item += gridDim.x, ++nitem) {
+                int m, pi, rt, g;
+                tc_item(a, item, m, pi, rt, g);
+                const int nkb = tc_nkb(a.L, m, pi, KPS);
+                if (!mbar_wait(tmem_empty, (nitem & 1) ^ 1, abort_flag, a.err)) break;
+                tc_fence_after();
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % TC_STAGES;
+                    const uint32_t ph = (it / TC_STAGES) & 1;
+                    if (!mbar_wait(&full[s], ph, abort_flag, a.err)) break;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + s * TC_A_STAGE);
+                    const uint32_t b0 = smem_u32(sB + s * 2 * b_tile);
+#pragma unroll
+                    for (int ks = 0; ks < NKC / 2; ++ks) {
+                        const uint32_t koff = ks * 2 * 128;          // 2 core matrices (32 B of K) per MMA
+                        const uint64_t ah = umma_desc(a0 + koff);
+                        const uint64_t al = umma_desc(a0 + TC_A_TILE + koff);
+                        const uint64_t bh = umma_desc(b0 + koff);
+                        const uint64_t bl = umma_desc(b0 + b_tile + koff);
+                        const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
+                        umma<TF32>(d1, ah, bh, idesc, first);
+                        if (S::PRODUCTS == 3) {
+                            umma<TF32>(d2, ah, bl, idesc, first);
+                            umma<TF32>(d2, al, bh, idesc, 1u);
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                }
+                umma_commit(tmem_full);
+            }
+        }
+    } else {
+        // ---------------- B producers + epilogue (TC_PROD_WARPS warps)
+        // These warps meet at named barrier 1 a data-independent number of times; after an
+        // abort they keep looping (skipping all work) so that no warp waits there alone.
+        const int pt = threadIdx.x - 64;                    // 0 .. 255
+        const int quarter = warp % 4;                       // TMEM lanes 32 quarter .. + 31
+        const int half = (warp - 2) / 4;                    // column half for the epilogue
+        const int nblk = a.P;                               // 16-column blocks (N = 16 P)
+        const int blk_lo = half ? (nblk + 1) / 2 : 0, blk_hi = half ? nblk : (nblk + 1) / 2;
+        uint32_t it = 0, nitem = 0;
+        for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x, ++nitem) {
+            int m, pi, rt, g;
+            tc_item(a, item, m, pi, rt, g);
+            const int nkb = tc_nkb(a.L, m, pi, KPS);
+            const int64_t base_m = d_alm_index(m, m, a.L);
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = it % TC_STAGES;
+                const uint32_t ph = (it / TC_STAGES) & 1;
+                const int l0 = m + pi + 2 * kb * KPS;              // l of K index k: l0 + 2 k
+                // stage a (8 maps x KPS values of l, scaled per map) and f (KPS x P)
+                named_sync(1, 32 * TC_PROD_WARPS);
+                for (int i = pt; i < TC_MAPS * KPS; i += 32 * TC_PROD_WARPS) {
+                    const int bl = i / KPS, k = i % KPS;
+                    const int b = g * TC_MAPS + bl, l = l0 + 2 * k;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (b < a.B && l <= a.L) {
+                        v = a.alm[(int64_t)b * a.n_alm + base_m + (l - m)];
+                        const float sc = exp2f((float)tc_scale_exp(a.amax[b]));
+                        v.x *= sc;
+                        v.y *= sc;
+                    }
+                    s_a[i] = v;
+                }
+                for (int i = pt; i < KPS * 16; i += 32 * TC_PROD_WARPS) {
+                    const int k = i / 16, p = i % 16, l = l0 + 2 * k;
+                    s_f[i] = (p < a.P && l <= a.L) ? a.filt[(int64_t)p * (a.L + 1) + l] : 0.f;
+                }
+                named_sync(1, 32 * TC_PROD_WARPS);
+                const bool ok = !*abort_flag && mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err);
+                if (ok) {
+                    char* bt = sB + s * 2 * b_tile;
+                    // chunks: (core-matrix column kc, row n); 16 bytes of K per chunk
+                    const int nchunks = NKC * N;
+                    for (int c = pt; c < nchunks; c += 32 * TC_PROD_WARPS) {
+                        const int kc = c / N, n = c % N;
+                        const int bl = n / (2 * a.P), p = (n / 2) % a.P, comp = n % 2;
+                        T hv[CM], lv[CM];
+#pragma unroll
+                        for (int i = 0; i < CM; ++i) {
+                            const int k = kc * CM + i;
+                            const float2 av = s_a[bl * KPS + k];
+                            const float x = s_f[k * 16 + p] * (comp ? av.y : av.x);
+                            S::split(x, hv[i], lv[i]);
+                        }
+                        const int off = (n / 8) * TC_SBO + kc * 128 + (n % 8) * 16;
+                        *reinterpret_cast<uint4*>(bt + off) = *reinterpret_cast<const uint4*>(hv);
+                        *reinterpret_cast<uint4*>(bt + b_tile + off) = *reinterpret_cast<const uint4*>(lv);
+                    }
+                    fence_proxy_async();
+                }
+                __syncwarp();
+                if (ok && lane == 0) mbar_arrive(&full[s]);
+            }
+            // ---------------- epilogue: TMEM -> D1 + D2 -> E or O row of delta
+            bool ok = !*abort_flag && mbar_wait(tmem_full, nitem & 1, abort_flag, a.err);
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                tc_fence_after();
+                const int jn = rt * 128 + quarter * 32 + lane;   // TMEM lane = ring pair within the tile
+                const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+                for (int blk = blk_lo; blk < blk_hi; ++blk) {
+                    const int c0 = blk * 16;
+                    float d[16], d2[16];
+                    tmem_ld16(lane_addr + c0, d);
+                    if (S::PRODUCTS == 3) {
+                        tmem_ld16(lane_addr + N + c0, d2);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) d[i] += d2[i];
+                    }
+                    if (jn < a.R_half) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int n = c0 + 2 * q;             // even column: re, odd: im
+                            const int bl = n / (2 * a.P), p = (n / 2) % a.P;
+                            const int b = g * TC_MAPS + bl;
+                            if (b < a.B) {
+                                // undo the per-map 2^k on a and 2^11 on lambda (16-bit formats)
+                                const float inv = exp2f((float)-tc_scale_exp(a.amax[b])) *
+                                                  ((S::E == 2) ? (1.f / TC_LAMBDA_SCALE) : 1.f);
+                                const int64_t row = (((int64_t)(b * a.P + p) * (a.L + 1) + m) * 2 + pi) * a.RH;
+                                a.delta[row + jn] = make_float2(d[2 * q] * inv, d[2 * q + 1] * inv);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+            }
+            __syncwarp();
+            if (ok && lane == 0) mbar_arrive(tmem_empty);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+    }
+}
+
+static size_t tc_smem_bytes() {
+    return 1024 /*alignment slack*/ + TC_STAGES * TC_A_STAGE + TC_STAGES * 2 * 256 * TC_KB + TC_MAPS * 64 * 8 +
+           64 * 16 * 4 + 8 * (2 * TC_STAGES + 2) + 16;
+}
+
+// ------------------------------------------------------------------ host side
+static int kps_for(int prec) { return prec == MODAL_3XTF32 ? TC_KB / 4 : TC_KB / 2; }
+
+cudaError_t build_tc_tables(Plan& pl, cudaStream_t st) {
+    const int L = pl.lmax;
+    const int KPS = kps_for(pl.prec);
+    pl.tc.n_rt = (pl.R_half + 127) / 128;
+    pl.tc.kb_off.assign(2 * (L + 1), 0);
+    int64_t total = 0;
+    for (int m = 0; m <= L; ++m)
+        for (int pi = 0; pi < 2; ++pi) {
+            pl.tc.kb_off[2 * m + pi] = total;
+            total += (int64_t)pl.tc.n_rt * tc_nkb(L, m, pi, KPS);
+        }
+    pl.tc.n_kb = total;
+    pl.tc.bytes = (size_t)total * TC_A_STAGE;
+    cudaError_t e = cudaMalloc(&pl.tc.hi, pl.tc.bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&pl.tc.d_kb_off, 2 * (L + 1) * sizeof(int64_t));
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&pl.tc.d_amax, 4096 * sizeof(unsigned));
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&pl.tc.d_fmax, (L + 1) * sizeof(float));
+    if (e != cudaSuccess) return e;
+    pl.device_bytes += pl.tc.bytes + (L + 1) * (2 * sizeof(int64_t) + sizeof(float)) + 4096 * sizeof(unsigned);
+    e = cudaMemcpy(pl.tc.d_kb_off, pl.tc.kb_off.data(), 2 * (L + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    {
+        std::vector<float> fm(L + 1, 0.f);
+        for (int l = 0; l <= L; ++l) {
+            if (pl.cl[l] <= 0) continue;
+            for (int p = 0; p < pl.P; ++p)
+                fm[l] = std::max(fm[l], (float)std::fabs(pl.basis[(size_t)p * (L + 1) + l] / std::sqrt(pl.cl[l])));
+        }
+        e = cudaMemcpy(pl.tc.d_fmax, fm.data(), (L + 1) * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(std::min(pl.tc.n_rt * 64, 1024), 2 * (L + 1));
+    switch (pl.prec) {
+        case MODAL_FP16X3:
+            k_build_tc_table<MODAL_FP16X3><<<grid, 256, 0, st>>>(L, pl.R_half, pl.RH, pl.tc.n_rt, pl.lam, pl.tc.d_kb_off, pl.tc.hi);
+            break;
+        case MODAL_BF16X3:
+            k_build_tc_table<MODAL_BF16X3><<<grid, 256, 0, st>>>(L, pl.R_half, pl.RH, pl.tc.n_rt, pl.lam, pl.tc.d_kb_off, pl.tc.hi);
+            break;
+        case MODAL_BF16:
+            k_build_tc_table<MODAL_BF16><<<grid, 256, 0, st>>>(L, pl.R_half, pl.RH, pl.tc.n_rt, pl.lam, pl.tc.d_kb_off, pl.tc.hi);
+            break;
+        case MODAL_3XTF32:
+            k_build_tc_table<MODAL_3XTF32><<<grid, 256, 0, st>>>(L, pl.R_half, pl.RH, pl.tc.n_rt, pl.lam, pl.tc.d_kb_off, pl.tc.hi);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+void free_tc_tables(Plan& pl) {
+    if (pl.tc.hi) cudaFree(pl.tc.hi);
+    if (pl.tc.d_kb_off) cudaFree(pl.tc.d_kb_off);
+    if (pl.tc.d_amax) cudaFree(pl.tc.d_amax);
+    if (pl.tc.d_fmax) cudaFree(pl.tc.d_fmax);
+    pl.tc = TcTable();
+}
+
+template <int PREC>
+static cudaError_t launch_tc(const Plan& pl, const TcArgs& args, cudaStream_t st) {
+    const size_t smem = tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_legendre_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl.dev);
+    const int grid = (int)std::min<int64_t>(args.n_items, (int64_t)std::max(nsm, 1));
+    k_legendre_tc<PREC><<<grid, TC_THREADS, smem, st>>>(args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st) {
+    if (B == 0) return cudaSuccess;
+    if (B > 4096) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(pl.tc.d_amax, 0, B * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    {
+        dim3 grid(std::max(1, std::min(8, (pl.lmax + 1 + 255) / 256)), pl.lmax + 1, B);
+        k_alm_amax<<<grid, 256, 0, st>>>(pl.lmax, pl.tc.d_fmax, alm, pl.n_alm, pl.tc.d_amax);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    TcArgs a;
+    a.L = pl.lmax;
+    a.P = pl.P;
+    a.R = pl.nrings;
+    a.R_half = pl.R_half;
+    a.RH = pl.RH;
+    a.n_rt = pl.tc.n_rt;
+    a.B = B;
+    a.n_groups = (B + TC_MAPS - 1) / TC_MAPS;
+    a.n_items = (int64_t)(pl.lmax + 1) * 2 * a.n_rt * a.n_groups;
+    a.n_alm = pl.n_alm;
+    a.table = static_cast<const char*>(pl.tc.hi);
+    a.blk_base = pl.tc.d_kb_off;
+    a.filt = pl.filt;
+    a.alm = alm;
+    a.amax = pl.tc.d_amax;
+    a.delta = delta;
+    a.err = pl.d_err;
+    switch (pl.prec) {
+        case MODAL_FP16X3: return launch_tc<MODAL_FP16X3>(pl, a, st);
+        case MODAL_BF16X3: return launch_tc<MODAL_BF16X3>(pl, a, st);
+        case MODAL_BF16: return launch_tc<MODAL_BF16>(pl, a, st);
+        case MODAL_3XTF32: return launch_tc<MODAL_3XTF32>(pl, a, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace modal

@@ -150,7 +150,7 @@ static void build_mode_tables(modal_plan* pl, std::vector<int>& mi) {
 // ------------------------------------------------------------------ workspace
 static size_t per_map_workspace(const modal_plan* pl) {
     const size_t L1 = pl->lmax + 1;
-    const size_t delta = (size_t)pl->P * L1 * pl->nrings * sizeof(float2);
+    const size_t delta = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
     const size_t maps = (size_t)pl->P * pl->npix * sizeof(float);
     const size_t ut = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
     return delta + maps + ut;
@@ -173,7 +173,7 @@ static modal_status alloc_workspace(modal_plan* pl, int chunk) {
     pl->chunk = chunk;
     const size_t before = pl->device_bytes;
     const size_t L1 = pl->lmax + 1;
-    CK(dalloc(pl, &pl->delta, (size_t)chunk * pl->P * L1 * pl->nrings), "workspace delta");
+    CK(dalloc(pl, &pl->delta, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace delta");
     CK(dalloc(pl, &pl->maps, (size_t)chunk * pl->P * pl->npix), "workspace maps");
     CK(dalloc(pl, &pl->ut, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace ut");
     CK(dalloc(pl, &pl->hk, (size_t)chunk * pl->P * pl->n_pair), "workspace hk");
@@ -205,6 +205,8 @@ static void destroy_plan(modal_plan* pl) {
     dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->S1); dfree(pl->S2);
     dfree(pl->solve_ws); dfree(pl->d_err);
     free_tc_tables(*pl);
+    for (auto& pe : pl->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
+    for (auto e : pl->prof_pool) cudaEventDestroy(e);
     delete pl;
 }
 
@@ -217,6 +219,40 @@ static modal_status check_plan(modal_h h) {
 
 static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Brackets one kernel launch: counts it under `stage` and, with profiling on, records
+// CUDA events before and after it on the launching stream.
+struct StageScope {
+    modal_plan* pl;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    static cudaEvent_t take(modal_plan* p) {
+        if (!p->prof_pool.empty()) {
+            cudaEvent_t e = p->prof_pool.back();
+            p->prof_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    StageScope(modal_plan* p, int s, cudaStream_t stream) : pl(p), stage(s), st(stream) {
+        pl->stage_launches[stage] += 1;
+        if (pl->prof) {
+            a = take(pl);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~StageScope() {
+        if (pl->prof && a) {
+            cudaEvent_t b = take(pl);
+            cudaEventRecord(b, st);
+            pl->prof_pending.push_back({stage, {a, b}});
+        }
+    }
+};
+#define STAGE(pl, id, st) StageScope _scope_##id((pl), (id), (st))
+
 // Legendre stage for one chunk: alm -> delta.
 static cudaError_t legendre_forward(modal_plan* pl, const float2* alm, int B, cudaStream_t st) {
     if (pl->prec == MODAL_FP32) return launch_legendre_simt(*pl, alm, B, pl->delta, st);
@@ -224,8 +260,12 @@ static cudaError_t legendre_forward(modal_plan* pl, const float2* alm, int B, cu
 }
 
 static cudaError_t synth_chunk(modal_plan* pl, const float2* alm, int B, float* maps_out, cudaStream_t st) {
-    cudaError_t e = legendre_forward(pl, alm, B, st);
-    if (e != cudaSuccess) return e;
+    {
+        STAGE(pl, ST_LEGENDRE, st);
+        cudaError_t e = legendre_forward(pl, alm, B, st);
+        if (e != cudaSuccess) return e;
+    }
+    STAGE(pl, ST_C2R, st);
     return launch_ring_c2r(*pl, pl->delta, B * pl->P, maps_out, st);
 }
 
@@ -408,8 +448,8 @@ modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void*
     const int step = h->chunk * h->P;   // ut holds chunk*P channels
     for (int b0 = 0; b0 < B; b0 += step) {
         const int nb = std::min(step, B - b0);
-        CK(launch_ring_r2c(*h, maps + (size_t)b0 * h->npix, nb, h->wring, h->ut, st), "analyze r2c");
-        CK(launch_legendre_adjoint_simt(*h, h->ut, nb, nullptr, 1, out + (size_t)b0 * h->n_alm, st), "analyze legendre");
+        { STAGE(h, ST_R2C, st); CK(launch_ring_r2c(*h, maps + (size_t)b0 * h->npix, nb, h->wring, h->ut, st), "analyze r2c"); }
+        { STAGE(h, ST_LEGENDRE_ADJ, st); CK(launch_legendre_adjoint_simt(*h, h->ut, nb, nullptr, 1, out + (size_t)b0 * h->n_alm, st), "analyze legendre"); }
     }
     return MODAL_OK;
 }
@@ -425,13 +465,12 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "linear-term synthesis");
-        CK(launch_pair_accumulate(*h, h->maps, nb, st), "pair accumulate");
+        { STAGE(h, ST_PAIRS, st); CK(launch_pair_accumulate(*h, h->maps, nb, st), "pair accumulate"); }
     }
     h->n_lin += B;
-    if (B > 0) h->lin_final = 0;
     if (finalize) {
         if (h->n_lin < 1) return set_error(MODAL_ESTATE, "finalize with no linear-term simulations");
-        CK(launch_pair_finalize(*h, st), "pair finalize");
+        { STAGE(h, ST_PAIRS, st); CK(launch_pair_finalize(*h, st), "pair finalize"); }
         h->lin_final = 1;
     }
     return MODAL_OK;
@@ -449,9 +488,9 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "cubic synthesis");
-        CK(launch_cubic(*h, h->maps, nb, cub, st), "cubic");
-        if (use_linear) CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm");
-        CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, beta + (size_t)b0 * h->n_max, st), "beta finalize");
+        { STAGE(h, ST_CUBIC, st); CK(launch_cubic(*h, h->maps, nb, cub, st), "cubic"); }
+        if (use_linear) { STAGE(h, ST_LINEAR, st); CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm"); }
+        { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, beta + (size_t)b0 * h->n_max, st), "beta finalize"); }
     }
     return MODAL_OK;
 }
@@ -460,7 +499,7 @@ modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* st
     if (check_plan(h)) return MODAL_EINVAL;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B > 0 && !beta) return set_error(MODAL_EINVAL, "null pointer");
-    CK(launch_cov_accumulate(*h, beta, B, as_stream(stream)), "cov accumulate");
+    { STAGE(h, ST_COV, as_stream(stream)); CK(launch_cov_accumulate(*h, beta, B, as_stream(stream)), "cov accumulate"); }
     h->n_cov += B;
     return MODAL_OK;
 }
@@ -492,14 +531,14 @@ modal_status modal_solve(modal_h h, const double* alpha, const double* beta, int
     double* est = rhs + (size_t)(B + 1) * n;
     modal_status s = MODAL_OK;
     auto run = [&]() -> modal_status {
-        CK(launch_zeta(*h, A, st), "zeta");
-        CK(launch_cholesky(*h, A, n, st), "cholesky");
+        { STAGE(h, ST_SOLVE, st); CK(launch_zeta(*h, A, st), "zeta"); }
+        { STAGE(h, ST_SOLVE, st); CK(launch_cholesky(*h, A, n, st), "cholesky"); }
         CK(cudaMemcpyAsync(rhs, alpha, n * sizeof(double), cudaMemcpyHostToDevice, st), "alpha copy");
         if (B > 0) CK(cudaMemcpyAsync(rhs + n, beta, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice, st), "beta copy");
         modal_status es = read_device_error(h, st);
         if (es != MODAL_OK) return es;
-        CK(launch_solve_rhs(*h, A, n, rhs, B + 1, st), "triangular solve");
-        CK(launch_estimates(*h, rhs, n, B, est, st), "estimates");
+        { STAGE(h, ST_SOLVE, st); CK(launch_solve_rhs(*h, A, n, rhs, B + 1, st), "triangular solve"); }
+        { STAGE(h, ST_SOLVE, st); CK(launch_estimates(*h, rhs, n, B, est, st), "estimates"); }
         std::vector<double> out(B + 1);
         CK(cudaMemcpyAsync(out.data(), est, (B + 1) * sizeof(double), cudaMemcpyDeviceToHost, st), "estimates copy");
         CK(cudaStreamSynchronize(st), "solve sync");
@@ -526,10 +565,10 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "backward synthesis");
-        CK(launch_adjoint_weights(*h, g + (size_t)b0 * h->n_max, nb, h->hk, st), "adjoint weights");
-        CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear, h->maps, st), "adjoint pixel");
-        CK(launch_ring_r2c(*h, h->maps, nb * h->P, nullptr, h->ut, st), "adjoint r2c");
-        CK(launch_legendre_adjoint_simt(*h, h->ut, nb, h->filt, h->P, out + (size_t)b0 * h->n_alm, st), "adjoint legendre");
+        { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_weights(*h, g + (size_t)b0 * h->n_max, nb, h->hk, st), "adjoint weights"); }
+        { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear, h->maps, st), "adjoint pixel"); }
+        { STAGE(h, ST_R2C, st); CK(launch_ring_r2c(*h, h->maps, nb * h->P, nullptr, h->ut, st), "adjoint r2c"); }
+        { STAGE(h, ST_LEGENDRE_ADJ, st); CK(launch_legendre_adjoint_simt(*h, h->ut, nb, h->filt, h->P, out + (size_t)b0 * h->n_alm, st), "adjoint legendre"); }
     }
     return MODAL_OK;
 }
@@ -645,7 +684,7 @@ modal_status modal_sync(modal_h h, void* stream) {
 modal_status modal_selftest_wait(modal_h h, int spin_limit, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
     if (spin_limit < 1) return set_error(MODAL_EINVAL, "spin_limit must be >= 1");
-    CK(launch_wait_selftest(h->d_err, spin_limit, as_stream(stream)), "wait selftest");
+    { STAGE(h, ST_OTHER, as_stream(stream)); CK(launch_wait_selftest(h->d_err, spin_limit, as_stream(stream)), "wait selftest"); }
     return MODAL_OK;
 }
 
@@ -721,6 +760,42 @@ modal_status modal_load_state(modal_h h, const char* path) {
         CK(launch_pair_finalize(*h, 0), "pair finalize");
         CK(cudaDeviceSynchronize(), "load sync");
         h->lin_final = 1;
+    }
+    return MODAL_OK;
+}
+
+static const char* kStageNames[MODAL_NSTAGES] = {
+    "legendre", "ring_c2r", "cubic", "linear_gemm", "beta_finalize", "pair_means",
+    "cov_accumulate", "solve", "adjoint_pixel", "ring_r2c", "legendre_adjoint", "other"};
+
+const char* modal_stage_name(int stage) {
+    return (stage >= 0 && stage < MODAL_NSTAGES) ? kStageNames[stage] : "";
+}
+
+modal_status modal_set_profiling(modal_h h, int enable) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    h->prof = enable ? 1 : 0;
+    return MODAL_OK;
+}
+
+modal_status modal_get_profile(modal_h h, double* stage_ms, long long* launches, int nstages) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (nstages < 0 || nstages > MODAL_NSTAGES) return set_error(MODAL_EINVAL, "nstages out of range");
+    CK(cudaDeviceSynchronize(), "profile sync");
+    for (auto& pe : h->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) h->stage_ms[pe.first] += ms;
+        h->prof_pool.push_back(pe.second.first);
+        h->prof_pool.push_back(pe.second.second);
+    }
+    h->prof_pending.clear();
+    for (int s = 0; s < nstages; ++s) {
+        if (stage_ms) stage_ms[s] = h->stage_ms[s];
+        if (launches) launches[s] = h->stage_launches[s];
+    }
+    for (int s = 0; s < MODAL_NSTAGES; ++s) {
+        h->stage_ms[s] = 0.0;
+        h->stage_launches[s] = 0;
     }
     return MODAL_OK;
 }

@@ -35,7 +35,9 @@ struct TcTable {
     int n_rt = 0;                       // ring tiles of TC_BM ring pairs
     std::vector<int64_t> kb_off;        // per (m, parity): first K block index (prefix sums)
     int64_t n_kb = 0;                   // total K blocks over all (m, parity)
-    int64_t* d_kb_off = nullptr;        // device copy of kb_off ([2*(lmax+1)+1])
+    int64_t* d_kb_off = nullptr;        // device copy of kb_off ([lmax+1])
+    unsigned* d_amax = nullptr;         // per-map scale bounds (float bits), [4096]
+    float* d_fmax = nullptr;            // max_p |f_p(l)|, [lmax+1]
     size_t bytes = 0;
 };
 
@@ -72,7 +74,7 @@ struct Plan {
     long long n_cov = 0;
 
     // workspace (sized by chunk)
-    float2* delta = nullptr;     // [chunk][P][lmax+1][nrings]
+    float2* delta = nullptr;     // [chunk][P][lmax+1][2][RH]: even/odd Legendre sums per ring pair
     float* maps = nullptr;       // [chunk][P][npix]
     float2* ut = nullptr;        // [chunk][P][lmax+1][2][RH] (adjoint)
     double* partial = nullptr;   // cubic / linear partial sums
@@ -85,6 +87,18 @@ struct Plan {
     size_t device_bytes = 0;
     size_t workspace_bytes = 0;
     std::vector<int> cubic_pair_ab_host, cubic_tiles_host;
+
+    // profiling: per-stage event pairs and launch counters
+    int prof = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double stage_ms[MODAL_NSTAGES] = {};
+    long long stage_launches[MODAL_NSTAGES] = {};
+};
+
+enum Stage {
+    ST_LEGENDRE = 0, ST_C2R = 1, ST_CUBIC = 2, ST_LINEAR = 3, ST_BETA = 4, ST_PAIRS = 5,
+    ST_COV = 6, ST_SOLVE = 7, ST_ADJ_PIXEL = 8, ST_R2C = 9, ST_LEGENDRE_ADJ = 10, ST_OTHER = 11
 };
 
 // ---- error reporting (modal_api.cu) ----

@@ -78,9 +78,11 @@ def test_maps_and_beta_parity(prec, L, P, R, nphi, nb, chunk):
     W = om.pixel_weights(w, nphi)
     for b in range(nb):
         ref = osh.synthesize(alm[b].astype(np.complex128), L, filt, mu, nphi)
-        assert np.max(np.abs(maps[b] - ref)) <= 1e-5 * np.max(np.abs(ref))
-        rb = om.cubic_beta(ref, W)
-        assert _rel(beta[b], rb) <= 1e-5
+        merr = np.max(np.abs(maps[b] - ref)) / np.max(np.abs(ref))
+        berr = _rel(beta[b], om.cubic_beta(ref, W))
+        print("lmax=%d P=%d %s map %d: maps max rel err %.3g, beta rel err %.3g" % (L, P, prec, b, merr, berr))
+        assert merr <= 1e-5
+        assert berr <= 1e-5
     plan.close()
 
 
@@ -226,8 +228,11 @@ def test_full_size_l2000_sampled_rings(prec):
     W = om.pixel_weights(w[rings], nphi)
     for b in range(2):
         ref = osh.synthesize(alm[b].astype(np.complex128), L, filt, mu[rings], nphi)
-        assert np.max(np.abs(maps[b] - ref)) <= 1e-5 * np.max(np.abs(ref))
-        assert _rel(beta[b], om.cubic_beta(ref, W)) <= 1e-5
+        merr = np.max(np.abs(maps[b] - ref)) / np.max(np.abs(ref))
+        berr = _rel(beta[b], om.cubic_beta(ref, W))
+        print("lmax=2000 %s map %d: maps max rel err %.3g, beta rel err %.3g" % (prec, b, merr, berr))
+        assert merr <= 1e-5
+        assert berr <= 1e-5
 
 
 def test_error_paths_and_edge_cases(tmp_path):
@@ -296,3 +301,22 @@ def test_checkpoint_resume_is_bit_exact(tmp_path):
     assert torch.equal(second.pair_mean().cpu(), pm_one)
     one.close()
     second.close()
+
+
+@pytest.mark.parametrize("prec,bound", [("bf16x3", 1e-3), ("bf16", 5e-2)])
+def test_reported_precisions(prec, bound):
+    """BF16X3 and BF16 are reported, not accepted at 1e-5: their beta error is measured and
+    printed, and only has to stay below a loose bound."""
+    M = _cuda_or_skip()
+    L, P, R, nphi = 70, 16, 71, 256
+    basis, cl, alm = _case(L, P, 2, seed=171)
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec)
+    beta = plan.cubic(torch.from_numpy(alm).cuda()).cpu().numpy()
+    plan.close()
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    W = om.pixel_weights(w, nphi)
+    errs = [_rel(beta[b], om.cubic_beta(osh.synthesize(alm[b].astype(np.complex128), L, filt, mu, nphi), W))
+            for b in range(2)]
+    print("%s beta rel err: %s" % (prec, errs))
+    assert max(errs) <= bound
