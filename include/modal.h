@@ -172,6 +172,21 @@ modal_status modal_load_state(modal_h h, const char* path);
  * the bounded-wait error path without faulting the GPU. */
 modal_status modal_selftest_wait(modal_h h, int spin_limit, void* stream);
 
+/* Allocation-free cubic coefficients, for callers that cannot call cudaMalloc (device
+ * memory owned by another allocator, or loops where an allocation's implicit device
+ * synchronisation is not acceptable).  The paper has no counterpart: it is the cubic
+ * reduction of modal_cubic without the linear term, on maps the caller already holds:
+ *   beta[b][n] = sum_x W[x] M_p M_r M_s,  n <-> (p <= r <= s) lexicographic.
+ * maps: dev float [B][P][npix]; W: dev float [npix]; beta: dev double [B][n_max].
+ * Needs no plan and allocates nothing: per-block partial sums go to one static device
+ * array of 4 Mi doubles (32 MiB, held by every GPU that loads the library until exit),
+ * so B * n_max must not exceed 4 Mi (and B <= 65535), else MODAL_EINVAL.  Every call
+ * shares that array and overwrites what it reads, so nothing needs clearing, but calls
+ * that overlap on the GPU race on it.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream capture. */
+modal_status modal_cubic_static(const float* maps, const float* W, long long npix, int P, int B,
+                                double* beta, void* stream);
+
 /* Per-stage timing.  With profiling enabled every kernel launch of the plan is
  * bracketed by CUDA events recorded on the launching stream.  modal_get_profile
  * synchronises, writes for each stage s < nstages the summed event time in ms

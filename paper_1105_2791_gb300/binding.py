@@ -29,7 +29,7 @@ EXPORTS = [
     "modal_cov_accumulate", "modal_solve", "modal_backward", "modal_alpha_local", "modal_get_info",
     "modal_get_rings", "modal_get_pair_mean", "modal_get_zeta", "modal_reset", "modal_set_chunk",
     "modal_sync", "modal_save_state", "modal_load_state", "modal_selftest_wait", "modal_destroy",
-    "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name",
+    "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
 ]
 MODAL_NSTAGES = 12
 
@@ -91,8 +91,14 @@ def load_library():
         "modal_selftest_wait": [H, c_int, c_void_p],
         "modal_set_profiling": [H, c_int],
         "modal_get_profile": [H, c_void_p, c_void_p, c_int],
+        "modal_cubic_static": [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p],
     }
     for name, args in sig.items():
+        if name == "modal_cubic_static":
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = c_int
+            continue
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = c_int
@@ -259,6 +265,12 @@ def modal_get_profile(h):
 
 def modal_stage_name(stage):
     return load_library().modal_stage_name(int(stage)).decode()
+
+
+def modal_cubic_static(maps, W, npix, P, B, beta, stream=None):
+    """Allocation-free cubic coefficients of caller-held maps (see include/modal.h)."""
+    _check(load_library().modal_cubic_static(_dev(maps), _dev(W), int(npix), int(P), int(B), _dev(beta),
+                                             _stream(stream)))
 
 
 def modal_destroy(h):
