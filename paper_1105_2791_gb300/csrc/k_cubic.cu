@@ -37,6 +37,13 @@ k_cubic(int P, int SU, int SM, int ntiles, const int* __restrict__ tiles, const 
     const int64_t x_begin = (int64_t)blockIdx.x * px_per_cta;
     const int64_t x_end = min(npix, x_begin + px_per_cta);
     const float* mb = maps + (int64_t)b * P * npix;
+    // pair-product fill: thread -> (pair column, block of pixels), fixed for the CTA
+    const int nsplit = max(1, nthr / SU);
+    const int fill_c = (tid < nsplit * SU) ? tid % SU : -1;
+    const int fill_part = (tid < nsplit * SU) ? tid / SU : 0;
+    const int fill_nx = (CUB_TX + nsplit - 1) / nsplit;
+    const int fill_x0 = fill_part * fill_nx;
+    const int fill_ab = (fill_c >= 0) ? pair_ab[fill_c] : -1;
 
     float acc[32];
 #pragma unroll
@@ -50,10 +57,10 @@ k_cubic(int P, int SU, int SM, int ntiles, const int* __restrict__ tiles, const 
         }
         for (int i = tid; i < CUB_TX; i += nthr) sW[i] = (x0 + i < x_end) ? W[x0 + i] : 0.f;
         __syncthreads();
-        for (int i = tid; i < CUB_TX * SU; i += nthr) {
-            const int xl = i / SU, c = i % SU;
-            const int ab = pair_ab[c];
-            sU[i] = (ab >= 0) ? sW[xl] * sM[xl * SM + (ab & 0xff)] * sM[xl * SM + (ab >> 8)] : 0.f;
+        if (fill_c >= 0) {
+            for (int xl = fill_x0; xl < fill_x0 + fill_nx && xl < CUB_TX; ++xl)
+                sU[xl * SU + fill_c] = (fill_ab >= 0) ? sW[xl] * sM[xl * SM + (fill_ab & 0xff)] * sM[xl * SM + (fill_ab >> 8)]
+                                                      : 0.f;
         }
         __syncthreads();
         if (computes) {
@@ -296,54 +303,84 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
 }
 
 // In place: maps[b][t][x] <- U_t(x) = W_x sum_c hk[b][t][c] (M_a M_b' - <c>_x).
-template <int PM>
-__global__ void __launch_bounds__(128)
+// One thread per pixel; its P map values sit in a shared-memory column; pairs are
+// taken 8 at a time so that each row of hk is read as two float4 per 8 pairs
+// (4 FMAs per shared load).
+constexpr int AU_THREADS = 256;
+
+__global__ void __launch_bounds__(AU_THREADS)
 k_adjoint_u(int P, int n_pair, int64_t npix, const float* __restrict__ hk, const float* __restrict__ pm,
             const float* __restrict__ W, float* __restrict__ maps) {
-    __shared__ float sh[PM * PM * (PM + 1) / 2];
-    const int b = blockIdx.y;
-    for (int i = threadIdx.x; i < P * n_pair; i += blockDim.x) sh[i] = hk[(int64_t)b * P * n_pair + i];
+    constexpr int SC = 136;                           // pairs padded to a multiple of 8 (P <= 16)
+    __shared__ __align__(16) float sH[MODAL_MAXP * SC];
+    __shared__ int s_pa[SC], s_pb[SC];
+    __shared__ float sM[MODAL_MAXP][AU_THREADS];
+    const int b = blockIdx.y, tid = threadIdx.x;
+    for (int i = tid; i < MODAL_MAXP * SC; i += AU_THREADS) {
+        const int t = i / SC, c = i % SC;
+        sH[i] = (t < P && c < n_pair) ? hk[((int64_t)b * P + t) * n_pair + c] : 0.f;
+    }
+    for (int c = tid; c < SC; c += AU_THREADS) {
+        int pa = 0, pb = 0;
+        if (c < n_pair) {
+            int cc = c;
+            while (cc >= P - pa) { cc -= P - pa; ++pa; }
+            pb = pa + cc;
+        }
+        s_pa[c] = pa;
+        s_pb[c] = pb;
+    }
     __syncthreads();
     float* mb = maps + (int64_t)b * P * npix;
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < npix; x += (int64_t)gridDim.x * blockDim.x) {
-        float mv[PM], u[PM];
+    const float4* H4 = reinterpret_cast<const float4*>(sH);
+    for (int64_t x0 = (int64_t)blockIdx.x * AU_THREADS; x0 < npix; x0 += (int64_t)gridDim.x * AU_THREADS) {
+        const int64_t x = x0 + tid;
+        const bool in = x < npix;
+        for (int p = 0; p < P; ++p) sM[p][tid] = in ? mb[(int64_t)p * npix + x] : 0.f;
+        float u[MODAL_MAXP];
 #pragma unroll
-        for (int p = 0; p < PM; ++p) {
-            mv[p] = (p < P) ? mb[(int64_t)p * npix + x] : 0.f;
-            u[p] = 0.f;
-        }
+        for (int t = 0; t < MODAL_MAXP; ++t) u[t] = 0.f;
+        for (int c0 = 0; c0 < n_pair; c0 += 8) {
+            float y[8];
 #pragma unroll
-        for (int p = 0; p < PM; ++p)
-#pragma unroll
-            for (int r = p; r < PM; ++r) {
-                if (r < P) {
-                    const int c = pair_lex(p, r, P);
-                    float y = mv[p] * mv[r];
-                    if (pm) y -= pm[(int64_t)c * npix + x];
-#pragma unroll
-                    for (int t = 0; t < PM; ++t)
-                        if (t < P) u[t] = fmaf(sh[t * n_pair + c], y, u[t]);
+            for (int i = 0; i < 8; ++i) {
+                const int c = c0 + i;
+                float v = 0.f;
+                if (c < n_pair) {
+                    v = sM[s_pa[c]][tid] * sM[s_pb[c]][tid];
+                    if (pm && in) v -= pm[(int64_t)c * npix + x];
                 }
+                y[i] = v;
             }
-        const float wx = W[x];
 #pragma unroll
-        for (int t = 0; t < PM; ++t)
-            if (t < P) mb[(int64_t)t * npix + x] = wx * u[t];
+            for (int t = 0; t < MODAL_MAXP; ++t) {
+                const float4 h0 = H4[(t * SC + c0) / 4], h1 = H4[(t * SC + c0) / 4 + 1];
+                u[t] = fmaf(h0.x, y[0], u[t]);
+                u[t] = fmaf(h0.y, y[1], u[t]);
+                u[t] = fmaf(h0.z, y[2], u[t]);
+                u[t] = fmaf(h0.w, y[3], u[t]);
+                u[t] = fmaf(h1.x, y[4], u[t]);
+                u[t] = fmaf(h1.y, y[5], u[t]);
+                u[t] = fmaf(h1.z, y[6], u[t]);
+                u[t] = fmaf(h1.w, y[7], u[t]);
+            }
+        }
+        if (in) {
+            const float wx = W[x];
+#pragma unroll
+            for (int t = 0; t < MODAL_MAXP; ++t)
+                if (t < P) mb[(int64_t)t * npix + x] = wx * u[t];
+        }
     }
 }
 
 cudaError_t launch_adjoint_u(Plan& pl, const float* /*maps_in*/, int B, const float* hk, int use_linear, float* maps,
                              cudaStream_t st) {
     if (B == 0) return cudaSuccess;
-    const int64_t nblk = (pl.npix + 127) / 128;
-    dim3 grid((unsigned)(nblk < 152 * 4 ? nblk : 152 * 4), B);
+    const int64_t nblk = (pl.npix + AU_THREADS - 1) / AU_THREADS;
+    dim3 grid((unsigned)(nblk < 152 * 8 ? nblk : 152 * 8), B);
     const float* pm = use_linear ? pl.pair_mean : nullptr;
-    if (pl.P <= 4)
-        k_adjoint_u<4><<<grid, 128, 0, st>>>(pl.P, pl.n_pair, pl.npix, hk, pm, pl.W, maps);
-    else if (pl.P <= 8)
-        k_adjoint_u<8><<<grid, 128, 0, st>>>(pl.P, pl.n_pair, pl.npix, hk, pm, pl.W, maps);
-    else
-        k_adjoint_u<16><<<grid, 128, 0, st>>>(pl.P, pl.n_pair, pl.npix, hk, pm, pl.W, maps);
+    k_adjoint_u<<<grid, AU_THREADS, 0, st>>>(pl.P, pl.n_pair, pl.npix, hk, pm, pl.W, maps);
     return cudaGetLastError();
 }
 

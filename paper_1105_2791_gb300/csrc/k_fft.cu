@@ -29,19 +29,19 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 // tw[q] = e^{+2 pi i q / N}.
 template <int SIGN>
 __device__ void stockham_inplace(float2* buf, int N, int log2N, int ntr, const float2* __restrict__ tw) {
-    int Ns = 1;
+    int Ns = 1, log2Ns = 0;
     if (log2N & 1) {
         // radix-2 stage at Ns = 1: no twiddles
-        const int half = N >> 1;
+        const int half = N >> 1, lh = log2N - 1;
         for (int base = 0; base < ntr * half; base += FFT_THREADS * 8) {
             float2 v0[8], v1[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int idx = base + threadIdx.x + u * FFT_THREADS;
                 if (idx < ntr * half) {
-                    const int q = idx / half, jj = idx % half;
-                    v0[u] = buf[q * N + jj];
-                    v1[u] = buf[q * N + jj + half];
+                    const int q = idx >> lh, jj = idx & (half - 1);
+                    v0[u] = buf[(q << log2N) + jj];
+                    v1[u] = buf[(q << log2N) + jj + half];
                 }
             }
             __syncthreads();
@@ -49,31 +49,32 @@ __device__ void stockham_inplace(float2* buf, int N, int log2N, int ntr, const f
             for (int u = 0; u < 8; ++u) {
                 const int idx = base + threadIdx.x + u * FFT_THREADS;
                 if (idx < ntr * half) {
-                    const int q = idx / half, jj = idx % half;
-                    buf[q * N + 2 * jj] = make_float2(v0[u].x + v1[u].x, v0[u].y + v1[u].y);
-                    buf[q * N + 2 * jj + 1] = make_float2(v0[u].x - v1[u].x, v0[u].y - v1[u].y);
+                    const int q = idx >> lh, jj = idx & (half - 1);
+                    buf[(q << log2N) + 2 * jj] = make_float2(v0[u].x + v1[u].x, v0[u].y + v1[u].y);
+                    buf[(q << log2N) + 2 * jj + 1] = make_float2(v0[u].x - v1[u].x, v0[u].y - v1[u].y);
                 }
             }
             __syncthreads();
         }
         Ns = 2;
+        log2Ns = 1;
     }
-    const int quarter = N >> 2;
-    for (; Ns < N; Ns <<= 2) {
-        const int stride = N / (Ns * 4);   // twiddle index step for r * k
+    const int quarter = N >> 2, lq = log2N - 2;
+    for (; Ns < N; Ns <<= 2, log2Ns += 2) {
+        const int lstride = log2N - log2Ns - 2;       // twiddle index step for r * k is 2^lstride
         for (int base = 0; base < ntr * quarter; base += FFT_THREADS * 4) {
             float2 v[4][4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int idx = base + threadIdx.x + u * FFT_THREADS;
                 if (idx < ntr * quarter) {
-                    const int q = idx / quarter, jj = idx % quarter;
-                    const int k = jj % Ns;
+                    const int q = idx >> lq, jj = idx & (quarter - 1);
+                    const int k = jj & (Ns - 1);
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        float2 x = buf[q * N + jj + r * quarter];
+                        float2 x = buf[(q << log2N) + jj + r * quarter];
                         if (r > 0) {
-                            float2 w = __ldg(&tw[(r * k * stride) & (N - 1)]);
+                            float2 w = __ldg(&tw[(r * k) << lstride]);
                             if (SIGN < 0) w.y = -w.y;
                             x = cmul(x, w);
                         }
@@ -86,16 +87,16 @@ __device__ void stockham_inplace(float2* buf, int N, int log2N, int ntr, const f
             for (int u = 0; u < 4; ++u) {
                 const int idx = base + threadIdx.x + u * FFT_THREADS;
                 if (idx < ntr * quarter) {
-                    const int q = idx / quarter, jj = idx % quarter;
-                    const int k = jj % Ns;
-                    const int d = (jj / Ns) * Ns * 4 + k;
+                    const int q = idx >> lq, jj = idx & (quarter - 1);
+                    const int k = jj & (Ns - 1);
+                    const int d = ((jj >> log2Ns) << (log2Ns + 2)) + k;
                     const float2 a0 = make_float2(v[u][0].x + v[u][2].x, v[u][0].y + v[u][2].y);
                     const float2 a1 = make_float2(v[u][0].x - v[u][2].x, v[u][0].y - v[u][2].y);
                     const float2 a2 = make_float2(v[u][1].x + v[u][3].x, v[u][1].y + v[u][3].y);
                     const float2 df = make_float2(v[u][1].x - v[u][3].x, v[u][1].y - v[u][3].y);
                     // a3 = SIGN * i * (v1 - v3)
                     const float2 a3 = (SIGN > 0) ? make_float2(-df.y, df.x) : make_float2(df.y, -df.x);
-                    float2* o = buf + q * N + d;
+                    float2* o = buf + (q << log2N) + d;
                     o[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
                     o[Ns] = make_float2(a1.x + a3.x, a1.y + a3.y);
                     o[2 * Ns] = make_float2(a0.x - a2.x, a0.y - a2.y);

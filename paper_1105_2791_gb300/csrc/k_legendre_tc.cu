@@ -9,12 +9,13 @@
 // Work item = (m, parity, tile of 128 ring pairs, group of 8 maps).  A persistent CTA
 // loops over items.  Per pipeline stage it holds 128 bytes of K per row:
 //   A (lambda, pre-split hi/lo, pre-tiled in HBM): fetched with one cp.async.bulk;
-//   B (filtered a_lm): formed, scaled and split hi/lo in shared memory by 8 warps.
+//   B (filtered a_lm, scaled and split hi/lo): built once per chunk by k_tc_prep_b in
+//      the same layout and shared by all ring tiles; fetched with cp.async.bulk.
 // One thread issues tcgen05.mma: hi*hi into TMEM accumulator D1 (columns 0..N-1) and
-// the cross products hi*lo + lo*hi into D2 (columns N..2N-1).  The tensor core rounds
+// the cross products hi*lo + lo*hi into D2 (columns N..2N-1).  8 further warps  The tensor core rounds
 // its FP32 accumulator once per MMA; keeping the small cross terms apart makes their
 // rounding 2^-11 smaller, so the error of a sum over ~10^3 values of l stays near
-// (K/16) 2^-24 instead of three times that.  The same 8 warps then drain TMEM,
+// (K/16) 2^-24 instead of three times that.  The 8 epilogue warps drain TMEM,
 // form D1 + D2, undo the scaling and write the even (E) or odd (O) row for the ring
 // pairs; the ring FFT forms north = E + O and south = E - O.
 // Operands use the no-swizzle K-major core-matrix layout: element (row r, k) at
@@ -31,7 +32,7 @@
 namespace modal {
 
 constexpr int TC_MAPS = 8;                 // maps per work item (N = 16 P)
-constexpr int TC_PROD_WARPS = 8;           // B producers / epilogue
+constexpr int TC_PROD_WARPS = 8;           // epilogue warps
 constexpr int TC_THREADS = 32 * (2 + TC_PROD_WARPS);
 constexpr int TC_STAGES = 2;
 constexpr int TC_KB = 128;                 // bytes of K per row per stage (8 core matrices)
@@ -252,14 +253,86 @@ __global__ void k_alm_amax(int L, const float* __restrict__ fmax_l, const float2
     if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(&amax[b], __float_as_uint(v));
 }
 
+// ------------------------------------------------------------------ B operand blocks
+// Stage block (g, m, pi, kb) of the filtered a_lm for maps 8g .. 8g+7: [hi tile, lo tile],
+// each N = 16 P rows (b, p, re/im) x 128 bytes of K (KPS values l = m + pi + 2 (kb KPS + k)),
+// the same core-matrix layout the MMA reads.  Built once per chunk and shared by every
+// ring tile.
+struct PrepArgs {
+    int L, P, B, n_groups;
+    int64_t n_alm, total_bkb;      // stage blocks per map group
+    const int64_t* bblk_base;      // [2 (L+1)] first stage block of (m, parity)
+    const float* filt;             // [P][L+1]
+    const float2* alm;             // [B][n_alm]
+    const unsigned* amax;          // [B] float bits
+    char* out;                     // [n_groups][total_bkb][2][N][128 bytes]
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_tc_prep_b(PrepArgs a) {
+    using S = Split<PREC>;
+    using T = typename ElemT<S::E>::T;
+    constexpr int KPS = TC_KB / S::E;
+    constexpr int CM = 16 / S::E;
+    constexpr int NKC = TC_KB / 16;
+    __shared__ float2 s_a[TC_MAPS * 64];
+    __shared__ float s_f[64 * 16];
+    __shared__ float s_scale[TC_MAPS];
+    const int N = 16 * a.P;
+    const int b_tile = N * TC_KB;
+    const int m = blockIdx.y >> 1, pi = blockIdx.y & 1, g = blockIdx.z;
+    const int nkb = tc_nkb(a.L, m, pi, KPS);
+    const int64_t base_m = d_alm_index(m, m, a.L);
+    if (threadIdx.x < TC_MAPS) {
+        const int b = g * TC_MAPS + threadIdx.x;
+        s_scale[threadIdx.x] = (b < a.B) ? exp2f((float)tc_scale_exp(a.amax[b])) : 0.f;
+    }
+    for (int kb = blockIdx.x; kb < nkb; kb += gridDim.x) {
+        const int l0 = m + pi + 2 * kb * KPS;                   // l of K index k: l0 + 2 k
+        __syncthreads();
+        for (int i = threadIdx.x; i < TC_MAPS * KPS; i += blockDim.x) {
+            const int bl = i / KPS, k = i % KPS;
+            const int b = g * TC_MAPS + bl, l = l0 + 2 * k;
+            float2 v = make_float2(0.f, 0.f);
+            if (b < a.B && l <= a.L) {
+                v = a.alm[(int64_t)b * a.n_alm + base_m + (l - m)];
+                v.x *= s_scale[bl];
+                v.y *= s_scale[bl];
+            }
+            s_a[i] = v;
+        }
+        for (int i = threadIdx.x; i < KPS * 16; i += blockDim.x) {
+            const int k = i / 16, p = i % 16, l = l0 + 2 * k;
+            s_f[i] = (p < a.P && l <= a.L) ? a.filt[(int64_t)p * (a.L + 1) + l] : 0.f;
+        }
+        __syncthreads();
+        char* bt = a.out + ((int64_t)g * a.total_bkb + a.bblk_base[2 * m + pi] + kb) * (int64_t)(2 * b_tile);
+        for (int c = threadIdx.x; c < NKC * N; c += blockDim.x) {
+            const int kc = c / N, n = c % N;
+            const int bl = n / (2 * a.P), p = (n / 2) % a.P, comp = n % 2;
+            T hv[CM], lv[CM];
+#pragma unroll
+            for (int i = 0; i < CM; ++i) {
+                const int k = kc * CM + i;
+                const float2 av = s_a[bl * KPS + k];
+                const float x = s_f[k * 16 + p] * (comp ? av.y : av.x);
+                S::split(x, hv[i], lv[i]);
+            }
+            const int off = (n / 8) * TC_SBO + kc * 128 + (n % 8) * 16;
+            *reinterpret_cast<uint4*>(bt + off) = *reinterpret_cast<const uint4*>(hv);
+            *reinterpret_cast<uint4*>(bt + b_tile + off) = *reinterpret_cast<const uint4*>(lv);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ main kernel
 struct TcArgs {
     int L, P, R, R_half, RH, n_rt, B, n_groups;
-    int64_t n_items, n_alm;
+    int64_t n_items, total_bkb;
     const char* table;             // pre-tiled A blocks
-    const int64_t* blk_base;       // [2 (L+1)] first block of (m, parity)
-    const float* filt;             // [P][L+1]
-    const float2* alm;             // [B][n_alm]
+    const int64_t* blk_base;       // [2 (L+1)] first A block of (m, parity)
+    const char* bops;              // B stage blocks (k_tc_prep_b)
+    const int64_t* bblk_base;      // [2 (L+1)] first B block of (m, parity)
     const unsigned* amax;          // [B] float bits
     float2* delta;                 // [B][P][L+1][2][RH]: E and O rows per ring pair
     int* err;
@@ -278,20 +351,17 @@ __device__ __forceinline__ void tc_item(const TcArgs& a, int64_t item, int& m, i
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
     using S = Split<PREC>;
-    using T = typename ElemT<S::E>::T;
     constexpr bool TF32 = (PREC == MODAL_3XTF32);
     constexpr int KPS = TC_KB / S::E;     // K values per stage
-    constexpr int CM = 16 / S::E;         // K values per core matrix
     constexpr int NKC = TC_KB / 16;       // core matrices along K per stage (8)
     const int N = 16 * a.P;               // 2 (re, im) x P x 8 maps
     const int b_tile = N * TC_KB;         // bytes of one B tile
+    const uint32_t stage_tx = TC_A_STAGE + 2 * b_tile;
 
     extern __shared__ __align__(1024) char smem[];
     char* sA = smem;                                        // [TC_STAGES][hi, lo]
     char* sB = sA + TC_STAGES * TC_A_STAGE;                 // [TC_STAGES][hi, lo][b_tile]
-    float2* s_a = reinterpret_cast<float2*>(sB + TC_STAGES * 2 * 256 * TC_KB);   // [8][KPS]
-    float* s_f = reinterpret_cast<float*>(s_a + TC_MAPS * 64);                   // [KPS][16]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(s_f + 64 * 16);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TC_STAGES * 2 * 256 * TC_KB);
     uint64_t* full = bars;                                  // [TC_STAGES]
     uint64_t* empty = bars + TC_STAGES;                     // [TC_STAGES]
     uint64_t* tmem_full = bars + 2 * TC_STAGES;
@@ -304,7 +374,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(&full[s], 1 + TC_PROD_WARPS);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(tmem_full, 1);
@@ -323,7 +393,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ---------------- A loader (one thread)
+        // ---------------- loader (one thread): A and B stage blocks by cp.async.bulk
         if (lane == 0) {
             uint32_t it = 0;
             uint32_t last_phase[TC_STAGES] = {0, 0};
@@ -332,13 +402,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
                 int m, pi, rt, g;
                 tc_item(a, item, m, pi, rt, g);
                 const int nkb = tc_nkb(a.L, m, pi, KPS);
-                const char* src = a.table + (a.blk_base[2 * m + pi] + (int64_t)rt * nkb) * TC_A_STAGE;
+                const char* srcA = a.table + (a.blk_base[2 * m + pi] + (int64_t)rt * nkb) * TC_A_STAGE;
+                const char* srcB = a.bops + ((int64_t)g * a.total_bkb + a.bblk_base[2 * m + pi]) * (int64_t)(2 * b_tile);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % TC_STAGES;
                     const uint32_t ph = (it / TC_STAGES) & 1;
                     if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err)) break;
-                    mbar_arrive_expect_tx(&full[s], TC_A_STAGE);
-                    bulk_copy_g2s(sA + s * TC_A_STAGE, src + (int64_t)kb * TC_A_STAGE, TC_A_STAGE, &full[s]);
+                    mbar_arrive_expect_tx(&full[s], stage_tx);
+                    bulk_copy_g2s(sA + s * TC_A_STAGE, srcA + (int64_t)kb * TC_A_STAGE, TC_A_STAGE, &full[s]);
+                    bulk_copy_g2s(sB + s * 2 * b_tile, srcB + (int64_t)kb * 2 * b_tile, 2 * b_tile, &full[s]);
                     last_phase[s] = ph;
                     issued[s] = true;
                 }
@@ -390,104 +462,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
             }
         }
     } else {
-        // ---------------- B producers + epilogue (TC_PROD_WARPS warps)
-        // These warps meet at named barrier 1 a data-independent number of times; after an
-        // abort they keep looping (skipping all work) so that no warp waits there alone.
-        const int pt = threadIdx.x - 64;                    // 0 .. 255
+        // ---------------- epilogue (TC_PROD_WARPS warps): TMEM -> D1 + D2 -> E or O row
+        // Columns are ordered (map bl, basis p, re/im); column pair cp = bl P + p maps to
+        // the delta row (8 g P + cp) (L+1) 2 RH + (2 m + pi) RH, so addresses advance by a
+        // fixed stride per column pair.
         const int quarter = warp % 4;                       // TMEM lanes 32 quarter .. + 31
-        const int half = (warp - 2) / 4;                    // column half for the epilogue
+        const int half = (warp - 2) / 4;                    // column half
         const int nblk = a.P;                               // 16-column blocks (N = 16 P)
         const int blk_lo = half ? (nblk + 1) / 2 : 0, blk_hi = half ? nblk : (nblk + 1) / 2;
-        uint32_t it = 0, nitem = 0;
+        const int64_t row_stride = (int64_t)(a.L + 1) * 2 * a.RH;
+        const float lam_inv = (S::E == 2) ? (1.f / TC_LAMBDA_SCALE) : 1.f;
+        uint32_t nitem = 0;
         for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x, ++nitem) {
             int m, pi, rt, g;
             tc_item(a, item, m, pi, rt, g);
-            const int nkb = tc_nkb(a.L, m, pi, KPS);
-            const int64_t base_m = d_alm_index(m, m, a.L);
-            for (int kb = 0; kb < nkb; ++kb, ++it) {
-                const int s = it % TC_STAGES;
-                const uint32_t ph = (it / TC_STAGES) & 1;
-                const int l0 = m + pi + 2 * kb * KPS;              // l of K index k: l0 + 2 k
-                // stage a (8 maps x KPS values of l, scaled per map) and f (KPS x P)
-                named_sync(1, 32 * TC_PROD_WARPS);
-                for (int i = pt; i < TC_MAPS * KPS; i += 32 * TC_PROD_WARPS) {
-                    const int bl = i / KPS, k = i % KPS;
-                    const int b = g * TC_MAPS + bl, l = l0 + 2 * k;
-                    float2 v = make_float2(0.f, 0.f);
-                    if (b < a.B && l <= a.L) {
-                        v = a.alm[(int64_t)b * a.n_alm + base_m + (l - m)];
-                        const float sc = exp2f((float)tc_scale_exp(a.amax[b]));
-                        v.x *= sc;
-                        v.y *= sc;
-                    }
-                    s_a[i] = v;
-                }
-                for (int i = pt; i < KPS * 16; i += 32 * TC_PROD_WARPS) {
-                    const int k = i / 16, p = i % 16, l = l0 + 2 * k;
-                    s_f[i] = (p < a.P && l <= a.L) ? a.filt[(int64_t)p * (a.L + 1) + l] : 0.f;
-                }
-                named_sync(1, 32 * TC_PROD_WARPS);
-                const bool ok = !*abort_flag && mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err);
-                if (ok) {
-                    char* bt = sB + s * 2 * b_tile;
-                    // chunks: (core-matrix column kc, row n); 16 bytes of K per chunk
-                    const int nchunks = NKC * N;
-                    for (int c = pt; c < nchunks; c += 32 * TC_PROD_WARPS) {
-                        const int kc = c / N, n = c % N;
-                        const int bl = n / (2 * a.P), p = (n / 2) % a.P, comp = n % 2;
-                        T hv[CM], lv[CM];
-#pragma unroll
-                        for (int i = 0; i < CM; ++i) {
-                            const int k = kc * CM + i;
-                            const float2 av = s_a[bl * KPS + k];
-                            const float x = s_f[k * 16 + p] * (comp ? av.y : av.x);
-                            S::split(x, hv[i], lv[i]);
-                        }
-                        const int off = (n / 8) * TC_SBO + kc * 128 + (n % 8) * 16;
-                        *reinterpret_cast<uint4*>(bt + off) = *reinterpret_cast<const uint4*>(hv);
-                        *reinterpret_cast<uint4*>(bt + b_tile + off) = *reinterpret_cast<const uint4*>(lv);
-                    }
-                    fence_proxy_async();
-                }
-                __syncwarp();
-                if (ok && lane == 0) mbar_arrive(&full[s]);
-            }
-            // ---------------- epilogue: TMEM -> D1 + D2 -> E or O row of delta
+            // per-map unscale factors of this map group (lane bl holds map 8 g + bl)
+            float inv_lane = 0.f;
+            if (lane < TC_MAPS && g * TC_MAPS + lane < a.B)
+                inv_lane = exp2f((float)-tc_scale_exp(a.amax[g * TC_MAPS + lane])) * lam_inv;
             bool ok = !*abort_flag && mbar_wait(tmem_full, nitem & 1, abort_flag, a.err);
             ok = __all_sync(0xffffffffu, ok);
-            if (ok) {
-                tc_fence_after();
-                const int jn = rt * 128 + quarter * 32 + lane;   // TMEM lane = ring pair within the tile
-                const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-                for (int blk = blk_lo; blk < blk_hi; ++blk) {
-                    const int c0 = blk * 16;
-                    float d[16], d2[16];
-                    tmem_ld16(lane_addr + c0, d);
-                    if (S::PRODUCTS == 3) {
-                        tmem_ld16(lane_addr + N + c0, d2);
+            if (!ok) break;
+            tc_fence_after();
+            const int jn = rt * 128 + quarter * 32 + lane;   // TMEM lane = ring pair within the tile
+            const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+            const int cp_valid = (a.B - g * TC_MAPS) * a.P;   // column pairs that belong to real maps
+            float2* base = a.delta + ((int64_t)g * TC_MAPS * a.P) * row_stride + (int64_t)(2 * m + pi) * a.RH + jn;
+            for (int blk = blk_lo; blk < blk_hi; ++blk) {
+                const int c0 = blk * 16;
+                float d[16], d2[16];
+                tmem_ld16(lane_addr + c0, d);
+                if (S::PRODUCTS == 3) {
+                    tmem_ld16(lane_addr + N + c0, d2);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) d[i] += d2[i];
-                    }
-                    if (jn < a.R_half) {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int n = c0 + 2 * q;             // even column: re, odd: im
-                            const int bl = n / (2 * a.P), p = (n / 2) % a.P;
-                            const int b = g * TC_MAPS + bl;
-                            if (b < a.B) {
-                                // undo the per-map 2^k on a and 2^11 on lambda (16-bit formats)
-                                const float inv = exp2f((float)-tc_scale_exp(a.amax[b])) *
-                                                  ((S::E == 2) ? (1.f / TC_LAMBDA_SCALE) : 1.f);
-                                const int64_t row = (((int64_t)(b * a.P + p) * (a.L + 1) + m) * 2 + pi) * a.RH;
-                                a.delta[row + jn] = make_float2(d[2 * q] * inv, d[2 * q + 1] * inv);
-                            }
-                        }
-                    }
+                    for (int i = 0; i < 16; ++i) d[i] += d2[i];
                 }
-                tc_fence_before();
+                const int cp0 = blk * 8;
+                int bl = cp0 / a.P, p = cp0 - bl * a.P;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float inv = __shfl_sync(0xffffffffu, inv_lane, bl);
+                    if (jn < a.R_half && cp0 + q < cp_valid)
+                        base[(int64_t)(cp0 + q) * row_stride] = make_float2(d[2 * q] * inv, d[2 * q + 1] * inv);
+                    if (++p == a.P) { p = 0; ++bl; }
+                }
             }
+            tc_fence_before();
             __syncwarp();
-            if (ok && lane == 0) mbar_arrive(tmem_empty);
+            if (lane == 0) mbar_arrive(tmem_empty);
         }
     }
     tc_fence_before();
@@ -499,36 +521,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
 }
 
 static size_t tc_smem_bytes() {
-    return 1024 /*alignment slack*/ + TC_STAGES * TC_A_STAGE + TC_STAGES * 2 * 256 * TC_KB + TC_MAPS * 64 * 8 +
-           64 * 16 * 4 + 8 * (2 * TC_STAGES + 2) + 16;
+    return 1024 /*alignment slack*/ + TC_STAGES * TC_A_STAGE + TC_STAGES * 2 * 256 * TC_KB +
+           8 * (2 * TC_STAGES + 2) + 16;
 }
 
 // ------------------------------------------------------------------ host side
 static int kps_for(int prec) { return prec == MODAL_3XTF32 ? TC_KB / 4 : TC_KB / 2; }
+
+size_t tc_b_workspace_bytes(const Plan& pl, int chunk) {
+    if (pl.prec == MODAL_FP32) return 0;
+    const int KPS = kps_for(pl.prec);
+    int64_t total = 0;
+    for (int m = 0; m <= pl.lmax; ++m)
+        for (int pi = 0; pi < 2; ++pi) total += tc_nkb(pl.lmax, m, pi, KPS);
+    const int groups = (chunk + TC_MAPS - 1) / TC_MAPS;
+    return (size_t)groups * total * 2 * (16 * pl.P) * TC_KB;
+}
 
 cudaError_t build_tc_tables(Plan& pl, cudaStream_t st) {
     const int L = pl.lmax;
     const int KPS = kps_for(pl.prec);
     pl.tc.n_rt = (pl.R_half + 127) / 128;
     pl.tc.kb_off.assign(2 * (L + 1), 0);
-    int64_t total = 0;
+    std::vector<int64_t> bb(2 * (L + 1), 0);
+    int64_t total = 0, btotal = 0;
     for (int m = 0; m <= L; ++m)
         for (int pi = 0; pi < 2; ++pi) {
             pl.tc.kb_off[2 * m + pi] = total;
-            total += (int64_t)pl.tc.n_rt * tc_nkb(L, m, pi, KPS);
+            bb[2 * m + pi] = btotal;
+            const int nkb = tc_nkb(L, m, pi, KPS);
+            total += (int64_t)pl.tc.n_rt * nkb;
+            btotal += nkb;
         }
     pl.tc.n_kb = total;
+    pl.tc.total_bkb = btotal;
     pl.tc.bytes = (size_t)total * TC_A_STAGE;
     cudaError_t e = cudaMalloc(&pl.tc.hi, pl.tc.bytes);
     if (e != cudaSuccess) return e;
     e = cudaMalloc(&pl.tc.d_kb_off, 2 * (L + 1) * sizeof(int64_t));
     if (e != cudaSuccess) return e;
+    e = cudaMalloc(&pl.tc.d_bkb_off, 2 * (L + 1) * sizeof(int64_t));
+    if (e != cudaSuccess) return e;
     e = cudaMalloc(&pl.tc.d_amax, 4096 * sizeof(unsigned));
     if (e != cudaSuccess) return e;
     e = cudaMalloc(&pl.tc.d_fmax, (L + 1) * sizeof(float));
     if (e != cudaSuccess) return e;
-    pl.device_bytes += pl.tc.bytes + (L + 1) * (2 * sizeof(int64_t) + sizeof(float)) + 4096 * sizeof(unsigned);
+    pl.device_bytes += pl.tc.bytes + (L + 1) * (4 * sizeof(int64_t) + sizeof(float)) + 4096 * sizeof(unsigned);
     e = cudaMemcpy(pl.tc.d_kb_off, pl.tc.kb_off.data(), 2 * (L + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(pl.tc.d_bkb_off, bb.data(), 2 * (L + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
     {
         std::vector<float> fm(L + 1, 0.f);
@@ -565,13 +606,21 @@ cudaError_t build_tc_tables(Plan& pl, cudaStream_t st) {
 void free_tc_tables(Plan& pl) {
     if (pl.tc.hi) cudaFree(pl.tc.hi);
     if (pl.tc.d_kb_off) cudaFree(pl.tc.d_kb_off);
+    if (pl.tc.d_bkb_off) cudaFree(pl.tc.d_bkb_off);
     if (pl.tc.d_amax) cudaFree(pl.tc.d_amax);
     if (pl.tc.d_fmax) cudaFree(pl.tc.d_fmax);
     pl.tc = TcTable();
 }
 
 template <int PREC>
-static cudaError_t launch_tc(const Plan& pl, const TcArgs& args, cudaStream_t st) {
+static cudaError_t launch_tc(const Plan& pl, const PrepArgs& pa, const TcArgs& args, cudaStream_t st) {
+    {
+        const int maxkb = tc_nkb(pl.lmax, 0, 0, kps_for(pl.prec));
+        dim3 grid(std::min(maxkb, 8), 2 * (pl.lmax + 1), pa.n_groups);
+        k_tc_prep_b<PREC><<<grid, 256, 0, st>>>(pa);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const size_t smem = tc_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_legendre_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -584,7 +633,7 @@ static cudaError_t launch_tc(const Plan& pl, const TcArgs& args, cudaStream_t st
 
 cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
-    if (B > 4096) return cudaErrorInvalidValue;
+    if (B > 4096 || B > pl.chunk) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(pl.tc.d_amax, 0, B * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     {
@@ -593,6 +642,18 @@ cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2*
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    PrepArgs pa;
+    pa.L = pl.lmax;
+    pa.P = pl.P;
+    pa.B = B;
+    pa.n_groups = (B + TC_MAPS - 1) / TC_MAPS;
+    pa.n_alm = pl.n_alm;
+    pa.total_bkb = pl.tc.total_bkb;
+    pa.bblk_base = pl.tc.d_bkb_off;
+    pa.filt = pl.filt;
+    pa.alm = alm;
+    pa.amax = pl.tc.d_amax;
+    pa.out = static_cast<char*>(pl.tc.bops);
     TcArgs a;
     a.L = pl.lmax;
     a.P = pl.P;
@@ -601,21 +662,21 @@ cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2*
     a.RH = pl.RH;
     a.n_rt = pl.tc.n_rt;
     a.B = B;
-    a.n_groups = (B + TC_MAPS - 1) / TC_MAPS;
+    a.n_groups = pa.n_groups;
     a.n_items = (int64_t)(pl.lmax + 1) * 2 * a.n_rt * a.n_groups;
-    a.n_alm = pl.n_alm;
+    a.total_bkb = pl.tc.total_bkb;
     a.table = static_cast<const char*>(pl.tc.hi);
     a.blk_base = pl.tc.d_kb_off;
-    a.filt = pl.filt;
-    a.alm = alm;
+    a.bops = static_cast<const char*>(pl.tc.bops);
+    a.bblk_base = pl.tc.d_bkb_off;
     a.amax = pl.tc.d_amax;
     a.delta = delta;
     a.err = pl.d_err;
     switch (pl.prec) {
-        case MODAL_FP16X3: return launch_tc<MODAL_FP16X3>(pl, a, st);
-        case MODAL_BF16X3: return launch_tc<MODAL_BF16X3>(pl, a, st);
-        case MODAL_BF16: return launch_tc<MODAL_BF16>(pl, a, st);
-        case MODAL_3XTF32: return launch_tc<MODAL_3XTF32>(pl, a, st);
+        case MODAL_FP16X3: return launch_tc<MODAL_FP16X3>(pl, pa, a, st);
+        case MODAL_BF16X3: return launch_tc<MODAL_BF16X3>(pl, pa, a, st);
+        case MODAL_BF16: return launch_tc<MODAL_BF16>(pl, pa, a, st);
+        case MODAL_3XTF32: return launch_tc<MODAL_3XTF32>(pl, pa, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -70,10 +70,11 @@ __global__ void __launch_bounds__(1024) k_cholesky(int n, double* __restrict__ A
             col[i] = v;
         }
         __syncthreads();
-        const int m = n - k - 1;
-        for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
-            const int i = k + 1 + (int)(t / m), j = k + 1 + (int)(t % m);
-            if (j <= i) A[(int64_t)i * n + j] -= col[i] * col[j];
+        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+        for (int i = k + 1 + ty; i < n; i += 32) {
+            const double ci = col[i];
+            double* row = A + (int64_t)i * n;
+            for (int j = k + 1 + tx; j <= i; j += 32) row[j] -= ci * col[j];
         }
         __syncthreads();
     }

@@ -153,7 +153,7 @@ static size_t per_map_workspace(const modal_plan* pl) {
     const size_t delta = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
     const size_t maps = (size_t)pl->P * pl->npix * sizeof(float);
     const size_t ut = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
-    return delta + maps + ut;
+    return delta + maps + ut + tc_b_workspace_bytes(*pl, 8) / 8;
 }
 
 static void free_workspace(modal_plan* pl) {
@@ -164,6 +164,7 @@ static void free_workspace(modal_plan* pl) {
     dfree(pl->ut); pl->ut = nullptr;
     dfree(pl->partial); pl->partial = nullptr;
     dfree(pl->hk); pl->hk = nullptr;
+    dfree(pl->tc.bops); pl->tc.bops = nullptr;
     pl->device_bytes -= pl->workspace_bytes;
     pl->workspace_bytes = 0;
 }
@@ -182,6 +183,12 @@ static modal_status alloc_workspace(modal_plan* pl, int chunk) {
     const size_t lin = (size_t)pl->lin_ksplit * pl->n_pair * chunk * pl->P;
     pl->partial_elems = cub + lin;
     CK(dalloc(pl, &pl->partial, pl->partial_elems), "workspace partial");
+    {
+        const size_t bb = tc_b_workspace_bytes(*pl, chunk);
+        char* p = nullptr;
+        CK(dalloc(pl, &p, bb), "workspace tensor-core operands");
+        pl->tc.bops = p;
+    }
     pl->workspace_bytes = pl->device_bytes - before;
     return MODAL_OK;
 }

@@ -35,7 +35,10 @@ struct TcTable {
     int n_rt = 0;                       // ring tiles of TC_BM ring pairs
     std::vector<int64_t> kb_off;        // per (m, parity): first K block index (prefix sums)
     int64_t n_kb = 0;                   // total K blocks over all (m, parity)
-    int64_t* d_kb_off = nullptr;        // device copy of kb_off ([lmax+1])
+    int64_t* d_kb_off = nullptr;        // device copy of kb_off ([2 (lmax+1)])
+    int64_t* d_bkb_off = nullptr;       // first B stage block of (m, parity) ([2 (lmax+1)])
+    int64_t total_bkb = 0;              // B stage blocks per group of 8 maps
+    void* bops = nullptr;               // B stage blocks of the current chunk (workspace)
     unsigned* d_amax = nullptr;         // per-map scale bounds (float bits), [4096]
     float* d_fmax = nullptr;            // max_p |f_p(l)|, [lmax+1]
     size_t bytes = 0;
@@ -110,6 +113,7 @@ modal_status cuda_check(cudaError_t e, const char* what);
 cudaError_t launch_lambda_table(const Plan& pl, const double* d_mu_north, const double* d_log2c,
                                 const double* d_a, const double* d_b, cudaStream_t st);
 cudaError_t build_tc_tables(Plan& pl, cudaStream_t st);      // allocates pl.tc
+size_t tc_b_workspace_bytes(const Plan& pl, int chunk);
 void free_tc_tables(Plan& pl);
 // k_legendre_simt.cu
 cudaError_t launch_legendre_simt(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st);
