@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the plain FP32 comparison and CPU baseline")
     ap.add_argument("--cpu-rings", type=int, default=8, help="rings in the CPU-baseline sample")
     ap.add_argument("--lmax", type=int, default=2000, help="smaller l_max for profiler captures only")
+    ap.add_argument("--chunk", type=int, default=32, help="maps per internal pass of the library")
     return ap.parse_args()
 
 
@@ -111,6 +112,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- multi-rank timing
+def max_over_ranks(ms, device=None):
+    """Slowest rank's timed-region length (ms); identity on one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(maps_per_rank_per_step, steps, world, ms_max):
+    """Whole-job maps/s: every rank's maps over the slowest rank's time (weak scaling)."""
+    return maps_per_rank_per_step * steps * world / (ms_max / 1e3)
+
+
 # ---------------------------------------------------------------- GPU arm
 def legendre_flops(P, lmax, nrings):
     """Algorithmic flops of the Legendre sums per map: each (l, m, ring pair) contributes
@@ -152,6 +170,7 @@ def run_gpu(args):
             if "not supported" in str(e):
                 return None
             raise
+        plan.set_chunk(min(args.chunk, B))
         plan.linear_term(lin_sims, finalize=True)      # a mean to subtract from the first step on
         return plan
 
@@ -207,10 +226,7 @@ def run_gpu(args):
         ms = ev0.elapsed_time(ev1)
         prof = M.modal_get_profile(pl.h)
         M.modal_set_profiling(pl.h, False)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         return ms, prof
 
     K, W = args.steps, args.warmup
@@ -224,8 +240,8 @@ def run_gpu(args):
     a_e2e = torch.empty_like(alm)
     e2e_ms, _ = timed(plan, a_e2e, K, 1, e2e=True)
 
-    value = B * K * world / (ms / 1e3)
-    e2e_value = B * K * world / (e2e_ms / 1e3)
+    value = job_throughput(B, K, world, ms)
+    e2e_value = job_throughput(B, K, world, e2e_ms)
     leg_ms, leg_n = prof["legendre"]
     n_prof_steps = max(1, K // 2)
     flops = legendre_flops(P, L, R) * B * n_prof_steps * 3     # three syntheses per map per step

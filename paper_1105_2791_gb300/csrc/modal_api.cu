@@ -153,7 +153,7 @@ static size_t per_map_workspace(const modal_plan* pl) {
     const size_t delta = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
     const size_t maps = (size_t)pl->P * pl->npix * sizeof(float);
     const size_t ut = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
-    return delta + maps + ut + tc_b_workspace_bytes(*pl, 8) / 8;
+    return delta + maps + ut + tc_b_workspace_bytes(*pl, 8) / 8 + tc_adj_workspace_bytes(*pl, 8) / 8;
 }
 
 static void free_workspace(modal_plan* pl) {
@@ -165,6 +165,7 @@ static void free_workspace(modal_plan* pl) {
     dfree(pl->partial); pl->partial = nullptr;
     dfree(pl->hk); pl->hk = nullptr;
     dfree(pl->tc.bops); pl->tc.bops = nullptr;
+    dfree(pl->tca.bops); pl->tca.bops = nullptr;
     pl->device_bytes -= pl->workspace_bytes;
     pl->workspace_bytes = 0;
 }
@@ -188,6 +189,9 @@ static modal_status alloc_workspace(modal_plan* pl, int chunk) {
         char* p = nullptr;
         CK(dalloc(pl, &p, bb), "workspace tensor-core operands");
         pl->tc.bops = p;
+        char* q = nullptr;
+        CK(dalloc(pl, &q, tc_adj_workspace_bytes(*pl, chunk)), "workspace tensor-core adjoint operands");
+        pl->tca.bops = q;
     }
     pl->workspace_bytes = pl->device_bytes - before;
     return MODAL_OK;
@@ -212,6 +216,7 @@ static void destroy_plan(modal_plan* pl) {
     dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->S1); dfree(pl->S2);
     dfree(pl->solve_ws); dfree(pl->d_err);
     free_tc_tables(*pl);
+    free_tc_adj_tables(*pl);
     for (auto& pe : pl->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
     for (auto e : pl->prof_pool) cudaEventDestroy(e);
     delete pl;
@@ -411,6 +416,7 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
     }
     // tensor-core tables
     if (prec != MODAL_FP32) CKI(build_tc_tables(*pl, 0), "tensor-core tables");
+    if (prec != MODAL_FP32) CKI(build_tc_adj_tables(*pl, 0), "tensor-core adjoint tables");
     // workspace: as many maps per pass as fit a 24 GB budget (at least 1, at most 64)
     {
         const size_t per = per_map_workspace(pl);
@@ -575,7 +581,13 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
         { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_weights(*h, g + (size_t)b0 * h->n_max, nb, h->hk, st), "adjoint weights"); }
         { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear, h->maps, st), "adjoint pixel"); }
         { STAGE(h, ST_R2C, st); CK(launch_ring_r2c(*h, h->maps, nb * h->P, nullptr, h->ut, st), "adjoint r2c"); }
-        { STAGE(h, ST_LEGENDRE_ADJ, st); CK(launch_legendre_adjoint_simt(*h, h->ut, nb, h->filt, h->P, out + (size_t)b0 * h->n_alm, st), "adjoint legendre"); }
+        {
+            STAGE(h, ST_LEGENDRE_ADJ, st);
+            if (h->prec == MODAL_FP32)
+                CK(launch_legendre_adjoint_simt(*h, h->ut, nb, h->filt, h->P, out + (size_t)b0 * h->n_alm, st), "adjoint legendre");
+            else
+                CK(launch_legendre_adjoint_tc(*h, h->ut, nb, out + (size_t)b0 * h->n_alm, st), "adjoint legendre");
+        }
     }
     return MODAL_OK;
 }

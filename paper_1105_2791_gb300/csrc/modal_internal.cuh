@@ -44,6 +44,17 @@ struct TcTable {
     size_t bytes = 0;
 };
 
+// Transposed pre-split Legendre table and operand workspace of the tensor-core adjoint.
+struct TcAdjTable {
+    void* table = nullptr;              // blocks (m, parity, l tile, ring-pair block): [hi][lo]
+    int64_t* d_blk_base = nullptr;      // [2 (lmax+1)] first block of (m, parity)
+    int64_t* d_item_base = nullptr;     // [2 (lmax+1) + 1] prefix sums of l tiles
+    int64_t n_lt_total = 0;             // l tiles over all (m, parity)
+    int nkb = 0;                        // ring-pair blocks per l tile
+    void* bops = nullptr;               // U operand blocks of the current chunk (workspace)
+    size_t bytes = 0;
+};
+
 struct Plan {
     int lmax = 0, P = 0, nrings = 0, nphi = 0, prec = 0, dev = 0;
     int R_half = 0;          // ring pairs (north rings incl. the equator)
@@ -66,6 +77,7 @@ struct Plan {
     int n_tiles = 0, n_pg = 0, n_sq = 0;
     int* pair_ab = nullptr;      // colex pair c -> (p | r << 8), padded entries = -1
     TcTable tc;
+    TcAdjTable tca;
 
     // Monte Carlo accumulators
     double* pair_sum = nullptr;  // [n_pair][npix]
@@ -114,6 +126,11 @@ cudaError_t launch_lambda_table(const Plan& pl, const double* d_mu_north, const 
                                 const double* d_a, const double* d_b, cudaStream_t st);
 cudaError_t build_tc_tables(Plan& pl, cudaStream_t st);      // allocates pl.tc
 size_t tc_b_workspace_bytes(const Plan& pl, int chunk);
+// k_legendre_tc_adj.cu
+cudaError_t build_tc_adj_tables(Plan& pl, cudaStream_t st);
+void free_tc_adj_tables(Plan& pl);
+size_t tc_adj_workspace_bytes(const Plan& pl, int chunk);
+cudaError_t launch_legendre_adjoint_tc(const Plan& pl, const float2* ut, int B, float2* grad, cudaStream_t st);
 void free_tc_tables(Plan& pl);
 // k_legendre_simt.cu
 cudaError_t launch_legendre_simt(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st);

@@ -320,3 +320,45 @@ def test_reported_precisions(prec, bound):
             for b in range(2)]
     print("%s beta rel err: %s" % (prec, errs))
     assert max(errs) <= bound
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_backward_parity_16_modes(prec):
+    M = _cuda_or_skip()
+    L, P, R, nphi = 70, 16, 71, 256
+    basis, cl, alm = _case(L, P, 3, seed=73)
+    mask = simgen.band_mask(R, 20.0)
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec, ring_mask=mask)
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    g = np.random.default_rng(74).standard_normal((3, plan.n_max))
+    grad = plan.backward(torch.from_numpy(alm).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
+    plan.close()
+    for b in range(3):
+        ref = om.adjoint_grad(alm[b].astype(np.complex128), g[b], L, filt, mu, w, nphi, mask, None)
+        err = _rel(grad[b], ref)
+        print("adjoint lmax=70 P=16 %s map %d: grad rel err %.3g" % (prec, b, err))
+        assert err <= 1e-5
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_backward_full_size_l2000_sampled_rings(prec):
+    """l_max = 2000, 16 modes: with the ring mask keeping 5 rings, U vanishes elsewhere, so
+    the oracle's adjoint over those rings alone is the exact reference."""
+    M = _cuda_or_skip()
+    L, P, R, nphi = 2000, 16, 2001, 4096
+    basis, cl, alm = _case(L, P, 2, seed=2001)
+    rings = np.array([0, 3, 517, 1000, 1998])
+    mask = np.zeros(R)
+    mask[rings] = 1.0
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec, ring_mask=mask)
+    g = np.random.default_rng(2002).standard_normal((2, plan.n_max))
+    grad = plan.backward(torch.from_numpy(alm).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
+    plan.close()
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    for b in range(2):
+        ref = om.adjoint_grad(alm[b].astype(np.complex128), g[b], L, filt, mu[rings], w[rings], nphi, None, None)
+        err = _rel(grad[b], ref)
+        print("adjoint lmax=2000 %s map %d: grad rel err %.3g" % (prec, b, err))
+        assert err <= 1e-5
