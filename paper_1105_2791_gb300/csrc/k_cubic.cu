@@ -8,6 +8,8 @@
 //   adjoint   U_t(x) = 3 W_x sum_{a,b} h_tab (M_a M_b - <M_a M_b>_x)
 #include "modal_internal.cuh"
 
+#include <algorithm>
+
 namespace modal {
 
 // ---------------------------------------------------------------- cubic term
@@ -303,24 +305,30 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
 }
 
 // In place: maps[b][t][x] <- U_t(x) = W_x sum_c hk[b][t][c] (M_a M_b' - <c>_x).
-// One thread per pixel; its P map values sit in a shared-memory column; pairs are
-// taken 8 at a time so that each row of hk is read as two float4 per 8 pairs
-// (4 FMAs per shared load).
-constexpr int AU_THREADS = 256;
+// A block handles AU_MB maps for a range of pixels, so the pair-mean panel <c>_x is
+// read once per AU_MB maps.  One thread per pixel; the maps' values sit in a
+// shared-memory column; pairs are taken 8 at a time and each weight row is read as
+// two float4 (4 FMAs per shared load).
+constexpr int AU_THREADS = 128;
+constexpr int AU_MB = 4;
+constexpr int AU_SC = 136;                  // pairs padded to a multiple of 8 (P <= 16)
 
 __global__ void __launch_bounds__(AU_THREADS)
-k_adjoint_u(int P, int n_pair, int64_t npix, const float* __restrict__ hk, const float* __restrict__ pm,
+k_adjoint_u(int P, int n_pair, int B, int64_t npix, const float* __restrict__ hk, const float* __restrict__ pm,
             const float* __restrict__ W, float* __restrict__ maps) {
-    constexpr int SC = 136;                           // pairs padded to a multiple of 8 (P <= 16)
-    __shared__ __align__(16) float sH[MODAL_MAXP * SC];
-    __shared__ int s_pa[SC], s_pb[SC];
-    __shared__ float sM[MODAL_MAXP][AU_THREADS];
-    const int b = blockIdx.y, tid = threadIdx.x;
-    for (int i = tid; i < MODAL_MAXP * SC; i += AU_THREADS) {
-        const int t = i / SC, c = i % SC;
-        sH[i] = (t < P && c < n_pair) ? hk[((int64_t)b * P + t) * n_pair + c] : 0.f;
+    extern __shared__ __align__(16) float au_smem[];
+    float* sH = au_smem;                                     // [AU_MB][MAXP][AU_SC]
+    float* sM = sH + AU_MB * MODAL_MAXP * AU_SC;            // [AU_MB][MAXP][AU_THREADS]
+    __shared__ int s_pa[AU_SC], s_pb[AU_SC];
+    const int tid = threadIdx.x;
+    const int b0 = blockIdx.y * AU_MB;
+    const int nb = min(AU_MB, B - b0);
+    for (int i = tid; i < AU_MB * MODAL_MAXP * AU_SC; i += AU_THREADS) {
+        const int mb = i / (MODAL_MAXP * AU_SC), rem = i % (MODAL_MAXP * AU_SC);
+        const int t = rem / AU_SC, c = rem % AU_SC;
+        sH[i] = (mb < nb && t < P && c < n_pair) ? hk[((int64_t)(b0 + mb) * P + t) * n_pair + c] : 0.f;
     }
-    for (int c = tid; c < SC; c += AU_THREADS) {
+    for (int c = tid; c < AU_SC; c += AU_THREADS) {
         int pa = 0, pb = 0;
         if (c < n_pair) {
             int cc = c;
@@ -330,46 +338,60 @@ k_adjoint_u(int P, int n_pair, int64_t npix, const float* __restrict__ hk, const
         s_pa[c] = pa;
         s_pb[c] = pb;
     }
+    for (int i = tid; i < AU_MB * MODAL_MAXP * AU_THREADS; i += AU_THREADS) sM[i] = 0.f;
     __syncthreads();
-    float* mb = maps + (int64_t)b * P * npix;
     const float4* H4 = reinterpret_cast<const float4*>(sH);
     for (int64_t x0 = (int64_t)blockIdx.x * AU_THREADS; x0 < npix; x0 += (int64_t)gridDim.x * AU_THREADS) {
         const int64_t x = x0 + tid;
         const bool in = x < npix;
-        for (int p = 0; p < P; ++p) sM[p][tid] = in ? mb[(int64_t)p * npix + x] : 0.f;
-        float u[MODAL_MAXP];
+        for (int mb = 0; mb < nb; ++mb)
+            for (int p = 0; p < P; ++p)
+                sM[(mb * MODAL_MAXP + p) * AU_THREADS + tid] = in ? maps[((int64_t)(b0 + mb) * P + p) * npix + x] : 0.f;
+        float u[AU_MB][MODAL_MAXP];
 #pragma unroll
-        for (int t = 0; t < MODAL_MAXP; ++t) u[t] = 0.f;
+        for (int mb = 0; mb < AU_MB; ++mb)
+#pragma unroll
+            for (int t = 0; t < MODAL_MAXP; ++t) u[mb][t] = 0.f;
         for (int c0 = 0; c0 < n_pair; c0 += 8) {
-            float y[8];
+            float pv[8];
+            int pa[8], pb[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int c = c0 + i;
-                float v = 0.f;
-                if (c < n_pair) {
-                    v = sM[s_pa[c]][tid] * sM[s_pb[c]][tid];
-                    if (pm && in) v -= pm[(int64_t)c * npix + x];
-                }
-                y[i] = v;
+                pa[i] = s_pa[c];
+                pb[i] = s_pb[c];
+                pv[i] = (pm && in && c < n_pair) ? pm[(int64_t)c * npix + x] : 0.f;
             }
 #pragma unroll
-            for (int t = 0; t < MODAL_MAXP; ++t) {
-                const float4 h0 = H4[(t * SC + c0) / 4], h1 = H4[(t * SC + c0) / 4 + 1];
-                u[t] = fmaf(h0.x, y[0], u[t]);
-                u[t] = fmaf(h0.y, y[1], u[t]);
-                u[t] = fmaf(h0.z, y[2], u[t]);
-                u[t] = fmaf(h0.w, y[3], u[t]);
-                u[t] = fmaf(h1.x, y[4], u[t]);
-                u[t] = fmaf(h1.y, y[5], u[t]);
-                u[t] = fmaf(h1.z, y[6], u[t]);
-                u[t] = fmaf(h1.w, y[7], u[t]);
+            for (int mb = 0; mb < AU_MB; ++mb) {
+                float y[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    y[i] = (c0 + i < n_pair)
+                               ? sM[(mb * MODAL_MAXP + pa[i]) * AU_THREADS + tid] * sM[(mb * MODAL_MAXP + pb[i]) * AU_THREADS + tid] - pv[i]
+                               : 0.f;
+#pragma unroll
+                for (int t = 0; t < MODAL_MAXP; ++t) {
+                    const int h = ((mb * MODAL_MAXP + t) * AU_SC + c0) / 4;
+                    const float4 h0 = H4[h], h1 = H4[h + 1];
+                    u[mb][t] = fmaf(h0.x, y[0], u[mb][t]);
+                    u[mb][t] = fmaf(h0.y, y[1], u[mb][t]);
+                    u[mb][t] = fmaf(h0.z, y[2], u[mb][t]);
+                    u[mb][t] = fmaf(h0.w, y[3], u[mb][t]);
+                    u[mb][t] = fmaf(h1.x, y[4], u[mb][t]);
+                    u[mb][t] = fmaf(h1.y, y[5], u[mb][t]);
+                    u[mb][t] = fmaf(h1.z, y[6], u[mb][t]);
+                    u[mb][t] = fmaf(h1.w, y[7], u[mb][t]);
+                }
             }
         }
         if (in) {
             const float wx = W[x];
 #pragma unroll
-            for (int t = 0; t < MODAL_MAXP; ++t)
-                if (t < P) mb[(int64_t)t * npix + x] = wx * u[t];
+            for (int mb = 0; mb < AU_MB; ++mb)
+#pragma unroll
+                for (int t = 0; t < MODAL_MAXP; ++t)
+                    if (mb < nb && t < P) maps[((int64_t)(b0 + mb) * P + t) * npix + x] = wx * u[mb][t];
         }
     }
 }
@@ -377,10 +399,15 @@ k_adjoint_u(int P, int n_pair, int64_t npix, const float* __restrict__ hk, const
 cudaError_t launch_adjoint_u(Plan& pl, const float* /*maps_in*/, int B, const float* hk, int use_linear, float* maps,
                              cudaStream_t st) {
     if (B == 0) return cudaSuccess;
+    const size_t smem = (size_t)AU_MB * MODAL_MAXP * (AU_SC + AU_THREADS) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     const int64_t nblk = (pl.npix + AU_THREADS - 1) / AU_THREADS;
-    dim3 grid((unsigned)(nblk < 152 * 8 ? nblk : 152 * 8), B);
+    const int ng = (B + AU_MB - 1) / AU_MB;
+    const int64_t want = (152 * 8 + ng - 1) / ng;            // about 8 blocks per SM in total
+    dim3 grid((unsigned)std::min<int64_t>(nblk, std::max<int64_t>(want, 152)), ng);
     const float* pm = use_linear ? pl.pair_mean : nullptr;
-    k_adjoint_u<<<grid, AU_THREADS, 0, st>>>(pl.P, pl.n_pair, pl.npix, hk, pm, pl.W, maps);
+    k_adjoint_u<<<grid, AU_THREADS, smem, st>>>(pl.P, pl.n_pair, B, pl.npix, hk, pm, pl.W, maps);
     return cudaGetLastError();
 }
 

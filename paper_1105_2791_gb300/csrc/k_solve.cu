@@ -43,45 +43,103 @@ cudaError_t launch_zeta(Plan& pl, double* zeta, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Right-looking Cholesky of the lower triangle of A (row-major n x n), one CTA.
-// On a pivot <= 0 (or NaN) the factorisation stops and MODAL_DEVERR_NOTPD is set.
-__global__ void __launch_bounds__(1024) k_cholesky(int n, double* __restrict__ A, int* __restrict__ err) {
-    extern __shared__ double col[];
+// Blocked right-looking Cholesky of the lower triangle of A (row-major n x n), 32-column
+// panels: (1) the diagonal block is factored in shared memory by one CTA, (2) the rows
+// below it are solved against it, (3) the trailing lower triangle is updated by a grid of
+// 32 x 32 tiles.  On a pivot <= 0 (or NaN) MODAL_DEVERR_NOTPD is set and every later
+// launch of the factorisation returns at once.
+constexpr int CH_NB = 32;
+
+__global__ void __launch_bounds__(CH_NB * CH_NB) k_chol_diag(int n, int k0, double* __restrict__ A, int* __restrict__ err) {
+    __shared__ double s[CH_NB][CH_NB + 1];
     __shared__ int bad;
-    __shared__ double piv;
+    if (*err & MODAL_DEVERR_NOTPD) return;
+    const int tx = threadIdx.x % CH_NB, ty = threadIdx.x / CH_NB;
+    const int kn = min(CH_NB, n - k0);
+    if (ty < kn && tx < kn) s[ty][tx] = A[(int64_t)(k0 + ty) * n + k0 + tx];
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < kn; ++k) {
         if (threadIdx.x == 0) {
-            const double d = A[(int64_t)k * n + k];
+            const double d = s[k][k];
             if (!(d > 0.0)) {
                 bad = 1;
                 atomicOr(err, MODAL_DEVERR_NOTPD);
             } else {
-                piv = sqrt(d);
-                A[(int64_t)k * n + k] = piv;
+                s[k][k] = sqrt(d);
             }
         }
         __syncthreads();
         if (bad) return;
-        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-            const double v = A[(int64_t)i * n + k] / piv;
-            A[(int64_t)i * n + k] = v;
-            col[i] = v;
-        }
+        if (ty == 0 && tx > k && tx < kn) s[tx][k] /= s[k][k];
         __syncthreads();
-        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        for (int i = k + 1 + ty; i < n; i += 32) {
-            const double ci = col[i];
-            double* row = A + (int64_t)i * n;
-            for (int j = k + 1 + tx; j <= i; j += 32) row[j] -= ci * col[j];
-        }
+        if (tx > k && ty > k && tx <= ty && ty < kn) s[ty][tx] -= s[ty][k] * s[tx][k];
         __syncthreads();
+    }
+    if (ty < kn && tx <= ty) A[(int64_t)(k0 + ty) * n + k0 + tx] = s[ty][tx];
+}
+
+// Rows i >= k0 + 32 of the panel: solve x L11^T = a for x (one 32-thread warp per row).
+__global__ void __launch_bounds__(256) k_chol_panel(int n, int k0, double* __restrict__ A, const int* __restrict__ err) {
+    __shared__ double L11[CH_NB][CH_NB + 1];
+    if (*err & MODAL_DEVERR_NOTPD) return;
+    const int kn = CH_NB;                                   // panel rows exist only below a full block
+    for (int i = threadIdx.x; i < CH_NB * CH_NB; i += blockDim.x) {
+        const int r = i / CH_NB, c = i % CH_NB;
+        L11[r][c] = (c <= r) ? A[(int64_t)(k0 + r) * n + k0 + c] : 0.0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int row = k0 + kn + blockIdx.x * 8 + warp;
+    if (row >= n) return;
+    double* a = A + (int64_t)row * n + k0;
+    double x = a[lane];
+    for (int j = 0; j < kn; ++j) {
+        // x_j = (a_j - sum_{i<j} x_i L_ji) / L_jj: lanes > j subtract lane j's finished value
+        const double xj = __shfl_sync(0xffffffffu, x, j) / L11[j][j];
+        if (lane == j) x = xj;
+        if (lane > j) x -= xj * L11[lane][j];
+    }
+    a[lane] = x;
+}
+
+// Trailing update A22 -= A21 A21^T on 32 x 32 tiles (rb >= cb), K = 32.
+__global__ void __launch_bounds__(256) k_chol_update(int n, int k0, double* __restrict__ A, const int* __restrict__ err) {
+    __shared__ double Ar[CH_NB][CH_NB + 1], Ac[CH_NB][CH_NB + 1];
+    if (*err & MODAL_DEVERR_NOTPD) return;
+    const int nt = (n - k0 - CH_NB + CH_NB - 1) / CH_NB;
+    // blockIdx.x enumerates the lower triangle of tiles: (rb, cb), cb <= rb
+    int rb = 0, rem = blockIdx.x;
+    while (rem > rb) { rem -= rb + 1; ++rb; }
+    const int cb = rem;
+    if (rb >= nt) return;
+    const int r0 = k0 + CH_NB + rb * CH_NB, c0 = k0 + CH_NB + cb * CH_NB;
+    for (int i = threadIdx.x; i < CH_NB * CH_NB; i += blockDim.x) {
+        const int r = i / CH_NB, k = i % CH_NB;
+        Ar[r][k] = (r0 + r < n) ? A[(int64_t)(r0 + r) * n + k0 + k] : 0.0;
+        Ac[r][k] = (c0 + r < n) ? A[(int64_t)(c0 + r) * n + k0 + k] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < CH_NB * CH_NB; i += blockDim.x) {
+        const int r = i / CH_NB, c = i % CH_NB;
+        if (r0 + r >= n || c0 + c >= n || c0 + c > r0 + r) continue;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < CH_NB; ++k) acc = fma(Ar[r][k], Ac[c][k], acc);
+        A[(int64_t)(r0 + r) * n + c0 + c] -= acc;
     }
 }
 
 cudaError_t launch_cholesky(Plan& pl, double* A, int n, cudaStream_t st) {
-    k_cholesky<<<1, 1024, (size_t)n * sizeof(double), st>>>(n, A, pl.d_err);
+    for (int k0 = 0; k0 < n; k0 += CH_NB) {
+        k_chol_diag<<<1, CH_NB * CH_NB, 0, st>>>(n, k0, A, pl.d_err);
+        const int below = n - k0 - CH_NB;
+        if (below > 0) {
+            k_chol_panel<<<(below + 7) / 8, 256, 0, st>>>(n, k0, A, pl.d_err);
+            const int nt = (below + CH_NB - 1) / CH_NB;
+            k_chol_update<<<nt * (nt + 1) / 2, 256, 0, st>>>(n, k0, A, pl.d_err);
+        }
+    }
     return cudaGetLastError();
 }
 
