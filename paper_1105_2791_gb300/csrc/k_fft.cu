@@ -1,9 +1,10 @@
-// Ring Fourier transforms in shared memory (power-of-two N = nphi).
+// Ring Fourier transforms in shared memory (power-of-two N = nphi, 128 <= N <= 8192).
 //
 // Synthesis (c2r):  M(theta, phi_k) = D_0 + 2 Re sum_{m=1}^{lmax} D_m e^{i m phi_k}
 // = sum_{m=-lmax}^{lmax} D_m e^{2 pi i m k / N} with D_{-m} = conj(D_m).  The north
 // and south rings of one ring pair share one complex transform:
-// Z = X_north + i X_south (both Hermitian), z = IDFT(Z), north = Re z, south = Im z.
+// Z = X_north + i X_south (both Hermitian), z = IDFT(Z), north = Re z, south = Im z,
+// where X_north = E + O and X_south = E - O from the even/odd Legendre sums.
 //
 // Analysis (r2c):  U~_m = sum_k U(k) e^{-2 pi i m k / N}, m = 0..lmax, for a pair of
 // real rings packed as z = U_north + i U_south; U~_north,m = (Z_m + conj Z_{N-m}) / 2,
@@ -11,106 +12,161 @@
 // (U~_north + U~_south, U~_north - U~_south), the even/odd-l combinations the
 // transposed Legendre sum consumes.
 //
-// Both use an in-place Stockham radix-4 (plus one radix-2 stage when log2 N is odd):
-// every thread loads its butterfly inputs, the block synchronises, every thread
-// stores its outputs.
+// Transform: Stockham autosort passes of radix 16 (a last pass of radix 8, 4 or 2 when
+// log2 N is not a multiple of 4).  Every thread owns 16 elements of one transform
+// (T = N / 16 threads per transform): it loads them, applies the inter-pass twiddles
+// and a radix-R butterfly in registers (16 / R butterflies), and stores them; one
+// block-wide sync separates loads from stores.  Shared-memory index i is padded to
+// i + i / 16 to spread the strided stores over the banks.  A CTA of 1024 threads
+// holds 16384 / N transforms (four ring pairs at N = 4096), so the E/O rows and the
+// U~ rows move in full 32-byte sectors.
 #include "modal_internal.cuh"
 
 namespace modal {
 
-constexpr int FFT_THREADS = 512;
+constexpr int FFT_THREADS = 1024;
+constexpr int FFT_ELEMS = 16384;                 // complex elements per CTA (all transforms)
 
+__host__ __device__ inline int fft_rings_per_block(int N) { return FFT_ELEMS / N; }
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-
-// Stockham passes over `ntr` transforms of length N stored back to back in buf.
-// sign = +1: e^{+2 pi i ...} (synthesis); sign = -1: e^{-2 pi i ...} (analysis).
-// tw[q] = e^{+2 pi i q / N}.
+// multiply by SIGN * i
 template <int SIGN>
-__device__ void stockham_inplace(float2* buf, int N, int log2N, int ntr, const float2* __restrict__ tw) {
-    int Ns = 1, log2Ns = 0;
-    if (log2N & 1) {
-        // radix-2 stage at Ns = 1: no twiddles
-        const int half = N >> 1, lh = log2N - 1;
-        for (int base = 0; base < ntr * half; base += FFT_THREADS * 8) {
-            float2 v0[8], v1[8];
+__device__ __forceinline__ float2 cmul_si(float2 a) {
+    return (SIGN > 0) ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos and sin of k pi / 8, k = 0..15 (exact values of the 16th roots of unity).
+__constant__ float c_cos16[16] = {1.f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                                  0.f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                                  -1.f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                                  0.f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+__constant__ float c_sin16[16] = {0.f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                                  1.f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                                  0.f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                                  -1.f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
+
+// e^{SIGN 2 pi i k / 16}
+template <int SIGN>
+__device__ __forceinline__ float2 w16(int k) {
+    return make_float2(c_cos16[k & 15], SIGN * c_sin16[k & 15]);
+}
+
+// In-register DFTs: X_k = sum_n x_n e^{SIGN 2 pi i n k / R}, in place (x[k] <- X_k).
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+    const float2 a0 = cadd(x0, x2), a1 = csub(x0, x2), a2 = cadd(x1, x3), a3 = cmul_si<SIGN>(csub(x1, x3));
+    x0 = cadd(a0, a2);
+    x1 = cadd(a1, a3);
+    x2 = csub(a0, a2);
+    x3 = csub(a1, a3);
+}
+
+template <int SIGN, int R>
+__device__ __forceinline__ void dft(float2* x) {
+    if (R == 2) {
+        const float2 a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    } else if (R == 4) {
+        dft4<SIGN>(x[0], x[1], x[2], x[3]);
+    } else if (R == 8) {
+        // n = 2 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W8^(n2 k1), DFT2 over n2
+        float2 y[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int idx = base + threadIdx.x + u * FFT_THREADS;
-                if (idx < ntr * half) {
-                    const int q = idx >> lh, jj = idx & (half - 1);
-                    v0[u] = buf[(q << log2N) + jj];
-                    v1[u] = buf[(q << log2N) + jj + half];
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int idx = base + threadIdx.x + u * FFT_THREADS;
-                if (idx < ntr * half) {
-                    const int q = idx >> lh, jj = idx & (half - 1);
-                    buf[(q << log2N) + 2 * jj] = make_float2(v0[u].x + v1[u].x, v0[u].y + v1[u].y);
-                    buf[(q << log2N) + 2 * jj + 1] = make_float2(v0[u].x - v1[u].x, v0[u].y - v1[u].y);
-                }
-            }
-            __syncthreads();
+        for (int n2 = 0; n2 < 2; ++n2) {
+            float2 a = x[n2], b = x[2 + n2], c = x[4 + n2], d = x[6 + n2];
+            dft4<SIGN>(a, b, c, d);
+            y[n2 * 4 + 0] = a;
+            y[n2 * 4 + 1] = (n2 == 0) ? b : cmul(b, w16<SIGN>(2));
+            y[n2 * 4 + 2] = (n2 == 0) ? c : cmul(c, w16<SIGN>(4));
+            y[n2 * 4 + 3] = (n2 == 0) ? d : cmul(d, w16<SIGN>(6));
         }
-        Ns = 2;
-        log2Ns = 1;
-    }
-    const int quarter = N >> 2, lq = log2N - 2;
-    for (; Ns < N; Ns <<= 2, log2Ns += 2) {
-        const int lstride = log2N - log2Ns - 2;       // twiddle index step for r * k is 2^lstride
-        for (int base = 0; base < ntr * quarter; base += FFT_THREADS * 4) {
-            float2 v[4][4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = base + threadIdx.x + u * FFT_THREADS;
-                if (idx < ntr * quarter) {
-                    const int q = idx >> lq, jj = idx & (quarter - 1);
-                    const int k = jj & (Ns - 1);
+        for (int k1 = 0; k1 < 4; ++k1) {
+            x[k1] = cadd(y[k1], y[4 + k1]);
+            x[k1 + 4] = csub(y[k1], y[4 + k1]);
+        }
+    } else {
+        // R = 16: n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W16^(n2 k1), DFT4 over n2
+        float2 y[16];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        float2 x = buf[(q << log2N) + jj + r * quarter];
-                        if (r > 0) {
-                            float2 w = __ldg(&tw[(r * k) << lstride]);
-                            if (SIGN < 0) w.y = -w.y;
-                            x = cmul(x, w);
-                        }
-                        v[u][r] = x;
-                    }
-                }
-            }
-            __syncthreads();
+        for (int n2 = 0; n2 < 4; ++n2) {
+            float2 a = x[n2], b = x[4 + n2], c = x[8 + n2], d = x[12 + n2];
+            dft4<SIGN>(a, b, c, d);
+            y[n2 * 4 + 0] = a;
+            y[n2 * 4 + 1] = (n2 == 0) ? b : cmul(b, w16<SIGN>(n2));
+            y[n2 * 4 + 2] = (n2 == 0) ? c : cmul(c, w16<SIGN>(2 * n2));
+            y[n2 * 4 + 3] = (n2 == 0) ? d : cmul(d, w16<SIGN>(3 * n2));
+        }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = base + threadIdx.x + u * FFT_THREADS;
-                if (idx < ntr * quarter) {
-                    const int q = idx >> lq, jj = idx & (quarter - 1);
-                    const int k = jj & (Ns - 1);
-                    const int d = ((jj >> log2Ns) << (log2Ns + 2)) + k;
-                    const float2 a0 = make_float2(v[u][0].x + v[u][2].x, v[u][0].y + v[u][2].y);
-                    const float2 a1 = make_float2(v[u][0].x - v[u][2].x, v[u][0].y - v[u][2].y);
-                    const float2 a2 = make_float2(v[u][1].x + v[u][3].x, v[u][1].y + v[u][3].y);
-                    const float2 df = make_float2(v[u][1].x - v[u][3].x, v[u][1].y - v[u][3].y);
-                    // a3 = SIGN * i * (v1 - v3)
-                    const float2 a3 = (SIGN > 0) ? make_float2(-df.y, df.x) : make_float2(df.y, -df.x);
-                    float2* o = buf + (q << log2N) + d;
-                    o[0] = make_float2(a0.x + a2.x, a0.y + a2.y);
-                    o[Ns] = make_float2(a1.x + a3.x, a1.y + a3.y);
-                    o[2 * Ns] = make_float2(a0.x - a2.x, a0.y - a2.y);
-                    o[3 * Ns] = make_float2(a1.x - a3.x, a1.y - a3.y);
-                }
-            }
-            __syncthreads();
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 a = y[k1], b = y[4 + k1], c = y[8 + k1], d = y[12 + k1];
+            dft4<SIGN>(a, b, c, d);
+            x[k1] = a;
+            x[k1 + 4] = b;
+            x[k1 + 8] = c;
+            x[k1 + 12] = d;
         }
     }
 }
 
-__host__ __device__ inline int fft_rings_per_block(int N) {
-    int r = 16384 / N;
-    return r < 1 ? 1 : (r > 16 ? 16 : r);
+// One Stockham pass of radix R at sub-transform length Ns over the transform at `buf`
+// (padded indices).  Thread tl (0 <= tl < T = N / 16) handles butterflies j = tl + T u.
+template <int SIGN, int R>
+__device__ __forceinline__ void stockham_pass(float2* buf, int N, int log2N, int Ns, int log2Ns, int tl,
+                                              const float2* __restrict__ tw) {
+    constexpr int NB = 16 / R;                   // butterflies per thread
+    constexpr int LR = (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
+    const int T = N >> 4;
+    const int NR = N / R;
+    const int lstride = log2N - log2Ns - LR;     // twiddle index step for r * k is 2^lstride
+    float2 v[16];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int j = tl + T * u;
+        const int k = j & (Ns - 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 x = buf[pad16(j + r * NR)];
+            if (r > 0 && Ns > 1) {
+                float2 w = __ldg(&tw[(r * k) << lstride]);
+                if (SIGN < 0) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[u * R + r] = x;
+        }
+        dft<SIGN, R>(v + u * R);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int j = tl + T * u;
+        const int k = j & (Ns - 1);
+        const int d = (((j >> log2Ns) * R) << log2Ns) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad16(d + r * Ns)] = v[u * R + r];
+    }
+    __syncthreads();
+}
+
+template <int SIGN>
+__device__ void fft_transform(float2* buf, int N, int log2N, int tl, const float2* __restrict__ tw) {
+    int Ns = 1, log2Ns = 0;
+    while (log2N - log2Ns >= 4) {
+        stockham_pass<SIGN, 16>(buf, N, log2N, Ns, log2Ns, tl, tw);
+        Ns <<= 4;
+        log2Ns += 4;
+    }
+    const int rem = log2N - log2Ns;
+    if (rem == 3) stockham_pass<SIGN, 8>(buf, N, log2N, Ns, log2Ns, tl, tw);
+    else if (rem == 2) stockham_pass<SIGN, 4>(buf, N, log2N, Ns, log2Ns, tl, tw);
+    else if (rem == 1) stockham_pass<SIGN, 2>(buf, N, log2N, Ns, log2Ns, tl, tw);
 }
 
 // grid: (ceil(R_half / RPB), nmp); nmp = number of (map, p) rows.
@@ -121,32 +177,42 @@ k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __r
            const float2* __restrict__ tw, float* __restrict__ maps) {
     extern __shared__ float2 buf[];
     const int RPB = fft_rings_per_block(N);
+    const int NP = N + (N >> 4);                         // padded transform length
     const int mp = blockIdx.y;
     const int j0 = blockIdx.x * RPB;
     const int ntr = min(RPB, R_half - j0);
-    for (int i = threadIdx.x; i < ntr * N; i += FFT_THREADS) buf[i] = make_float2(0.f, 0.f);
-    __syncthreads();
+    const int nzero = N - 2 * L - 1;                     // entries L+1 .. N-L-1 stay zero
+    for (int i = threadIdx.x; i < RPB * nzero; i += FFT_THREADS) {
+        const int q = i / nzero, k = L + 1 + i % nzero;
+        buf[q * NP + pad16(k)] = make_float2(0.f, 0.f);
+    }
     const float2* d = delta + (int64_t)mp * (L + 1) * 2 * RH;
-    for (int i = threadIdx.x; i < (L + 1) * ntr; i += FFT_THREADS) {
-        const int m = i / ntr, q = i % ntr;
-        const float2 e = d[(int64_t)m * 2 * RH + j0 + q];
-        const float2 o = d[(int64_t)m * 2 * RH + RH + j0 + q];
-        const float2 dn = make_float2(e.x + o.x, e.y + o.y);
-        const float2 ds = make_float2(e.x - o.x, e.y - o.y);
+    for (int i = threadIdx.x; i < (L + 1) * RPB; i += FFT_THREADS) {
+        const int m = i / RPB, q = i % RPB;
+        float2 e = make_float2(0.f, 0.f), o = e;
+        if (q < ntr) {
+            e = d[(int64_t)m * 2 * RH + j0 + q];
+            o = d[(int64_t)m * 2 * RH + RH + j0 + q];
+        }
+        const float2 dn = cadd(e, o), ds = csub(e, o);
+        float2* b = buf + q * NP;
         if (m == 0) {
-            buf[q * N] = make_float2(dn.x, ds.x);
+            b[0] = make_float2(dn.x, ds.x);
         } else {
-            buf[q * N + m] = make_float2(dn.x - ds.y, dn.y + ds.x);       // X_n + i X_s
-            buf[q * N + N - m] = make_float2(dn.x + ds.y, ds.x - dn.y);   // conj(X_n) + i conj(X_s)
+            b[pad16(m)] = make_float2(dn.x - ds.y, dn.y + ds.x);       // X_n + i X_s
+            b[pad16(N - m)] = make_float2(dn.x + ds.y, ds.x - dn.y);   // conj(X_n) + i conj(X_s)
         }
     }
     __syncthreads();
-    stockham_inplace<+1>(buf, N, log2N, ntr, tw);
+    const int T = N >> 4;
+    const int q = threadIdx.x / T, tl = threadIdx.x % T;
+    fft_transform<+1>(buf + q * NP, N, log2N, tl, tw);
     float* out = maps + (int64_t)mp * R * N;
-    for (int q = 0; q < ntr; ++q) {
-        const int jn = j0 + q, js = R - 1 - jn;
+    for (int qq = 0; qq < ntr; ++qq) {
+        const int jn = j0 + qq, js = R - 1 - jn;
+        const float2* b = buf + qq * NP;
         for (int k = threadIdx.x; k < N; k += FFT_THREADS) {
-            const float2 z = buf[q * N + k];
+            const float2 z = b[pad16(k)];
             out[(int64_t)jn * N + k] = z.x;
             if (js != jn) out[(int64_t)js * N + k] = z.y;
         }
@@ -159,32 +225,42 @@ k_ring_r2c(int L, int R, int R_half, int RH, int N, int log2N, const float* __re
            const float* __restrict__ ring_weight, const float2* __restrict__ tw, float2* __restrict__ ut) {
     extern __shared__ float2 buf[];
     const int RPB = fft_rings_per_block(N);
+    const int NP = N + (N >> 4);
     const int mp = blockIdx.y;
     const int j0 = blockIdx.x * RPB;
     const int ntr = min(RPB, R_half - j0);
     const float* in = maps + (int64_t)mp * R * N;
-    for (int q = 0; q < ntr; ++q) {
-        const int jn = j0 + q, js = R - 1 - jn;
+    for (int qq = 0; qq < RPB; ++qq) {
+        const int jn = j0 + qq, js = R - 1 - jn;
+        float2* b = buf + qq * NP;
+        if (qq >= ntr) {
+            for (int k = threadIdx.x; k < N; k += FFT_THREADS) b[pad16(k)] = make_float2(0.f, 0.f);
+            continue;
+        }
         const float wn = ring_weight ? ring_weight[jn] : 1.f;
         const float ws = ring_weight ? ring_weight[js] : 1.f;
         for (int k = threadIdx.x; k < N; k += FFT_THREADS) {
             const float xn = wn * in[(int64_t)jn * N + k];
             const float xs = (js != jn) ? ws * in[(int64_t)js * N + k] : 0.f;
-            buf[q * N + k] = make_float2(xn, xs);
+            b[pad16(k)] = make_float2(xn, xs);
         }
     }
     __syncthreads();
-    stockham_inplace<-1>(buf, N, log2N, ntr, tw);
+    const int T = N >> 4;
+    const int q = threadIdx.x / T, tl = threadIdx.x % T;
+    fft_transform<-1>(buf + q * NP, N, log2N, tl, tw);
     float2* o = ut + (int64_t)mp * (L + 1) * 2 * RH;
-    for (int i = threadIdx.x; i < (L + 1) * ntr; i += FFT_THREADS) {
-        const int m = i / ntr, q = i % ntr;
-        const float2 zm = buf[q * N + m];
-        const float2 zc = buf[q * N + ((N - m) & (N - 1))];
+    for (int i = threadIdx.x; i < (L + 1) * RPB; i += FFT_THREADS) {
+        const int m = i / RPB, qq = i % RPB;
+        if (qq >= ntr) continue;
+        const float2* b = buf + qq * NP;
+        const float2 zm = b[pad16(m)];
+        const float2 zc = b[pad16((N - m) & (N - 1))];
         // U~_n = (Z_m + conj Z_{N-m}) / 2 ; U~_s = (Z_m - conj Z_{N-m}) / 2i
         const float2 un = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
         const float2 us = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
-        o[((int64_t)m * 2 + 0) * RH + j0 + q] = make_float2(un.x + us.x, un.y + us.y);
-        o[((int64_t)m * 2 + 1) * RH + j0 + q] = make_float2(un.x - us.x, un.y - us.y);
+        o[((int64_t)m * 2 + 0) * RH + j0 + qq] = cadd(un, us);
+        o[((int64_t)m * 2 + 1) * RH + j0 + qq] = csub(un, us);
     }
 }
 
@@ -194,10 +270,12 @@ static int ilog2(int n) {
     return r;
 }
 
+static size_t fft_smem(int N) { return (size_t)fft_rings_per_block(N) * (N + (N >> 4)) * sizeof(float2); }
+
 cudaError_t launch_ring_c2r(const Plan& pl, const float2* delta, int nmp, float* maps, cudaStream_t st) {
     if (nmp == 0) return cudaSuccess;
     const int N = pl.nphi, RPB = fft_rings_per_block(N);
-    const size_t smem = (size_t)RPB * N * sizeof(float2);
+    const size_t smem = fft_smem(N);
     cudaError_t e = cudaFuncSetAttribute(k_ring_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
@@ -210,7 +288,7 @@ cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmp, const fl
                             cudaStream_t st) {
     if (nmp == 0) return cudaSuccess;
     const int N = pl.nphi, RPB = fft_rings_per_block(N);
-    const size_t smem = (size_t)RPB * N * sizeof(float2);
+    const size_t smem = fft_smem(N);
     cudaError_t e = cudaFuncSetAttribute(k_ring_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
