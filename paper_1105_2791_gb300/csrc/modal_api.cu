@@ -502,7 +502,11 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
         const int nb = std::min(h->chunk, B - b0);
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "cubic synthesis");
         { STAGE(h, ST_CUBIC, st); CK(launch_cubic(*h, h->maps, nb, cub, st), "cubic"); }
-        if (use_linear) { STAGE(h, ST_LINEAR, st); CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm"); }
+        if (use_linear) {
+            STAGE(h, ST_LINEAR, st);
+            if (h->prec == MODAL_FP32) CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm");
+            else CK(launch_linear_tc(*h, h->maps, nb, lin, st), "linear gemm");
+        }
         { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, beta + (size_t)b0 * h->n_max, st), "beta finalize"); }
     }
     return MODAL_OK;

@@ -145,6 +145,7 @@ cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmaps_p, cons
 // k_cubic.cu
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
+cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);   // k_linear_tc.cu
 cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* cub_partial,
                                  const double* lin_partial, double* beta, cudaStream_t st);
 cudaError_t launch_pair_accumulate(Plan& pl, const float* maps, int B, cudaStream_t st);

@@ -362,3 +362,64 @@ def test_backward_full_size_l2000_sampled_rings(prec):
         err = _rel(grad[b], ref)
         print("adjoint lmax=2000 %s map %d: grad rel err %.3g" % (prec, b, err))
         assert err <= 1e-5
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_linear_term_16_modes(prec):
+    """beta with the linear term at 16 modes (136 pairs): pair means and the linear GEMM
+    at full width, masked sky."""
+    M = _cuda_or_skip()
+    L, P, R, nphi = 70, 16, 71, 256
+    basis, cl, alm = _case(L, P, 3, seed=81)
+    mask = simgen.band_mask(R, 20.0)
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec, ring_mask=mask)
+    sims = simgen.gaussian_alm(cl, 12, seed=82, stream=simgen.STREAM_LINEAR).astype(np.complex64)
+    plan.linear_term(torch.from_numpy(sims).cuda(), finalize=True)
+    beta = plan.cubic(torch.from_numpy(alm).cuda(), use_linear=True).cpu().numpy()
+    plan.close()
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    W = om.pixel_weights(w, nphi, mask)
+    pm = om.pair_means([osh.synthesize(s.astype(np.complex128), L, filt, mu, nphi) for s in sims])
+    for b in range(3):
+        ref = om.cubic_beta(osh.synthesize(alm[b].astype(np.complex128), L, filt, mu, nphi), W, pm)
+        err = _rel(beta[b], ref)
+        print("linear term lmax=70 P=16 %s map %d: beta rel err %.3g" % (prec, b, err))
+        assert err <= 1e-5
+
+
+def test_wmap_resolution_workload():
+    """l_max = 500 on 501 x 1024 rings, 10 modes (220 coefficients), anisotropic noise and
+    a 20-degree band mask, linear term from 6 noisy simulations: beta of one data map
+    with the split-precision path against the full-grid oracle."""
+    M = _cuda_or_skip()
+    cfg = simgen.config("wmap")
+    L, P, R, nphi = cfg["lmax"], cfg["P"], cfg["nrings"], cfg["nphi"]
+    basis = simgen.shifted_legendre_basis(L, P)
+    cl = simgen.cl_model(L)
+    s0 = 0.1 * cl[L]
+    sig = simgen.noise_sigma_rings(R, s0)
+    cl_tot = cl + np.where(np.arange(L + 1) >= 2, 2 * s0, 0.0)
+    mask = simgen.band_mask(R, 20.0)
+    plan = _plan(M, L, P, basis, cl_tot, R, nphi, "fp16x3", ring_mask=mask)
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl_tot)
+    W = om.pixel_weights(w, nphi, mask)
+
+    def sims(n, seed, stream):
+        sa = simgen.gaussian_alm(cl, n, seed=seed, stream=stream).astype(np.complex64)
+        xi = simgen.pixel_normals(R, nphi, n, seed=seed, stream=simgen.STREAM_NOISE)
+        g = torch.from_numpy(sa).cuda() + _noise_alm_gpu(plan, xi, sig)
+        o = sa.astype(np.complex128) + _noise_alm_oracle(L, R, nphi, xi, sig)
+        return g.contiguous(), o
+
+    g_lin, o_lin = sims(6, cfg["seed"], simgen.STREAM_LINEAR)
+    plan.linear_term(g_lin, finalize=True)
+    g_dat, o_dat = sims(1, cfg["seed"], simgen.STREAM_DATA)
+    beta = plan.cubic(g_dat, use_linear=True).cpu().numpy()[0]
+    plan.close()
+    pm = om.pair_means([osh.synthesize(a, L, filt, mu, nphi) for a in o_lin])
+    ref = om.cubic_beta(osh.synthesize(o_dat[0], L, filt, mu, nphi), W, pm)
+    err = _rel(beta, ref)
+    print("WMAP-resolution workload (lmax=500, P=10) fp16x3: beta rel err %.3g" % err)
+    assert err <= 1e-5
