@@ -13,80 +13,150 @@
 namespace modal {
 
 // ---------------------------------------------------------------- cubic term
-// Register tiles of 8 pairs x 4 values of s over pairs in colex order (by r, then p),
-// so that tiles entirely below the diagonal s < r are skipped; each thread of a CTA
-// owns one tile and one of 8 pixel lanes.  Pair products W M_p M_r are formed once
-// per pixel in shared memory.  Per-CTA partial sums go to `partial` (FP64) and are
-// summed in a fixed order by k_beta_finalize.
-constexpr int CUB_TX = 64;
-constexpr int CUB_LANES = 8;
+// C_prs = sum_x U_(pr)(x) M_s(x) with U_(pr) = W M_p M_r: a GEMM of the pair-product
+// panel against the map panel, one map per CTA row of the grid, the panel built in
+// shared memory tile by tile and never written to HBM.
+//
+// Warp roles (named barriers, two shared-memory stages of CUB_TX pixels each):
+//   fill warps     one pixel per thread: the map values and W are prefetched two tiles
+//                  ahead in registers, the pair products of all colex pairs are formed
+//                  in registers and stored as float4 rows of the panel;
+//   compute warps  one register tile of 8 pairs x 4 values of s per thread and one of
+//                  `nl` pixel lanes; pairs in colex order (by r, then p), so that tiles
+//                  entirely below the diagonal s < r are absent from the tile list.
+// Panel row layout: [half][pair group][4] so that the two float4 of a tile sit in two
+// contiguous 16-byte runs across the warp; row stride 8 n_pg + 4 floats keeps the
+// per-thread float4 stores of the fill warps free of bank conflicts.  Per-CTA partial
+// sums go to `partial` (FP64) and are summed in a fixed order by k_beta_finalize.
+constexpr int CUB_TX = 128;                 // pixels per stage (= fill threads)
+constexpr int CUB_MS = 20;                  // row stride of the staged map values
+constexpr int CUB_MAXCOMP = 288;            // compute threads at most
+constexpr int CUB_THREADS = CUB_MAXCOMP + CUB_TX;
 
-__global__ void __launch_bounds__(320)
-k_cubic(int P, int SU, int SM, int ntiles, const int* __restrict__ tiles, const int* __restrict__ pair_ab,
+__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void named_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+template <int PM>
+__global__ void __launch_bounds__(CUB_THREADS, 1)
+k_cubic(int P, int n_pg, int ntiles, int nl, int ncomp, const int* __restrict__ tiles,
         const int* __restrict__ modeidx, int64_t npix, int64_t px_per_cta, const float* __restrict__ maps,
         const float* __restrict__ W, double* __restrict__ partial, int n_max) {
     extern __shared__ __align__(16) float smem[];
-    float* sU = smem;                         // [CUB_TX][SU]
-    float* sM = sU + CUB_TX * SU;             // [CUB_TX][SM]
-    float* sW = sM + CUB_TX * SM;             // [CUB_TX]
+    const int SU = 8 * n_pg + 4;
+    const int stage_floats = CUB_TX * (SU + CUB_MS);
     const int b = blockIdx.y;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int tile = tid % ntiles;
-    const int lane = tid / ntiles;
-    const bool computes = lane < CUB_LANES;
-    const int tpk = tiles[tile];
-    const int pg = tpk & 0xff, sq = tpk >> 8;
+    const int tid = threadIdx.x;
+    const int nthr = ncomp + CUB_TX;
     const int64_t x_begin = (int64_t)blockIdx.x * px_per_cta;
     const int64_t x_end = min(npix, x_begin + px_per_cta);
+    const int nch = (x_end > x_begin) ? (int)((x_end - x_begin + CUB_TX - 1) / CUB_TX) : 0;
     const float* mb = maps + (int64_t)b * P * npix;
-    // pair-product fill: thread -> (pair column, block of pixels), fixed for the CTA
-    const int nsplit = max(1, nthr / SU);
-    const int fill_c = (tid < nsplit * SU) ? tid % SU : -1;
-    const int fill_part = (tid < nsplit * SU) ? tid / SU : 0;
-    const int fill_nx = (CUB_TX + nsplit - 1) / nsplit;
-    const int fill_x0 = fill_part * fill_nx;
-    const int fill_ab = (fill_c >= 0) ? pair_ab[fill_c] : -1;
 
     float acc[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) acc[e] = 0.f;
+    const int tile = tid % ntiles, lane = tid / ntiles;
 
-    for (int64_t x0 = x_begin; x0 < x_end; x0 += CUB_TX) {
-        for (int i = tid; i < CUB_TX * SM; i += nthr) {
-            const int xl = i % CUB_TX, s = i / CUB_TX;
-            const int64_t x = x0 + xl;
-            sM[xl * SM + s] = (s < P && x < x_end) ? mb[(int64_t)s * npix + x] : 0.f;
-        }
-        for (int i = tid; i < CUB_TX; i += nthr) sW[i] = (x0 + i < x_end) ? W[x0 + i] : 0.f;
-        __syncthreads();
-        if (fill_c >= 0) {
-            for (int xl = fill_x0; xl < fill_x0 + fill_nx && xl < CUB_TX; ++xl)
-                sU[xl * SU + fill_c] = (fill_ab >= 0) ? sW[xl] * sM[xl * SM + (fill_ab & 0xff)] * sM[xl * SM + (fill_ab >> 8)]
-                                                      : 0.f;
-        }
-        __syncthreads();
-        if (computes) {
-            float tmp[32];
+    if (tid >= ncomp) {
+        // ------------------------------------------------ fill warps
+        const int xl = tid - ncomp;
+        float cur[PM + 1], n1[PM + 1], n2[PM + 1];
+        auto load = [&](float* v, int k) {
+            const int64_t x = x_begin + (int64_t)k * CUB_TX + xl;
+            const bool in = k < nch && x < x_end;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) tmp[e] = 0.f;
-            for (int xi = lane; xi < CUB_TX; xi += CUB_LANES) {
-                const float4 u0 = *reinterpret_cast<const float4*>(sU + xi * SU + pg * 8);
-                const float4 u1 = *reinterpret_cast<const float4*>(sU + xi * SU + pg * 8 + 4);
-                const float4 mv = *reinterpret_cast<const float4*>(sM + xi * SM + sq * 4);
-                const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-                const float mm[4] = {mv.x, mv.y, mv.z, mv.w};
+            for (int p = 0; p < PM; ++p) v[p] = (in && p < P) ? mb[(int64_t)p * npix + x] : 0.f;
+            v[PM] = in ? W[x] : 0.f;
+        };
+        load(cur, 0);
+        load(n1, 1);
+        const int hoff = 4 * n_pg;
+        for (int k = 0; k < nch; ++k) {
+            load(n2, k + 2);
+            const int s = k & 1;
+            if (k >= 2) named_sync(3 + s, nthr);
+            float* sU = smem + s * stage_floats + xl * SU;
+            float* sMs = smem + s * stage_floats + CUB_TX * SU + xl * CUB_MS;
+            float wm[PM];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+            for (int p = 0; p < PM; ++p) wm[p] = cur[PM] * cur[p];
+            float st[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) tmp[i * 4 + k] = fmaf(u[i], mm[k], tmp[i * 4 + k]);
+            for (int r = 0; r < PM; ++r)
+#pragma unroll
+                for (int p = 0; p <= r; ++p) {
+                    const int c = r * (r + 1) / 2 + p;           // colex pair index
+                    st[c & 3] = wm[p] * cur[r];
+                    if ((c & 3) == 3 && c < 8 * n_pg) {
+                        const int k4 = c >> 2;
+                        *reinterpret_cast<float4*>(sU + (k4 & 1) * hoff + (k4 >> 1) * 4) =
+                            make_float4(st[0], st[1], st[2], st[3]);
+                    }
+                }
+            constexpr int NPR = PM * (PM + 1) / 2;
+            if ((NPR & 3) != 0) {                                // tail of a partial float4
+                const int c0 = NPR & ~3;
+#pragma unroll
+                for (int i = (NPR & 3); i < 4; ++i) st[i] = 0.f;
+                if (c0 < 8 * n_pg) {
+                    const int k4 = c0 >> 2;
+                    *reinterpret_cast<float4*>(sU + (k4 & 1) * hoff + (k4 >> 1) * 4) =
+                        make_float4(st[0], st[1], st[2], st[3]);
+                }
+            }
+            // pair slots past the colex pairs of PM modes (8 n_pg > NPR) are zero
+            for (int c0 = (NPR + 3) & ~3; c0 < 8 * n_pg; c0 += 4) {
+                const int k4 = c0 >> 2;
+                *reinterpret_cast<float4*>(sU + (k4 & 1) * hoff + (k4 >> 1) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int e = 0; e < 32; ++e) acc[e] += tmp[e];
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<float4*>(sMs + 4 * q) =
+                    make_float4(q * 4 + 0 < PM ? cur[q * 4 + 0] : 0.f, q * 4 + 1 < PM ? cur[q * 4 + 1] : 0.f,
+                                q * 4 + 2 < PM ? cur[q * 4 + 2] : 0.f, q * 4 + 3 < PM ? cur[q * 4 + 3] : 0.f);
+            named_arrive(1 + s, nthr);
+#pragma unroll
+            for (int p = 0; p <= PM; ++p) {
+                cur[p] = n1[p];
+                n1[p] = n2[p];
+            }
         }
-        __syncthreads();
+    } else {
+        // ------------------------------------------------ compute warps
+        const bool computes = lane < nl;
+        const int tpk = computes ? tiles[tile] : 0;
+        const int pg = tpk & 0xff, sq = tpk >> 8;
+        const int hoff = 4 * n_pg;
+        for (int k = 0; k < nch; ++k) {
+            const int s = k & 1;
+            named_sync(1 + s, nthr);
+            if (computes) {
+                const float* sU = smem + s * stage_floats;
+                const float* sMs = sU + CUB_TX * SU;
+                float tmp[32];
+#pragma unroll
+                for (int e = 0; e < 32; ++e) tmp[e] = 0.f;
+#pragma unroll 2
+                for (int xi = lane; xi < CUB_TX; xi += nl) {
+                    const float4 u0 = *reinterpret_cast<const float4*>(sU + xi * SU + pg * 4);
+                    const float4 u1 = *reinterpret_cast<const float4*>(sU + xi * SU + hoff + pg * 4);
+                    const float4 mv = *reinterpret_cast<const float4*>(sMs + xi * CUB_MS + sq * 4);
+                    const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+                    const float mm[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) tmp[i * 4 + q] = fmaf(u[i], mm[q], tmp[i * 4 + q]);
+                }
+#pragma unroll
+                for (int e = 0; e < 32; ++e) acc[e] += tmp[e];
+            }
+            if (k + 2 < nch) named_arrive(3 + s, nthr);
+        }
     }
-    float* red = smem;   // [CUB_LANES][ntiles][32]
-    if (computes) {
+    __syncthreads();
+    float* red = smem;   // [nl][ntiles][32]
+    if (tid < ncomp && lane < nl) {
 #pragma unroll
         for (int e = 0; e < 32; ++e) red[(lane * ntiles + tile) * 32 + e] = acc[e];
     }
@@ -94,31 +164,43 @@ k_cubic(int P, int SU, int SM, int ntiles, const int* __restrict__ tiles, const 
     for (int i = tid; i < ntiles * 32; i += nthr) {
         const int t = i / 32, e = i % 32;
         float v = 0.f;
-        for (int ln = 0; ln < CUB_LANES; ++ln) v += red[(ln * ntiles + t) * 32 + e];
+        for (int ln = 0; ln < nl; ++ln) v += red[(ln * ntiles + t) * 32 + e];
         const int tp = tiles[t];
-        const int c = (tp & 0xff) * 8 + e / 4, s = (tp >> 8) * 4 + e % 4;
-        const int n = modeidx[c * 16 + s];
+        const int c = (tp & 0xff) * 8 + e / 4, sv = (tp >> 8) * 4 + e % 4;
+        const int n = modeidx[c * 16 + sv];
         if (n >= 0) partial[((int64_t)b * gridDim.x + blockIdx.x) * n_max + n] = (double)v;
     }
 }
 
+static int cubic_lanes(const Plan& pl) { return std::max(1, std::min(8, CUB_MAXCOMP / pl.n_tiles)); }
+
 static size_t cubic_smem(const Plan& pl) {
-    const size_t tilebuf = (size_t)CUB_TX * (pl.n_pg * 8 + pl.n_sq * 4 + 1) * 4;
-    const size_t redbuf = (size_t)CUB_LANES * pl.n_tiles * 32 * 4;
+    const size_t SU = 8 * (size_t)pl.n_pg + 4;
+    const size_t tilebuf = 2 * (size_t)CUB_TX * (SU + CUB_MS) * 4;
+    const size_t redbuf = (size_t)cubic_lanes(pl) * pl.n_tiles * 32 * 4;
     return tilebuf > redbuf ? tilebuf : redbuf;
+}
+
+template <int PM>
+static cudaError_t launch_cubic_pm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st) {
+    const int nl = cubic_lanes(pl);
+    const int ncomp = ((pl.n_tiles * nl + 31) / 32) * 32;
+    const size_t smem = cubic_smem(pl);
+    cudaError_t e = cudaFuncSetAttribute(k_cubic<PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t ppc = ((pl.npix + pl.cubic_ctas - 1) / pl.cubic_ctas + CUB_TX - 1) / CUB_TX * CUB_TX;
+    dim3 grid(pl.cubic_ctas, B);
+    k_cubic<PM><<<grid, ncomp + CUB_TX, smem, st>>>(pl.P, pl.n_pg, pl.n_tiles, nl, ncomp, pl.tiles, pl.modeidx,
+                                                    pl.npix, ppc, maps, pl.W, partial, pl.n_max);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
-    const int nthr = ((pl.n_tiles * CUB_LANES + 31) / 32) * 32;
-    const size_t smem = cubic_smem(pl);
-    cudaError_t e = cudaFuncSetAttribute(k_cubic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int64_t ppc = ((pl.npix + pl.cubic_ctas - 1) / pl.cubic_ctas + CUB_TX - 1) / CUB_TX * CUB_TX;
-    dim3 grid(pl.cubic_ctas, B);
-    k_cubic<<<grid, nthr, smem, st>>>(pl.P, pl.n_pg * 8, pl.n_sq * 4, pl.n_tiles, pl.tiles, pl.pair_ab, pl.modeidx,
-                                      pl.npix, ppc, maps, pl.W, partial, pl.n_max);
-    return cudaGetLastError();
+    if (pl.n_tiles > CUB_MAXCOMP) return cudaErrorInvalidValue;
+    if (pl.P <= 4) return launch_cubic_pm<4>(pl, maps, B, partial, st);
+    if (pl.P <= 8) return launch_cubic_pm<8>(pl, maps, B, partial, st);
+    return launch_cubic_pm<16>(pl, maps, B, partial, st);
 }
 
 // ---------------------------------------------------------------- linear term GEMM
@@ -305,110 +387,164 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
 }
 
 // In place: maps[b][t][x] <- U_t(x) = W_x sum_c hk[b][t][c] (M_a M_b' - <c>_x).
-// A block handles AU_MB maps for a range of pixels, so the pair-mean panel <c>_x is
-// read once per AU_MB maps.  One thread per pixel; the maps' values sit in a
-// shared-memory column; pairs are taken 8 at a time and each weight row is read as
-// two float4 (4 FMAs per shared load).
+// Register tile per thread: AU_NX adjacent pixels x AU_NB maps, all PM values of each
+// map in registers.  The pair loop runs over a (outer, dynamic) and b' >= a (inner,
+// unrolled), so that M_b' is a register and M_a comes from a shared-memory copy of the
+// tile; each pair costs four broadcast float4 loads of the weights per map and one
+// 8-byte load of the pair means for 16 AU_NX AU_NB FMAs.  The pair-mean row of a + 1 is
+// copied into shared memory (cp.async, each thread its own pixels) while row a is being
+// used.  A CTA keeps its AU_NB maps' weights in shared memory and walks pixel tiles
+// g, g + G, ...; CTAs of the same g but different map pairs are adjacent in launch
+// order, so they read the same pair-mean rows close together in time.
 constexpr int AU_THREADS = 128;
-constexpr int AU_MB = 4;
-constexpr int AU_SC = 136;                  // pairs padded to a multiple of 8 (P <= 16)
+constexpr int AU_NX = 2;                    // adjacent pixels per thread
+constexpr int AU_NB = 2;                    // maps per thread (and per CTA)
+constexpr int AU_TILE = AU_THREADS * AU_NX; // pixels per CTA tile
 
-__global__ void __launch_bounds__(AU_THREADS)
-k_adjoint_u(int P, int n_pair, int B, int64_t npix, const float* __restrict__ hk, const float* __restrict__ pm,
-            const float* __restrict__ W, float* __restrict__ maps) {
+__device__ __forceinline__ void cp_async8(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <int PM>
+__global__ void __launch_bounds__(AU_THREADS, 2)
+k_adjoint_u(int P, int n_pair, int B, int ngroups, int64_t npix, const float* __restrict__ hk,
+            const float* __restrict__ pm, const float* __restrict__ W, float* __restrict__ maps) {
+    constexpr int NPM = PM * (PM + 1) / 2;
     extern __shared__ __align__(16) float au_smem[];
-    float* sH = au_smem;                                     // [AU_MB][MAXP][AU_SC]
-    float* sM = sH + AU_MB * MODAL_MAXP * AU_SC;            // [AU_MB][MAXP][AU_THREADS]
-    __shared__ int s_pa[AU_SC], s_pb[AU_SC];
+    float* sH = au_smem;                                   // [AU_NB][NPM][PM], pairs in PM-lex order
+    float* sM = sH + AU_NB * NPM * PM;                     // [AU_NB][PM][AU_TILE]
+    float* sP = sM + AU_NB * PM * AU_TILE;                 // [2][PM][AU_TILE] pair-mean rows
     const int tid = threadIdx.x;
-    const int b0 = blockIdx.y * AU_MB;
-    const int nb = min(AU_MB, B - b0);
-    for (int i = tid; i < AU_MB * MODAL_MAXP * AU_SC; i += AU_THREADS) {
-        const int mb = i / (MODAL_MAXP * AU_SC), rem = i % (MODAL_MAXP * AU_SC);
-        const int t = rem / AU_SC, c = rem % AU_SC;
-        sH[i] = (mb < nb && t < P && c < n_pair) ? hk[((int64_t)(b0 + mb) * P + t) * n_pair + c] : 0.f;
+    const int nmp = (B + AU_NB - 1) / AU_NB;
+    const int mp = blockIdx.x % nmp;
+    const int g = blockIdx.x / nmp;
+    const int b0 = mp * AU_NB;
+    const int nb = min(AU_NB, B - b0);
+    for (int i = tid; i < AU_NB * NPM * PM; i += AU_THREADS) {
+        const int mb = i / (NPM * PM), rem = i % (NPM * PM);
+        const int k = rem / PM, t = rem % PM;
+        int a = 0, kk = k;
+        while (kk >= PM - a) { kk -= PM - a; ++a; }
+        const int bb = a + kk;
+        float v = 0.f;
+        if (mb < nb && t < P && bb < P) v = hk[((int64_t)(b0 + mb) * P + t) * n_pair + pair_lex(a, bb, P)];
+        sH[i] = v;
     }
-    for (int c = tid; c < AU_SC; c += AU_THREADS) {
-        int pa = 0, pb = 0;
-        if (c < n_pair) {
-            int cc = c;
-            while (cc >= P - pa) { cc -= P - pa; ++pa; }
-            pb = pa + cc;
-        }
-        s_pa[c] = pa;
-        s_pb[c] = pb;
-    }
-    for (int i = tid; i < AU_MB * MODAL_MAXP * AU_THREADS; i += AU_THREADS) sM[i] = 0.f;
     __syncthreads();
-    const float4* H4 = reinterpret_cast<const float4*>(sH);
-    for (int64_t x0 = (int64_t)blockIdx.x * AU_THREADS; x0 < npix; x0 += (int64_t)gridDim.x * AU_THREADS) {
-        const int64_t x = x0 + tid;
-        const bool in = x < npix;
-        for (int mb = 0; mb < nb; ++mb)
-            for (int p = 0; p < P; ++p)
-                sM[(mb * MODAL_MAXP + p) * AU_THREADS + tid] = in ? maps[((int64_t)(b0 + mb) * P + p) * npix + x] : 0.f;
-        float u[AU_MB][MODAL_MAXP];
-#pragma unroll
-        for (int mb = 0; mb < AU_MB; ++mb)
-#pragma unroll
-            for (int t = 0; t < MODAL_MAXP; ++t) u[mb][t] = 0.f;
-        for (int c0 = 0; c0 < n_pair; c0 += 8) {
-            float pv[8];
-            int pa[8], pb[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int c = c0 + i;
-                pa[i] = s_pa[c];
-                pb[i] = s_pb[c];
-                pv[i] = (pm && in && c < n_pair) ? pm[(int64_t)c * npix + x] : 0.f;
+    const int64_t ntile = (npix + AU_TILE - 1) / AU_TILE;
+    const int px = AU_NX * tid;                            // this thread's pixels within a tile
+    for (int64_t tile = g; tile < ntile; tile += ngroups) {
+        const int64_t x0 = tile * AU_TILE;
+        const bool in = x0 + px < npix;                    // npix is even: both pixels or neither
+        // pair-mean row of a into stage a & 1 (rows b' = a .. P-1 of this thread's pixels)
+        auto issue_row = [&](int a) {
+            if (pm && in) {
+                const int crow = a * P - a * (a - 1) / 2 - a;
+                float* dst = sP + (a & 1) * PM * AU_TILE + px;
+                for (int bb = a; bb < P; ++bb) cp_async8(dst + bb * AU_TILE, pm + (int64_t)(crow + bb) * npix + x0 + px);
             }
+            cp_async_commit();
+        };
+        issue_row(0);
+        float M[AU_NB][AU_NX][PM];
 #pragma unroll
-            for (int mb = 0; mb < AU_MB; ++mb) {
-                float y[8];
+        for (int i = 0; i < AU_NB; ++i)
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    y[i] = (c0 + i < n_pair)
-                               ? sM[(mb * MODAL_MAXP + pa[i]) * AU_THREADS + tid] * sM[(mb * MODAL_MAXP + pb[i]) * AU_THREADS + tid] - pv[i]
-                               : 0.f;
+            for (int p = 0; p < PM; ++p) {
+                float2 v = make_float2(0.f, 0.f);
+                if (i < nb && p < P && in) v = *reinterpret_cast<const float2*>(maps + ((int64_t)(b0 + i) * P + p) * npix + x0 + px);
+                M[i][0][p] = v.x;
+                M[i][1][p] = v.y;
+                *reinterpret_cast<float2*>(sM + (i * PM + p) * AU_TILE + px) = v;
+            }
+        float u[AU_NB][AU_NX][PM];
 #pragma unroll
-                for (int t = 0; t < MODAL_MAXP; ++t) {
-                    const int h = ((mb * MODAL_MAXP + t) * AU_SC + c0) / 4;
-                    const float4 h0 = H4[h], h1 = H4[h + 1];
-                    u[mb][t] = fmaf(h0.x, y[0], u[mb][t]);
-                    u[mb][t] = fmaf(h0.y, y[1], u[mb][t]);
-                    u[mb][t] = fmaf(h0.z, y[2], u[mb][t]);
-                    u[mb][t] = fmaf(h0.w, y[3], u[mb][t]);
-                    u[mb][t] = fmaf(h1.x, y[4], u[mb][t]);
-                    u[mb][t] = fmaf(h1.y, y[5], u[mb][t]);
-                    u[mb][t] = fmaf(h1.z, y[6], u[mb][t]);
-                    u[mb][t] = fmaf(h1.w, y[7], u[mb][t]);
+        for (int i = 0; i < AU_NB; ++i)
+#pragma unroll
+            for (int j = 0; j < AU_NX; ++j)
+#pragma unroll
+                for (int t = 0; t < PM; ++t) u[i][j][t] = 0.f;
+        // sM and sP entries are written (or copied in) and read by the same thread only
+        for (int a = 0; a < P; ++a) {
+            if (a + 1 < P) issue_row(a + 1);
+            else cp_async_commit();
+            cp_async_wait1();                              // row a has landed
+            float Ma[AU_NB][AU_NX];
+#pragma unroll
+            for (int i = 0; i < AU_NB; ++i) {
+                const float2 v = *reinterpret_cast<const float2*>(sM + (i * PM + a) * AU_TILE + px);
+                Ma[i][0] = v.x;
+                Ma[i][1] = v.y;
+            }
+            const float* prow = sP + (a & 1) * PM * AU_TILE + px;
+            const int krow = a * PM - a * (a - 1) / 2 - a;         // PM-lex index of (a, b') is krow + b'
+#pragma unroll
+            for (int bb = 0; bb < PM; ++bb) {
+                if (bb < a || bb >= P) continue;
+                float2 pv = make_float2(0.f, 0.f);
+                if (pm && in) pv = *reinterpret_cast<const float2*>(prow + bb * AU_TILE);
+#pragma unroll
+                for (int i = 0; i < AU_NB; ++i) {
+                    const float y0 = fmaf(Ma[i][0], M[i][0][bb], -pv.x);
+                    const float y1 = fmaf(Ma[i][1], M[i][1][bb], -pv.y);
+                    const float4* h4 = reinterpret_cast<const float4*>(sH + (i * NPM + krow + bb) * PM);
+#pragma unroll
+                    for (int q = 0; q < PM / 4; ++q) {
+                        const float4 h = h4[q];
+                        u[i][0][4 * q + 0] = fmaf(h.x, y0, u[i][0][4 * q + 0]);
+                        u[i][0][4 * q + 1] = fmaf(h.y, y0, u[i][0][4 * q + 1]);
+                        u[i][0][4 * q + 2] = fmaf(h.z, y0, u[i][0][4 * q + 2]);
+                        u[i][0][4 * q + 3] = fmaf(h.w, y0, u[i][0][4 * q + 3]);
+                        u[i][1][4 * q + 0] = fmaf(h.x, y1, u[i][1][4 * q + 0]);
+                        u[i][1][4 * q + 1] = fmaf(h.y, y1, u[i][1][4 * q + 1]);
+                        u[i][1][4 * q + 2] = fmaf(h.z, y1, u[i][1][4 * q + 2]);
+                        u[i][1][4 * q + 3] = fmaf(h.w, y1, u[i][1][4 * q + 3]);
+                    }
                 }
             }
         }
         if (in) {
-            const float wx = W[x];
+            const float2 wx = *reinterpret_cast<const float2*>(W + x0 + px);
 #pragma unroll
-            for (int mb = 0; mb < AU_MB; ++mb)
+            for (int i = 0; i < AU_NB; ++i)
 #pragma unroll
-                for (int t = 0; t < MODAL_MAXP; ++t)
-                    if (mb < nb && t < P) maps[((int64_t)(b0 + mb) * P + t) * npix + x] = wx * u[mb][t];
+                for (int t = 0; t < PM; ++t)
+                    if (i < nb && t < P)
+                        *reinterpret_cast<float2*>(maps + ((int64_t)(b0 + i) * P + t) * npix + x0 + px) =
+                            make_float2(wx.x * u[i][0][t], wx.y * u[i][1][t]);
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <int PM>
+static cudaError_t launch_adjoint_u_pm(Plan& pl, int B, const float* hk, const float* pm, float* maps,
+                                       cudaStream_t st) {
+    constexpr int NPM = PM * (PM + 1) / 2;
+    const size_t smem = ((size_t)AU_NB * NPM * PM + (size_t)(AU_NB + 2) * PM * AU_TILE) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint_u<PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nmp = (B + AU_NB - 1) / AU_NB;
+    const int64_t ntile = (pl.npix + AU_TILE - 1) / AU_TILE;
+    // two resident CTAs per SM in total, every map pair in every group
+    int64_t ng = std::max<int64_t>(1, (152 * 2) / nmp);
+    ng = std::min<int64_t>(ng, ntile);
+    k_adjoint_u<PM><<<(unsigned)(ng * nmp), AU_THREADS, smem, st>>>(pl.P, pl.n_pair, B, (int)ng, pl.npix, hk, pm,
+                                                                    pl.W, maps);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_u(Plan& pl, const float* /*maps_in*/, int B, const float* hk, int use_linear, float* maps,
                              cudaStream_t st) {
     if (B == 0) return cudaSuccess;
-    const size_t smem = (size_t)AU_MB * MODAL_MAXP * (AU_SC + AU_THREADS) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_adjoint_u, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int64_t nblk = (pl.npix + AU_THREADS - 1) / AU_THREADS;
-    const int ng = (B + AU_MB - 1) / AU_MB;
-    const int64_t want = (152 * 8 + ng - 1) / ng;            // about 8 blocks per SM in total
-    dim3 grid((unsigned)std::min<int64_t>(nblk, std::max<int64_t>(want, 152)), ng);
+    if (pl.npix % 2 != 0) return cudaErrorInvalidValue;
     const float* pm = use_linear ? pl.pair_mean : nullptr;
-    k_adjoint_u<<<grid, AU_THREADS, smem, st>>>(pl.P, pl.n_pair, B, pl.npix, hk, pm, pl.W, maps);
-    return cudaGetLastError();
+    if (pl.P <= 4) return launch_adjoint_u_pm<4>(pl, B, hk, pm, maps, st);
+    if (pl.P <= 8) return launch_adjoint_u_pm<8>(pl, B, hk, pm, maps, st);
+    return launch_adjoint_u_pm<16>(pl, B, hk, pm, maps, st);
 }
 
 }  // namespace modal

@@ -26,6 +26,7 @@ namespace modal {
 
 constexpr int FFT_THREADS = 1024;
 constexpr int FFT_ELEMS = 16384;                 // complex elements per CTA (all transforms)
+constexpr int FFT_LB = 4;                        // loads batched per thread
 
 __host__ __device__ inline int fft_rings_per_block(int N) { return FFT_ELEMS / N; }
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
@@ -119,13 +120,11 @@ __device__ __forceinline__ void dft(float2* x) {
 // One Stockham pass of radix R at sub-transform length Ns over the transform at `buf`
 // (padded indices).  Thread tl (0 <= tl < T = N / 16) handles butterflies j = tl + T u.
 template <int SIGN, int R>
-__device__ __forceinline__ void stockham_pass(float2* buf, int N, int log2N, int Ns, int log2Ns, int tl,
+__device__ __forceinline__ void stockham_pass(float2* buf, int N, int Ns, int log2Ns, int tl,
                                               const float2* __restrict__ tw) {
     constexpr int NB = 16 / R;                   // butterflies per thread
-    constexpr int LR = (R == 16) ? 4 : (R == 8) ? 3 : (R == 4) ? 2 : 1;
     const int T = N >> 4;
     const int NR = N / R;
-    const int lstride = log2N - log2Ns - LR;     // twiddle index step for r * k is 2^lstride
     float2 v[16];
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
@@ -135,7 +134,7 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int N, int log2N, int
         for (int r = 0; r < R; ++r) {
             float2 x = buf[pad16(j + r * NR)];
             if (r > 0 && Ns > 1) {
-                float2 w = __ldg(&tw[(r * k) << lstride]);
+                float2 w = __ldg(&tw[(r - 1) * Ns + k]);
                 if (SIGN < 0) w.y = -w.y;
                 x = cmul(x, w);
             }
@@ -155,18 +154,23 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int N, int log2N, int
     __syncthreads();
 }
 
+// Twiddle table, one block per pass in pass order: for the pass of radix R at
+// sub-transform length Ns, entries (r - 1) Ns + k = e^{2 pi i r k / (R Ns)}, r = 1..R-1,
+// k = 0..Ns-1 (N - 1 entries in all), so that the threads of a warp read consecutive
+// entries.
 template <int SIGN>
 __device__ void fft_transform(float2* buf, int N, int log2N, int tl, const float2* __restrict__ tw) {
     int Ns = 1, log2Ns = 0;
     while (log2N - log2Ns >= 4) {
-        stockham_pass<SIGN, 16>(buf, N, log2N, Ns, log2Ns, tl, tw);
+        stockham_pass<SIGN, 16>(buf, N, Ns, log2Ns, tl, tw);
+        tw += 15 * Ns;
         Ns <<= 4;
         log2Ns += 4;
     }
     const int rem = log2N - log2Ns;
-    if (rem == 3) stockham_pass<SIGN, 8>(buf, N, log2N, Ns, log2Ns, tl, tw);
-    else if (rem == 2) stockham_pass<SIGN, 4>(buf, N, log2N, Ns, log2Ns, tl, tw);
-    else if (rem == 1) stockham_pass<SIGN, 2>(buf, N, log2N, Ns, log2Ns, tl, tw);
+    if (rem == 3) stockham_pass<SIGN, 8>(buf, N, Ns, log2Ns, tl, tw);
+    else if (rem == 2) stockham_pass<SIGN, 4>(buf, N, Ns, log2Ns, tl, tw);
+    else if (rem == 1) stockham_pass<SIGN, 2>(buf, N, Ns, log2Ns, tl, tw);
 }
 
 // grid: (ceil(R_half / RPB), nmp); nmp = number of (map, p) rows.
@@ -187,20 +191,35 @@ k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __r
         buf[q * NP + pad16(k)] = make_float2(0.f, 0.f);
     }
     const float2* d = delta + (int64_t)mp * (L + 1) * 2 * RH;
-    for (int i = threadIdx.x; i < (L + 1) * RPB; i += FFT_THREADS) {
-        const int m = i / RPB, q = i % RPB;
-        float2 e = make_float2(0.f, 0.f), o = e;
-        if (q < ntr) {
-            e = d[(int64_t)m * 2 * RH + j0 + q];
-            o = d[(int64_t)m * 2 * RH + RH + j0 + q];
+    // FFT_LB rows of (m, ring pair) per thread are loaded before any is stored, so that
+    // 2 FFT_LB loads per thread are in flight.
+    const int nitem = (L + 1) * RPB;
+    for (int i0 = threadIdx.x; i0 < nitem; i0 += FFT_LB * FFT_THREADS) {
+        float2 e[FFT_LB], o[FFT_LB];
+#pragma unroll
+        for (int u = 0; u < FFT_LB; ++u) {
+            const int i = i0 + u * FFT_THREADS;
+            const int m = i / RPB, q = i % RPB;
+            e[u] = make_float2(0.f, 0.f);
+            o[u] = e[u];
+            if (i < nitem && q < ntr) {
+                e[u] = d[(int64_t)m * 2 * RH + j0 + q];
+                o[u] = d[(int64_t)m * 2 * RH + RH + j0 + q];
+            }
         }
-        const float2 dn = cadd(e, o), ds = csub(e, o);
-        float2* b = buf + q * NP;
-        if (m == 0) {
-            b[0] = make_float2(dn.x, ds.x);
-        } else {
-            b[pad16(m)] = make_float2(dn.x - ds.y, dn.y + ds.x);       // X_n + i X_s
-            b[pad16(N - m)] = make_float2(dn.x + ds.y, ds.x - dn.y);   // conj(X_n) + i conj(X_s)
+#pragma unroll
+        for (int u = 0; u < FFT_LB; ++u) {
+            const int i = i0 + u * FFT_THREADS;
+            if (i >= nitem) break;
+            const int m = i / RPB, q = i % RPB;
+            const float2 dn = cadd(e[u], o[u]), ds = csub(e[u], o[u]);
+            float2* b = buf + q * NP;
+            if (m == 0) {
+                b[0] = make_float2(dn.x, ds.x);
+            } else {
+                b[pad16(m)] = make_float2(dn.x - ds.y, dn.y + ds.x);       // X_n + i X_s
+                b[pad16(N - m)] = make_float2(dn.x + ds.y, ds.x - dn.y);   // conj(X_n) + i conj(X_s)
+            }
         }
     }
     __syncthreads();
@@ -230,19 +249,31 @@ k_ring_r2c(int L, int R, int R_half, int RH, int N, int log2N, const float* __re
     const int j0 = blockIdx.x * RPB;
     const int ntr = min(RPB, R_half - j0);
     const float* in = maps + (int64_t)mp * R * N;
-    for (int qq = 0; qq < RPB; ++qq) {
-        const int jn = j0 + qq, js = R - 1 - jn;
-        float2* b = buf + qq * NP;
-        if (qq >= ntr) {
-            for (int k = threadIdx.x; k < N; k += FFT_THREADS) b[pad16(k)] = make_float2(0.f, 0.f);
-            continue;
+    // (ring pair, k) items, FFT_LB per thread loaded before any is stored.
+    const int nitem = RPB * N;
+    for (int i0 = threadIdx.x; i0 < nitem; i0 += FFT_LB * FFT_THREADS) {
+        float xn[FFT_LB], xs[FFT_LB];
+#pragma unroll
+        for (int u = 0; u < FFT_LB; ++u) {
+            const int i = i0 + u * FFT_THREADS;
+            const int qq = i / N, k = i % N;
+            const int jn = j0 + qq, js = R - 1 - jn;
+            xn[u] = 0.f;
+            xs[u] = 0.f;
+            if (i < nitem && qq < ntr) {
+                xn[u] = in[(int64_t)jn * N + k];
+                if (js != jn) xs[u] = in[(int64_t)js * N + k];
+            }
         }
-        const float wn = ring_weight ? ring_weight[jn] : 1.f;
-        const float ws = ring_weight ? ring_weight[js] : 1.f;
-        for (int k = threadIdx.x; k < N; k += FFT_THREADS) {
-            const float xn = wn * in[(int64_t)jn * N + k];
-            const float xs = (js != jn) ? ws * in[(int64_t)js * N + k] : 0.f;
-            b[pad16(k)] = make_float2(xn, xs);
+#pragma unroll
+        for (int u = 0; u < FFT_LB; ++u) {
+            const int i = i0 + u * FFT_THREADS;
+            if (i >= nitem) break;
+            const int qq = i / N, k = i % N;
+            const int jn = j0 + qq, js = R - 1 - jn;
+            const float wn = (ring_weight && qq < ntr) ? ring_weight[jn] : 1.f;
+            const float ws = (ring_weight && qq < ntr) ? ring_weight[js] : 1.f;
+            buf[qq * NP + pad16(k)] = make_float2(wn * xn[u], ws * xs[u]);
         }
     }
     __syncthreads();

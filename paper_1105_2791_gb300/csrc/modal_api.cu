@@ -379,10 +379,25 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
         CKI(cudaMemcpy(pl->W, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice), "weights copy");
         CKI(dalloc(pl, &pl->wring, wr.size()), "ring weights");
         CKI(cudaMemcpy(pl->wring, wr.data(), wr.size() * sizeof(float), cudaMemcpyHostToDevice), "ring weights copy");
-        std::vector<float2> tw(pl->nphi);
-        for (int k = 0; k < pl->nphi; ++k) {
-            const double a = 2.0 * M_PI * k / pl->nphi;
-            tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        // per-pass twiddles of the ring FFT: radix-16 passes, then one of radix 8, 4 or 2;
+        // pass (R, Ns) holds e^{2 pi i r k / (R Ns)} at (r - 1) Ns + k
+        std::vector<float2> tw(pl->nphi, make_float2(0.f, 0.f));
+        {
+            int lg = 0;
+            while ((1 << lg) < pl->nphi) ++lg;
+            size_t off = 0;
+            for (int Ns = 1, left = lg; left > 0;) {
+                const int lr = left >= 4 ? 4 : left;
+                const int R = 1 << lr;
+                for (int r = 1; r < R; ++r)
+                    for (int k = 0; k < Ns; ++k) {
+                        const double a = 2.0 * M_PI * (double)(r * k) / (double)(R * Ns);
+                        tw[off + (size_t)(r - 1) * Ns + k] = make_float2((float)std::cos(a), (float)std::sin(a));
+                    }
+                off += (size_t)(R - 1) * Ns;
+                Ns *= R;
+                left -= lr;
+            }
         }
         CKI(dalloc(pl, &pl->twiddle, tw.size()), "twiddles");
         CKI(cudaMemcpy(pl->twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice), "twiddles copy");
