@@ -133,23 +133,34 @@ k_cubic(int P, int n_pg, int ntiles, int nl, int ncomp, const int* __restrict__ 
             if (computes) {
                 const float* sU = smem + s * stage_floats;
                 const float* sMs = sU + CUB_TX * SU;
-                float tmp[32];
+                // packed FP32 pairs (one rounding per lane, as fmaf): tmp2[ip][q] holds the
+                // sums of pairs 2 ip and 2 ip + 1 against s = 4 sq + q
+                float2 tmp2[4][4];
 #pragma unroll
-                for (int e = 0; e < 32; ++e) tmp[e] = 0.f;
+                for (int ip = 0; ip < 4; ++ip)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) tmp2[ip][q] = make_float2(0.f, 0.f);
 #pragma unroll 2
                 for (int xi = lane; xi < CUB_TX; xi += nl) {
                     const float4 u0 = *reinterpret_cast<const float4*>(sU + xi * SU + pg * 4);
                     const float4 u1 = *reinterpret_cast<const float4*>(sU + xi * SU + hoff + pg * 4);
                     const float4 mv = *reinterpret_cast<const float4*>(sMs + xi * CUB_MS + sq * 4);
-                    const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-                    const float mm[4] = {mv.x, mv.y, mv.z, mv.w};
+                    const float2 u2[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                                          make_float2(u1.z, u1.w)};
+                    const float2 m2[4] = {make_float2(mv.x, mv.x), make_float2(mv.y, mv.y), make_float2(mv.z, mv.z),
+                                          make_float2(mv.w, mv.w)};
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
+                    for (int ip = 0; ip < 4; ++ip)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) tmp[i * 4 + q] = fmaf(u[i], mm[q], tmp[i * 4 + q]);
+                        for (int q = 0; q < 4; ++q) tmp2[ip][q] = __ffma2_rn(u2[ip], m2[q], tmp2[ip][q]);
                 }
 #pragma unroll
-                for (int e = 0; e < 32; ++e) acc[e] += tmp[e];
+                for (int ip = 0; ip < 4; ++ip)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        acc[(2 * ip) * 4 + q] += tmp2[ip][q].x;
+                        acc[(2 * ip + 1) * 4 + q] += tmp2[ip][q].y;
+                    }
             }
             if (k + 2 < nch) named_arrive(3 + s, nthr);
         }
@@ -301,48 +312,102 @@ cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* 
 }
 
 // ---------------------------------------------------------------- Monte Carlo pair means
+// Two threads per pixel: thread h (h = 0, 1, warp-uniform) owns the mode rows p = 2k + h,
+// k = 0 .. PM/2 - 1.  It works on its pixel's map values shifted by h (v[i] = M_{i+h}),
+// so that both threads run the same code with compile-time indices: its pairs are
+// (2k, r') in the shifted frame, r' >= 2k, i.e. (2k + h, r' + h).  The maps stream
+// through a PA_STAGES-deep ring in shared memory by cp.async (each thread copies and
+// reads only its own column, so no barrier is needed); the FP64 sums are read, updated
+// and written once per launch.
+constexpr int PA_THREADS = 128;             // 64 pixels x 2 row parities
+constexpr int PA_PIX = PA_THREADS / 2;
+constexpr int PA_STAGES = 5;               // PM = 16: 80 floats per column >= 72 sums
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
 template <int PM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(PA_THREADS)
 k_pair_accumulate(int P, int B, int64_t npix, const float* __restrict__ maps, double* __restrict__ sums) {
-    constexpr int NPM = PM * (PM + 1) / 2;
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < npix; x += (int64_t)gridDim.x * blockDim.x) {
-        float acc[NPM];
+    constexpr int NACC = (PM / 2) * (PM / 2 + 1);                // sum over k of (PM - 2k)
+    static_assert(NACC <= PA_STAGES * PM, "the sums must fit one ring column");
+    extern __shared__ __align__(16) float pa_ring[];            // [PA_STAGES][PM][PA_THREADS]
+    const int tid = threadIdx.x;
+    const int h = tid / PA_PIX, xl = tid % PA_PIX;
+    const int nv = P - h;                                       // shifted values that exist
+    for (int64_t x0 = (int64_t)blockIdx.x * PA_PIX; x0 < npix; x0 += (int64_t)gridDim.x * PA_PIX) {
+        const int64_t x = x0 + xl;
+        const bool in = x < npix;
+        auto issue = [&](int b) {
+            if (b < B && in) {
+                const float* src = maps + ((int64_t)b * P + h) * npix + x;
+                float* dst = pa_ring + (b % PA_STAGES) * PM * PA_THREADS + tid;
+                for (int i = 0; i < nv; ++i) {
+                    cp_async4(dst, src);
+                    src += npix;
+                    dst += PA_THREADS;
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
 #pragma unroll
-        for (int c = 0; c < NPM; ++c) acc[c] = 0.f;
+        for (int b = 0; b < PA_STAGES - 1; ++b) issue(b);
+        float acc[NACC];
+#pragma unroll
+        for (int c = 0; c < NACC; ++c) acc[c] = 0.f;
+#pragma unroll 1
         for (int b = 0; b < B; ++b) {
-            float mv[PM];
+            issue(b + PA_STAGES - 1);
+            asm volatile("cp.async.wait_group %0;" ::"n"(PA_STAGES - 1) : "memory");   // map b has landed
+            const float* col = pa_ring + (b % PA_STAGES) * PM * PA_THREADS + tid;
+            float v[PM];
 #pragma unroll
-            for (int p = 0; p < PM; ++p) mv[p] = (p < P) ? maps[((int64_t)b * P + p) * npix + x] : 0.f;
+            for (int i = 0; i < PM; ++i) v[i] = (i < nv && in) ? col[i * PA_THREADS] : 0.f;
             int c = 0;
 #pragma unroll
-            for (int p = 0; p < PM; ++p)
+            for (int k = 0; k < PM / 2; ++k)
 #pragma unroll
-                for (int r = p; r < PM; ++r) {
-                    acc[c] = fmaf(mv[p], mv[r], acc[c]);
+                for (int r = 2 * k; r < PM; ++r) {
+                    acc[c] = fmaf(v[2 * k], v[r], acc[c]);
                     ++c;
                 }
         }
-        int c = 0;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        // the sums pass through this thread's own ring column (NACC <= PA_STAGES PM floats)
+        // so that the FP64 update below is a plain loop
+        float* mine = pa_ring + tid;
 #pragma unroll
-        for (int p = 0; p < PM; ++p)
-#pragma unroll
-            for (int r = p; r < PM; ++r) {
-                if (r < P) sums[(int64_t)pair_lex(p, r, P) * npix + x] += (double)acc[c];
-                ++c;
+        for (int c = 0; c < NACC; ++c) mine[c * PA_THREADS] = acc[c];
+        if (in) {
+            int c = 0;
+#pragma unroll 1
+            for (int k = 0; k < PM / 2; ++k) {
+                const int pa = 2 * k + h;
+                double* dst = sums + (int64_t)pair_lex(pa, pa, P) * npix + x;       // (pa, pa)
+                // rows hold an even number (PM - 2k) of sums: 8 read-modify-writes in flight
+#pragma unroll 4
+                for (int r = 2 * k; r < PM; r += 2, c += 2, dst += 2 * npix) {
+                    if (r + h < P) dst[0] += (double)mine[c * PA_THREADS];
+                    if (r + 1 + h < P) dst[npix] += (double)mine[(c + 1) * PA_THREADS];
+                }
             }
+        }
     }
 }
 
 cudaError_t launch_pair_accumulate(Plan& pl, const float* maps, int B, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
-    const int64_t nblk = (pl.npix + 127) / 128;
+    const int64_t nblk = (pl.npix + PA_PIX - 1) / PA_PIX;
     const int grid = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
     if (pl.P <= 4)
-        k_pair_accumulate<4><<<grid, 128, 0, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
+        k_pair_accumulate<4><<<grid, PA_THREADS, PA_STAGES * 4 * PA_THREADS * 4, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
     else if (pl.P <= 8)
-        k_pair_accumulate<8><<<grid, 128, 0, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
+        k_pair_accumulate<8><<<grid, PA_THREADS, PA_STAGES * 8 * PA_THREADS * 4, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
     else
-        k_pair_accumulate<16><<<grid, 128, 0, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
+        k_pair_accumulate<16><<<grid, PA_THREADS, PA_STAGES * 16 * PA_THREADS * 4, st>>>(pl.P, B, pl.npix, maps,
+                                                                                      pl.pair_sum);
     return cudaGetLastError();
 }
 
@@ -388,14 +453,14 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
 
 // In place: maps[b][t][x] <- U_t(x) = W_x sum_c hk[b][t][c] (M_a M_b' - <c>_x).
 // Register tile per thread: AU_NX adjacent pixels x AU_NB maps, all PM values of each
-// map in registers.  The pair loop runs over a (outer, dynamic) and b' >= a (inner,
-// unrolled), so that M_b' is a register and M_a comes from a shared-memory copy of the
-// tile; each pair costs four broadcast float4 loads of the weights per map and one
-// 8-byte load of the pair means for 16 AU_NX AU_NB FMAs.  The pair-mean row of a + 1 is
-// copied into shared memory (cp.async, each thread its own pixels) while row a is being
-// used.  A CTA keeps its AU_NB maps' weights in shared memory and walks pixel tiles
-// g, g + G, ...; CTAs of the same g but different map pairs are adjacent in launch
-// order, so they read the same pair-mean rows close together in time.
+// map in registers, accumulators packed in FP32 pairs over t.  Both pair loops (a, then
+// b' >= a) are unrolled at compile time, so every map value is a register and the body
+// has no branches; each pair costs four broadcast float4 loads of the weights per map
+// and one 8-byte load of the pair means for 8 AU_NX AU_NB packed FMAs.  The pair-mean
+// row of a + 1 is copied into shared memory (cp.async, each thread its own pixels) while
+// row a is being used.  A CTA keeps its AU_NB maps' weights in shared memory and walks
+// pixel tiles g, g + G, ...; CTAs of the same g but different map pairs are adjacent in
+// launch order, so they read the same pair-mean rows close together in time.
 constexpr int AU_THREADS = 128;
 constexpr int AU_NX = 2;                    // adjacent pixels per thread
 constexpr int AU_NB = 2;                    // maps per thread (and per CTA)
@@ -408,6 +473,57 @@ __device__ __forceinline__ void cp_async8(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Pair-mean row a (b' = a .. P-1 of this thread's two pixels) into stage a & 1.
+template <int PM>
+__device__ __forceinline__ void adj_issue_row(int a, const float* __restrict__ pm, bool in, int P, int64_t npix,
+                                              int64_t x0, int px, float* sP) {
+    if (pm && in) {
+        const int crow = a * P - a * (a - 1) / 2 - a;
+        float* dst = sP + (a & 1) * PM * AU_TILE + px;
+#pragma unroll
+        for (int bb = 0; bb < PM; ++bb)
+            if (bb >= a && bb < P) cp_async8(dst + bb * AU_TILE, pm + (int64_t)(crow + bb) * npix + x0 + px);
+    }
+    cp_async_commit();
+}
+
+// Row A of the pair loop (pairs (A, b'), b' >= A), then rows A+1 .. PM-1: a template
+// recursion, so that every map-value index is a compile-time constant.
+template <int PM, int A>
+__device__ __forceinline__ void adj_rows(const float2 (&M)[AU_NB][PM], float2 (&u)[AU_NB][AU_NX][PM / 2],
+                                         const float* sH, float* sP, const float* __restrict__ pm, bool in, int P,
+                                         int64_t npix, int64_t x0, int px) {
+    if constexpr (A < PM) {
+        constexpr int NPM = PM * (PM + 1) / 2;
+        if (A + 1 < PM) adj_issue_row<PM>(A + 1, pm, in, P, npix, x0, px, sP);
+        else cp_async_commit();
+        cp_async_wait1();                                  // row A has landed
+        const float* prow = sP + (A & 1) * PM * AU_TILE + px;
+#pragma unroll
+        for (int bb = A; bb < PM; ++bb) {
+            const float2 pv = *reinterpret_cast<const float2*>(prow + bb * AU_TILE);
+            const int k = A * PM - A * (A - 1) / 2 + (bb - A);  // PM-lex pair index
+#pragma unroll
+            for (int i = 0; i < AU_NB; ++i) {
+                const float y0 = fmaf(M[i][A].x, M[i][bb].x, -pv.x);
+                const float y1 = fmaf(M[i][A].y, M[i][bb].y, -pv.y);
+                const float2 y02 = make_float2(y0, y0), y12 = make_float2(y1, y1);
+                const float4* h4 = reinterpret_cast<const float4*>(sH + (i * NPM + k) * PM);
+#pragma unroll
+                for (int q = 0; q < PM / 4; ++q) {
+                    const float4 h = h4[q];
+                    const float2 hlo = make_float2(h.x, h.y), hhi = make_float2(h.z, h.w);
+                    u[i][0][2 * q] = __ffma2_rn(hlo, y02, u[i][0][2 * q]);
+                    u[i][0][2 * q + 1] = __ffma2_rn(hhi, y02, u[i][0][2 * q + 1]);
+                    u[i][1][2 * q] = __ffma2_rn(hlo, y12, u[i][1][2 * q]);
+                    u[i][1][2 * q + 1] = __ffma2_rn(hhi, y12, u[i][1][2 * q + 1]);
+                }
+            }
+        }
+        adj_rows<PM, A + 1>(M, u, sH, sP, pm, in, P, npix, x0, px);
+    }
+}
+
 template <int PM>
 __global__ void __launch_bounds__(AU_THREADS, 2)
 k_adjoint_u(int P, int n_pair, int B, int ngroups, int64_t npix, const float* __restrict__ hk,
@@ -415,14 +531,14 @@ k_adjoint_u(int P, int n_pair, int B, int ngroups, int64_t npix, const float* __
     constexpr int NPM = PM * (PM + 1) / 2;
     extern __shared__ __align__(16) float au_smem[];
     float* sH = au_smem;                                   // [AU_NB][NPM][PM], pairs in PM-lex order
-    float* sM = sH + AU_NB * NPM * PM;                     // [AU_NB][PM][AU_TILE]
-    float* sP = sM + AU_NB * PM * AU_TILE;                 // [2][PM][AU_TILE] pair-mean rows
+    float* sP = sH + AU_NB * NPM * PM;                     // [2][PM][AU_TILE] pair-mean rows
     const int tid = threadIdx.x;
     const int nmp = (B + AU_NB - 1) / AU_NB;
     const int mp = blockIdx.x % nmp;
     const int g = blockIdx.x / nmp;
     const int b0 = mp * AU_NB;
     const int nb = min(AU_NB, B - b0);
+    const int px = AU_NX * tid;                            // this thread's pixels within a tile
     for (int i = tid; i < AU_NB * NPM * PM; i += AU_THREADS) {
         const int mb = i / (NPM * PM), rem = i % (NPM * PM);
         const int k = rem / PM, t = rem % PM;
@@ -433,88 +549,48 @@ k_adjoint_u(int P, int n_pair, int B, int ngroups, int64_t npix, const float* __
         if (mb < nb && t < P && bb < P) v = hk[((int64_t)(b0 + mb) * P + t) * n_pair + pair_lex(a, bb, P)];
         sH[i] = v;
     }
+    // pair-mean rows that are never copied (b' >= P, or no linear term) read as zero
+#pragma unroll
+    for (int st = 0; st < 2; ++st)
+#pragma unroll
+        for (int bb = 0; bb < PM; ++bb)
+            if (!pm || bb >= P) *reinterpret_cast<float2*>(sP + (st * PM + bb) * AU_TILE + px) = make_float2(0.f, 0.f);
     __syncthreads();
     const int64_t ntile = (npix + AU_TILE - 1) / AU_TILE;
-    const int px = AU_NX * tid;                            // this thread's pixels within a tile
     for (int64_t tile = g; tile < ntile; tile += ngroups) {
         const int64_t x0 = tile * AU_TILE;
         const bool in = x0 + px < npix;                    // npix is even: both pixels or neither
-        // pair-mean row of a into stage a & 1 (rows b' = a .. P-1 of this thread's pixels)
-        auto issue_row = [&](int a) {
-            if (pm && in) {
-                const int crow = a * P - a * (a - 1) / 2 - a;
-                float* dst = sP + (a & 1) * PM * AU_TILE + px;
-                for (int bb = a; bb < P; ++bb) cp_async8(dst + bb * AU_TILE, pm + (int64_t)(crow + bb) * npix + x0 + px);
-            }
-            cp_async_commit();
-        };
-        issue_row(0);
-        float M[AU_NB][AU_NX][PM];
+        adj_issue_row<PM>(0, pm, in, P, npix, x0, px, sP);
+        float2 M[AU_NB][PM];                               // (pixel 0, pixel 1) per map and mode
 #pragma unroll
         for (int i = 0; i < AU_NB; ++i)
 #pragma unroll
             for (int p = 0; p < PM; ++p) {
                 float2 v = make_float2(0.f, 0.f);
                 if (i < nb && p < P && in) v = *reinterpret_cast<const float2*>(maps + ((int64_t)(b0 + i) * P + p) * npix + x0 + px);
-                M[i][0][p] = v.x;
-                M[i][1][p] = v.y;
-                *reinterpret_cast<float2*>(sM + (i * PM + p) * AU_TILE + px) = v;
+                M[i][p] = v;
             }
-        float u[AU_NB][AU_NX][PM];
+        float2 u[AU_NB][AU_NX][PM / 2];                    // (t = 2 tp, 2 tp + 1) packed
 #pragma unroll
         for (int i = 0; i < AU_NB; ++i)
 #pragma unroll
             for (int j = 0; j < AU_NX; ++j)
 #pragma unroll
-                for (int t = 0; t < PM; ++t) u[i][j][t] = 0.f;
-        // sM and sP entries are written (or copied in) and read by the same thread only
-        for (int a = 0; a < P; ++a) {
-            if (a + 1 < P) issue_row(a + 1);
-            else cp_async_commit();
-            cp_async_wait1();                              // row a has landed
-            float Ma[AU_NB][AU_NX];
-#pragma unroll
-            for (int i = 0; i < AU_NB; ++i) {
-                const float2 v = *reinterpret_cast<const float2*>(sM + (i * PM + a) * AU_TILE + px);
-                Ma[i][0] = v.x;
-                Ma[i][1] = v.y;
-            }
-            const float* prow = sP + (a & 1) * PM * AU_TILE + px;
-            const int krow = a * PM - a * (a - 1) / 2 - a;         // PM-lex index of (a, b') is krow + b'
-#pragma unroll
-            for (int bb = 0; bb < PM; ++bb) {
-                if (bb < a || bb >= P) continue;
-                float2 pv = make_float2(0.f, 0.f);
-                if (pm && in) pv = *reinterpret_cast<const float2*>(prow + bb * AU_TILE);
-#pragma unroll
-                for (int i = 0; i < AU_NB; ++i) {
-                    const float y0 = fmaf(Ma[i][0], M[i][0][bb], -pv.x);
-                    const float y1 = fmaf(Ma[i][1], M[i][1][bb], -pv.y);
-                    const float4* h4 = reinterpret_cast<const float4*>(sH + (i * NPM + krow + bb) * PM);
-#pragma unroll
-                    for (int q = 0; q < PM / 4; ++q) {
-                        const float4 h = h4[q];
-                        u[i][0][4 * q + 0] = fmaf(h.x, y0, u[i][0][4 * q + 0]);
-                        u[i][0][4 * q + 1] = fmaf(h.y, y0, u[i][0][4 * q + 1]);
-                        u[i][0][4 * q + 2] = fmaf(h.z, y0, u[i][0][4 * q + 2]);
-                        u[i][0][4 * q + 3] = fmaf(h.w, y0, u[i][0][4 * q + 3]);
-                        u[i][1][4 * q + 0] = fmaf(h.x, y1, u[i][1][4 * q + 0]);
-                        u[i][1][4 * q + 1] = fmaf(h.y, y1, u[i][1][4 * q + 1]);
-                        u[i][1][4 * q + 2] = fmaf(h.z, y1, u[i][1][4 * q + 2]);
-                        u[i][1][4 * q + 3] = fmaf(h.w, y1, u[i][1][4 * q + 3]);
-                    }
-                }
-            }
-        }
+                for (int tp = 0; tp < PM / 2; ++tp) u[i][j][tp] = make_float2(0.f, 0.f);
+        // sP entries are copied in and read by the same thread only
+        adj_rows<PM, 0>(M, u, sH, sP, pm, in, P, npix, x0, px);
         if (in) {
             const float2 wx = *reinterpret_cast<const float2*>(W + x0 + px);
 #pragma unroll
             for (int i = 0; i < AU_NB; ++i)
 #pragma unroll
                 for (int t = 0; t < PM; ++t)
-                    if (i < nb && t < P)
+                    if (i < nb && t < P) {
+                        const float u0 = (t & 1) ? u[i][0][t >> 1].y : u[i][0][t >> 1].x;
+                        const float u1 = (t & 1) ? u[i][1][t >> 1].y : u[i][1][t >> 1].x;
                         *reinterpret_cast<float2*>(maps + ((int64_t)(b0 + i) * P + t) * npix + x0 + px) =
-                            make_float2(wx.x * u[i][0][t], wx.y * u[i][1][t]);
+                            make_float2(wx.x * u0, wx.y * u1);
+                    }
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -524,7 +600,7 @@ template <int PM>
 static cudaError_t launch_adjoint_u_pm(Plan& pl, int B, const float* hk, const float* pm, float* maps,
                                        cudaStream_t st) {
     constexpr int NPM = PM * (PM + 1) / 2;
-    const size_t smem = ((size_t)AU_NB * NPM * PM + (size_t)(AU_NB + 2) * PM * AU_TILE) * sizeof(float);
+    const size_t smem = ((size_t)AU_NB * NPM * PM + (size_t)2 * PM * AU_TILE) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_adjoint_u<PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nmp = (B + AU_NB - 1) / AU_NB;

@@ -17,15 +17,16 @@
 // (T = N / 16 threads per transform): it loads them, applies the inter-pass twiddles
 // and a radix-R butterfly in registers (16 / R butterflies), and stores them; one
 // block-wide sync separates loads from stores.  Shared-memory index i is padded to
-// i + i / 16 to spread the strided stores over the banks.  A CTA of 1024 threads
-// holds 16384 / N transforms (four ring pairs at N = 4096), so the E/O rows and the
-// U~ rows move in full 32-byte sectors.
+// i + i / 16 to spread the strided stores over the banks.  A CTA of 512 threads holds
+// 8192 / N transforms (two ring pairs at N = 4096, 70 KB of shared memory), so that two
+// CTAs share an SM and one's global loads and stores overlap the other's passes; the
+// E/O rows and the U~ rows of neighbouring CTAs share 32-byte sectors, which L2 merges.
 #include "modal_internal.cuh"
 
 namespace modal {
 
-constexpr int FFT_THREADS = 1024;
-constexpr int FFT_ELEMS = 16384;                 // complex elements per CTA (all transforms)
+constexpr int FFT_THREADS = 512;
+constexpr int FFT_ELEMS = 8192;                  // complex elements per CTA (all transforms)
 constexpr int FFT_LB = 4;                        // loads batched per thread
 
 __host__ __device__ inline int fft_rings_per_block(int N) { return FFT_ELEMS / N; }
@@ -173,15 +174,21 @@ __device__ void fft_transform(float2* buf, int N, int log2N, int tl, const float
     else if (rem == 1) stockham_pass<SIGN, 2>(buf, N, Ns, log2Ns, tl, tw);
 }
 
+// Padded transform stride in float2: N + N/16 for the in-transform padding, + 4 so that
+// the transforms of one CTA start 8 banks apart (the (m, ring pair) loads and the
+// U~ reads, where the ring pair varies fastest, are then free of bank conflicts).
+__host__ __device__ inline int fft_stride(int N) { return N + (N >> 4) + 4; }
+
 // grid: (ceil(R_half / RPB), nmp); nmp = number of (map, p) rows.
 // delta layout [nmp][L+1][2][RH]: even (E) and odd (O) Legendre sums per ring pair;
 // north = E + O, south = E - O.
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, 2)
 k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __restrict__ delta,
            const float2* __restrict__ tw, float* __restrict__ maps) {
     extern __shared__ float2 buf[];
-    const int RPB = fft_rings_per_block(N);
-    const int NP = N + (N >> 4);                         // padded transform length
+    const int lgR = 13 - log2N;                          // RPB = 2^lgR transforms per CTA
+    const int RPB = 1 << lgR;
+    const int NP = fft_stride(N);
     const int mp = blockIdx.y;
     const int j0 = blockIdx.x * RPB;
     const int ntr = min(RPB, R_half - j0);
@@ -190,28 +197,29 @@ k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __r
         const int q = i / nzero, k = L + 1 + i % nzero;
         buf[q * NP + pad16(k)] = make_float2(0.f, 0.f);
     }
-    const float2* d = delta + (int64_t)mp * (L + 1) * 2 * RH;
-    // FFT_LB rows of (m, ring pair) per thread are loaded before any is stored, so that
+    const float2* d = delta + (int64_t)mp * (L + 1) * 2 * RH + j0;
+    // FFT_LB items (m, ring pair) per thread are loaded before any is stored, so that
     // 2 FFT_LB loads per thread are in flight.
-    const int nitem = (L + 1) * RPB;
+    const int nitem = (L + 1) << lgR;
     for (int i0 = threadIdx.x; i0 < nitem; i0 += FFT_LB * FFT_THREADS) {
         float2 e[FFT_LB], o[FFT_LB];
 #pragma unroll
         for (int u = 0; u < FFT_LB; ++u) {
             const int i = i0 + u * FFT_THREADS;
-            const int m = i / RPB, q = i % RPB;
+            const int m = i >> lgR, q = i & (RPB - 1);
             e[u] = make_float2(0.f, 0.f);
             o[u] = e[u];
             if (i < nitem && q < ntr) {
-                e[u] = d[(int64_t)m * 2 * RH + j0 + q];
-                o[u] = d[(int64_t)m * 2 * RH + RH + j0 + q];
+                const float2* dm = d + (int64_t)m * 2 * RH + q;
+                e[u] = dm[0];
+                o[u] = dm[RH];
             }
         }
 #pragma unroll
         for (int u = 0; u < FFT_LB; ++u) {
             const int i = i0 + u * FFT_THREADS;
             if (i >= nitem) break;
-            const int m = i / RPB, q = i % RPB;
+            const int m = i >> lgR, q = i & (RPB - 1);
             const float2 dn = cadd(e[u], o[u]), ds = csub(e[u], o[u]);
             float2* b = buf + q * NP;
             if (m == 0) {
@@ -226,63 +234,71 @@ k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __r
     const int T = N >> 4;
     const int q = threadIdx.x / T, tl = threadIdx.x % T;
     fft_transform<+1>(buf + q * NP, N, log2N, tl, tw);
+    // four consecutive longitudes per thread: four 8-byte shared loads, two 16-byte stores
     float* out = maps + (int64_t)mp * R * N;
-    for (int qq = 0; qq < ntr; ++qq) {
+    const int n4 = (ntr * N) >> 2;
+    for (int i = threadIdx.x; i < n4; i += FFT_THREADS) {
+        const int qq = (4 * i) >> log2N, k = (4 * i) & (N - 1);
         const int jn = j0 + qq, js = R - 1 - jn;
-        const float2* b = buf + qq * NP;
-        for (int k = threadIdx.x; k < N; k += FFT_THREADS) {
-            const float2 z = b[pad16(k)];
-            out[(int64_t)jn * N + k] = z.x;
-            if (js != jn) out[(int64_t)js * N + k] = z.y;
-        }
+        const float2* b = buf + qq * NP + pad16(k);      // k .. k+3 lie in one padded group of 16
+        const float2 z0 = b[0], z1 = b[1], z2 = b[2], z3 = b[3];
+        *reinterpret_cast<float4*>(out + (int64_t)jn * N + k) = make_float4(z0.x, z1.x, z2.x, z3.x);
+        if (js != jn) *reinterpret_cast<float4*>(out + (int64_t)js * N + k) = make_float4(z0.y, z1.y, z2.y, z3.y);
     }
 }
 
 // grid: (ceil(R_half / RPB), nmp).  ut layout [nmp][L+1][2][RH].
-__global__ void __launch_bounds__(FFT_THREADS)
+__global__ void __launch_bounds__(FFT_THREADS, 2)
 k_ring_r2c(int L, int R, int R_half, int RH, int N, int log2N, const float* __restrict__ maps,
            const float* __restrict__ ring_weight, const float2* __restrict__ tw, float2* __restrict__ ut) {
     extern __shared__ float2 buf[];
-    const int RPB = fft_rings_per_block(N);
-    const int NP = N + (N >> 4);
+    const int lgR = 13 - log2N;
+    const int RPB = 1 << lgR;
+    const int NP = fft_stride(N);
     const int mp = blockIdx.y;
     const int j0 = blockIdx.x * RPB;
     const int ntr = min(RPB, R_half - j0);
     const float* in = maps + (int64_t)mp * R * N;
-    // (ring pair, k) items, FFT_LB per thread loaded before any is stored.
-    const int nitem = RPB * N;
+    // (ring pair, 4 consecutive longitudes) items: two 16-byte loads each, FFT_LB items
+    // per thread loaded before any is stored.
+    const int nitem = (RPB * N) >> 2;
     for (int i0 = threadIdx.x; i0 < nitem; i0 += FFT_LB * FFT_THREADS) {
-        float xn[FFT_LB], xs[FFT_LB];
+        float4 xn[FFT_LB], xs[FFT_LB];
 #pragma unroll
         for (int u = 0; u < FFT_LB; ++u) {
             const int i = i0 + u * FFT_THREADS;
-            const int qq = i / N, k = i % N;
+            const int qq = (4 * i) >> log2N, k = (4 * i) & (N - 1);
             const int jn = j0 + qq, js = R - 1 - jn;
-            xn[u] = 0.f;
-            xs[u] = 0.f;
+            xn[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            xs[u] = xn[u];
             if (i < nitem && qq < ntr) {
-                xn[u] = in[(int64_t)jn * N + k];
-                if (js != jn) xs[u] = in[(int64_t)js * N + k];
+                xn[u] = *reinterpret_cast<const float4*>(in + (int64_t)jn * N + k);
+                if (js != jn) xs[u] = *reinterpret_cast<const float4*>(in + (int64_t)js * N + k);
             }
         }
 #pragma unroll
         for (int u = 0; u < FFT_LB; ++u) {
             const int i = i0 + u * FFT_THREADS;
             if (i >= nitem) break;
-            const int qq = i / N, k = i % N;
+            const int qq = (4 * i) >> log2N, k = (4 * i) & (N - 1);
             const int jn = j0 + qq, js = R - 1 - jn;
             const float wn = (ring_weight && qq < ntr) ? ring_weight[jn] : 1.f;
             const float ws = (ring_weight && qq < ntr) ? ring_weight[js] : 1.f;
-            buf[qq * NP + pad16(k)] = make_float2(wn * xn[u], ws * xs[u]);
+            float2* b = buf + qq * NP + pad16(k);
+            b[0] = make_float2(wn * xn[u].x, ws * xs[u].x);
+            b[1] = make_float2(wn * xn[u].y, ws * xs[u].y);
+            b[2] = make_float2(wn * xn[u].z, ws * xs[u].z);
+            b[3] = make_float2(wn * xn[u].w, ws * xs[u].w);
         }
     }
     __syncthreads();
     const int T = N >> 4;
     const int q = threadIdx.x / T, tl = threadIdx.x % T;
     fft_transform<-1>(buf + q * NP, N, log2N, tl, tw);
-    float2* o = ut + (int64_t)mp * (L + 1) * 2 * RH;
-    for (int i = threadIdx.x; i < (L + 1) * RPB; i += FFT_THREADS) {
-        const int m = i / RPB, qq = i % RPB;
+    float2* o = ut + (int64_t)mp * (L + 1) * 2 * RH + j0;
+    const int nout = (L + 1) << lgR;
+    for (int i = threadIdx.x; i < nout; i += FFT_THREADS) {
+        const int m = i >> lgR, qq = i & (RPB - 1);
         if (qq >= ntr) continue;
         const float2* b = buf + qq * NP;
         const float2 zm = b[pad16(m)];
@@ -290,8 +306,8 @@ k_ring_r2c(int L, int R, int R_half, int RH, int N, int log2N, const float* __re
         // U~_n = (Z_m + conj Z_{N-m}) / 2 ; U~_s = (Z_m - conj Z_{N-m}) / 2i
         const float2 un = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
         const float2 us = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
-        o[((int64_t)m * 2 + 0) * RH + j0 + qq] = cadd(un, us);
-        o[((int64_t)m * 2 + 1) * RH + j0 + qq] = csub(un, us);
+        o[((int64_t)m * 2 + 0) * RH + qq] = cadd(un, us);
+        o[((int64_t)m * 2 + 1) * RH + qq] = csub(un, us);
     }
 }
 
@@ -301,7 +317,7 @@ static int ilog2(int n) {
     return r;
 }
 
-static size_t fft_smem(int N) { return (size_t)fft_rings_per_block(N) * (N + (N >> 4)) * sizeof(float2); }
+static size_t fft_smem(int N) { return (size_t)fft_rings_per_block(N) * fft_stride(N) * sizeof(float2); }
 
 cudaError_t launch_ring_c2r(const Plan& pl, const float2* delta, int nmp, float* maps, cudaStream_t st) {
     if (nmp == 0) return cudaSuccess;
