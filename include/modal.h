@@ -74,7 +74,7 @@ typedef enum {
 
 typedef struct {
     int nrings;              /* Gauss-Legendre rings, >= lmax + 1                          */
-    int nphi;                /* longitudes: a power of two, >= 2 lmax + 2, <= 8192          */
+    int nphi;                /* longitudes: a power of two, >= max(16, 2 lmax + 2), <= 8192 */
     const float* ring_mask;  /* host [nrings] multiplying W_x, or NULL (all ones)           */
     const float* pix_mask;   /* host [nrings*nphi] multiplying W_x, or NULL (all ones)      */
 } modal_grid;

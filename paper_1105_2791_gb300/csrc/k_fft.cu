@@ -1,4 +1,4 @@
-// Ring Fourier transforms in shared memory (power-of-two N = nphi, 128 <= N <= 8192).
+// Ring Fourier transforms in shared memory (power-of-two N = nphi, 16 <= N <= 8192).
 //
 // Synthesis (c2r):  M(theta, phi_k) = D_0 + 2 Re sum_{m=1}^{lmax} D_m e^{i m phi_k}
 // = sum_{m=-lmax}^{lmax} D_m e^{2 pi i m k / N} with D_{-m} = conj(D_m).  The north
@@ -118,24 +118,36 @@ __device__ __forceinline__ void dft(float2* x) {
     }
 }
 
-// One Stockham pass of radix R at sub-transform length Ns over the transform at `buf`
-// (padded indices).  Thread tl (0 <= tl < T = N / 16) handles butterflies j = tl + T u.
-template <int SIGN, int R>
-__device__ __forceinline__ void stockham_pass(float2* buf, int N, int Ns, int log2Ns, int tl,
-                                              const float2* __restrict__ tw) {
+// Padded shared-memory index of element base + r * STRIDE.  When STRIDE is a multiple of
+// 16 the padding of the r-th element is that of `base` plus r * STRIDE / 16, so every
+// access of a pass is a per-thread base plus a compile-time offset.
+template <int STRIDE>
+__device__ __forceinline__ int pad_at(int base, int r) {
+    if constexpr (STRIDE % 16 == 0) return pad16(base) + r * (STRIDE + STRIDE / 16);
+    else return pad16(base + r * STRIDE);
+}
+
+// One Stockham pass of radix R at sub-transform length NS of an N-point transform at
+// `buf` (padded indices).  Thread tl (0 <= tl < T = N / 16) handles butterflies
+// j = tl + T u, u < 16 / R: it reads elements j + r N / R, applies the twiddles
+// e^{SIGN 2 pi i r k / (R NS)} (k = j mod NS), transforms, and writes element r of
+// butterfly j to R (j - k) + k + r NS.
+template <int SIGN, int R, int N, int NS>
+__device__ __forceinline__ void stockham_pass(float2* buf, int tl, const float2* __restrict__ tw) {
     constexpr int NB = 16 / R;                   // butterflies per thread
-    const int T = N >> 4;
-    const int NR = N / R;
+    constexpr int T = N / 16;
+    constexpr int NR = N / R;
+    static_assert(NS == 1 ? R == 16 : NS % 16 == 0, "pass shapes of a radix-16-first Stockham FFT");
     float2 v[16];
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
         const int j = tl + T * u;
-        const int k = j & (Ns - 1);
+        const int k = j & (NS - 1);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            float2 x = buf[pad16(j + r * NR)];
-            if (r > 0 && Ns > 1) {
-                float2 w = __ldg(&tw[(r - 1) * Ns + k]);
+            float2 x = buf[pad_at<NR>(j, r)];
+            if (r > 0 && NS > 1) {
+                float2 w = __ldg(&tw[(r - 1) * NS + k]);
                 if (SIGN < 0) w.y = -w.y;
                 x = cmul(x, w);
             }
@@ -147,48 +159,48 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int N, int Ns, int lo
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
         const int j = tl + T * u;
-        const int k = j & (Ns - 1);
-        const int d = (((j >> log2Ns) * R) << log2Ns) + k;
+        const int k = j & (NS - 1);
+        const int d = R * (j - k) + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pad16(d + r * Ns)] = v[u * R + r];
+        for (int r = 0; r < R; ++r) {
+            if constexpr (NS == 1) buf[pad16(d) + r] = v[u * R + r];   // d = 16 j: one padded group
+            else buf[pad_at<NS>(d, r)] = v[u * R + r];
+        }
     }
     __syncthreads();
 }
 
 // Twiddle table, one block per pass in pass order: for the pass of radix R at
-// sub-transform length Ns, entries (r - 1) Ns + k = e^{2 pi i r k / (R Ns)}, r = 1..R-1,
-// k = 0..Ns-1 (N - 1 entries in all), so that the threads of a warp read consecutive
-// entries.
-template <int SIGN>
-__device__ void fft_transform(float2* buf, int N, int log2N, int tl, const float2* __restrict__ tw) {
-    int Ns = 1, log2Ns = 0;
-    while (log2N - log2Ns >= 4) {
-        stockham_pass<SIGN, 16>(buf, N, Ns, log2Ns, tl, tw);
-        tw += 15 * Ns;
-        Ns <<= 4;
-        log2Ns += 4;
+// sub-transform length NS, entries (r - 1) NS + k = e^{2 pi i r k / (R NS)}, r = 1..R-1,
+// k = 0..NS-1 (N - 1 entries in all), so that the threads of a warp read consecutive
+// entries.  Passes: radix 16 while at least 16 remain, then the remainder (8, 4 or 2).
+template <int SIGN, int N, int NS>
+__device__ __forceinline__ void fft_passes(float2* buf, int tl, const float2* __restrict__ tw) {
+    if constexpr (NS < N) {
+        constexpr int R = (N / NS >= 16) ? 16 : N / NS;
+        stockham_pass<SIGN, R, N, NS>(buf, tl, tw);
+        fft_passes<SIGN, N, NS * R>(buf, tl, tw + (R - 1) * NS);
     }
-    const int rem = log2N - log2Ns;
-    if (rem == 3) stockham_pass<SIGN, 8>(buf, N, Ns, log2Ns, tl, tw);
-    else if (rem == 2) stockham_pass<SIGN, 4>(buf, N, Ns, log2Ns, tl, tw);
-    else if (rem == 1) stockham_pass<SIGN, 2>(buf, N, Ns, log2Ns, tl, tw);
 }
 
 // Padded transform stride in float2: N + N/16 for the in-transform padding, + 4 so that
 // the transforms of one CTA start 8 banks apart (the (m, ring pair) loads and the
 // U~ reads, where the ring pair varies fastest, are then free of bank conflicts).
-__host__ __device__ inline int fft_stride(int N) { return N + (N >> 4) + 4; }
+__host__ __device__ constexpr int fft_stride(int N) { return N + (N >> 4) + 4; }
 
 // grid: (ceil(R_half / RPB), nmp); nmp = number of (map, p) rows.
 // delta layout [nmp][L+1][2][RH]: even (E) and odd (O) Legendre sums per ring pair;
 // north = E + O, south = E - O.
+template <int LOG2N>
 __global__ void __launch_bounds__(FFT_THREADS, 2)
-k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __restrict__ delta,
-           const float2* __restrict__ tw, float* __restrict__ maps) {
+k_ring_c2r(int L, int R, int R_half, int RH, const float2* __restrict__ delta, const float2* __restrict__ tw,
+           float* __restrict__ maps) {
+    constexpr int N = 1 << LOG2N;
+    constexpr int lgR = 13 - LOG2N;                      // RPB = 2^lgR transforms per CTA
+    constexpr int RPB = 1 << lgR;
+    constexpr int NP = fft_stride(N);
+    constexpr int T = N / 16;
     extern __shared__ float2 buf[];
-    const int lgR = 13 - log2N;                          // RPB = 2^lgR transforms per CTA
-    const int RPB = 1 << lgR;
-    const int NP = fft_stride(N);
     const int mp = blockIdx.y;
     const int j0 = blockIdx.x * RPB;
     const int ntr = min(RPB, R_half - j0);
@@ -231,14 +243,13 @@ k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __r
         }
     }
     __syncthreads();
-    const int T = N >> 4;
     const int q = threadIdx.x / T, tl = threadIdx.x % T;
-    fft_transform<+1>(buf + q * NP, N, log2N, tl, tw);
+    fft_passes<+1, N, 1>(buf + q * NP, tl, tw);
     // four consecutive longitudes per thread: four 8-byte shared loads, two 16-byte stores
     float* out = maps + (int64_t)mp * R * N;
     const int n4 = (ntr * N) >> 2;
     for (int i = threadIdx.x; i < n4; i += FFT_THREADS) {
-        const int qq = (4 * i) >> log2N, k = (4 * i) & (N - 1);
+        const int qq = (4 * i) >> LOG2N, k = (4 * i) & (N - 1);
         const int jn = j0 + qq, js = R - 1 - jn;
         const float2* b = buf + qq * NP + pad16(k);      // k .. k+3 lie in one padded group of 16
         const float2 z0 = b[0], z1 = b[1], z2 = b[2], z3 = b[3];
@@ -248,26 +259,29 @@ k_ring_c2r(int L, int R, int R_half, int RH, int N, int log2N, const float2* __r
 }
 
 // grid: (ceil(R_half / RPB), nmp).  ut layout [nmp][L+1][2][RH].
+template <int LOG2N>
 __global__ void __launch_bounds__(FFT_THREADS, 2)
-k_ring_r2c(int L, int R, int R_half, int RH, int N, int log2N, const float* __restrict__ maps,
-           const float* __restrict__ ring_weight, const float2* __restrict__ tw, float2* __restrict__ ut) {
+k_ring_r2c(int L, int R, int R_half, int RH, const float* __restrict__ maps, const float* __restrict__ ring_weight,
+           const float2* __restrict__ tw, float2* __restrict__ ut) {
+    constexpr int N = 1 << LOG2N;
+    constexpr int lgR = 13 - LOG2N;
+    constexpr int RPB = 1 << lgR;
+    constexpr int NP = fft_stride(N);
+    constexpr int T = N / 16;
     extern __shared__ float2 buf[];
-    const int lgR = 13 - log2N;
-    const int RPB = 1 << lgR;
-    const int NP = fft_stride(N);
     const int mp = blockIdx.y;
     const int j0 = blockIdx.x * RPB;
     const int ntr = min(RPB, R_half - j0);
     const float* in = maps + (int64_t)mp * R * N;
     // (ring pair, 4 consecutive longitudes) items: two 16-byte loads each, FFT_LB items
     // per thread loaded before any is stored.
-    const int nitem = (RPB * N) >> 2;
+    constexpr int nitem = (RPB * N) >> 2;
     for (int i0 = threadIdx.x; i0 < nitem; i0 += FFT_LB * FFT_THREADS) {
         float4 xn[FFT_LB], xs[FFT_LB];
 #pragma unroll
         for (int u = 0; u < FFT_LB; ++u) {
             const int i = i0 + u * FFT_THREADS;
-            const int qq = (4 * i) >> log2N, k = (4 * i) & (N - 1);
+            const int qq = (4 * i) >> LOG2N, k = (4 * i) & (N - 1);
             const int jn = j0 + qq, js = R - 1 - jn;
             xn[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             xs[u] = xn[u];
@@ -280,7 +294,7 @@ k_ring_r2c(int L, int R, int R_half, int RH, int N, int log2N, const float* __re
         for (int u = 0; u < FFT_LB; ++u) {
             const int i = i0 + u * FFT_THREADS;
             if (i >= nitem) break;
-            const int qq = (4 * i) >> log2N, k = (4 * i) & (N - 1);
+            const int qq = (4 * i) >> LOG2N, k = (4 * i) & (N - 1);
             const int jn = j0 + qq, js = R - 1 - jn;
             const float wn = (ring_weight && qq < ntr) ? ring_weight[jn] : 1.f;
             const float ws = (ring_weight && qq < ntr) ? ring_weight[js] : 1.f;
@@ -292,9 +306,8 @@ k_ring_r2c(int L, int R, int R_half, int RH, int N, int log2N, const float* __re
         }
     }
     __syncthreads();
-    const int T = N >> 4;
     const int q = threadIdx.x / T, tl = threadIdx.x % T;
-    fft_transform<-1>(buf + q * NP, N, log2N, tl, tw);
+    fft_passes<-1, N, 1>(buf + q * NP, tl, tw);
     float2* o = ut + (int64_t)mp * (L + 1) * 2 * RH + j0;
     const int nout = (L + 1) << lgR;
     for (int i = threadIdx.x; i < nout; i += FFT_THREADS) {
@@ -319,29 +332,65 @@ static int ilog2(int n) {
 
 static size_t fft_smem(int N) { return (size_t)fft_rings_per_block(N) * fft_stride(N) * sizeof(float2); }
 
+template <int LOG2N>
+static cudaError_t c2r_n(const Plan& pl, const float2* delta, int nmp, float* maps, cudaStream_t st) {
+    constexpr int N = 1 << LOG2N;
+    const size_t smem = fft_smem(N);
+    cudaError_t e = cudaFuncSetAttribute(k_ring_c2r<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int RPB = fft_rings_per_block(N);
+    dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
+    k_ring_c2r<LOG2N><<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, delta, pl.twiddle, maps);
+    return cudaGetLastError();
+}
+
+template <int LOG2N>
+static cudaError_t r2c_n(const Plan& pl, const float* maps, int nmp, const float* ring_weight, float2* ut,
+                         cudaStream_t st) {
+    constexpr int N = 1 << LOG2N;
+    const size_t smem = fft_smem(N);
+    cudaError_t e = cudaFuncSetAttribute(k_ring_r2c<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int RPB = fft_rings_per_block(N);
+    dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
+    k_ring_r2c<LOG2N><<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, maps, ring_weight,
+                                                        pl.twiddle, ut);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ring_c2r(const Plan& pl, const float2* delta, int nmp, float* maps, cudaStream_t st) {
     if (nmp == 0) return cudaSuccess;
-    const int N = pl.nphi, RPB = fft_rings_per_block(N);
-    const size_t smem = fft_smem(N);
-    cudaError_t e = cudaFuncSetAttribute(k_ring_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
-    k_ring_c2r<<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, N, ilog2(N), delta, pl.twiddle,
-                                                maps);
-    return cudaGetLastError();
+    switch (ilog2(pl.nphi)) {
+        case 4: return c2r_n<4>(pl, delta, nmp, maps, st);
+        case 5: return c2r_n<5>(pl, delta, nmp, maps, st);
+        case 6: return c2r_n<6>(pl, delta, nmp, maps, st);
+        case 7: return c2r_n<7>(pl, delta, nmp, maps, st);
+        case 8: return c2r_n<8>(pl, delta, nmp, maps, st);
+        case 9: return c2r_n<9>(pl, delta, nmp, maps, st);
+        case 10: return c2r_n<10>(pl, delta, nmp, maps, st);
+        case 11: return c2r_n<11>(pl, delta, nmp, maps, st);
+        case 12: return c2r_n<12>(pl, delta, nmp, maps, st);
+        case 13: return c2r_n<13>(pl, delta, nmp, maps, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmp, const float* ring_weight, float2* ut,
                             cudaStream_t st) {
     if (nmp == 0) return cudaSuccess;
-    const int N = pl.nphi, RPB = fft_rings_per_block(N);
-    const size_t smem = fft_smem(N);
-    cudaError_t e = cudaFuncSetAttribute(k_ring_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
-    k_ring_r2c<<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, N, ilog2(N), maps, ring_weight,
-                                                pl.twiddle, ut);
-    return cudaGetLastError();
+    switch (ilog2(pl.nphi)) {
+        case 4: return r2c_n<4>(pl, maps, nmp, ring_weight, ut, st);
+        case 5: return r2c_n<5>(pl, maps, nmp, ring_weight, ut, st);
+        case 6: return r2c_n<6>(pl, maps, nmp, ring_weight, ut, st);
+        case 7: return r2c_n<7>(pl, maps, nmp, ring_weight, ut, st);
+        case 8: return r2c_n<8>(pl, maps, nmp, ring_weight, ut, st);
+        case 9: return r2c_n<9>(pl, maps, nmp, ring_weight, ut, st);
+        case 10: return r2c_n<10>(pl, maps, nmp, ring_weight, ut, st);
+        case 11: return r2c_n<11>(pl, maps, nmp, ring_weight, ut, st);
+        case 12: return r2c_n<12>(pl, maps, nmp, ring_weight, ut, st);
+        case 13: return r2c_n<13>(pl, maps, nmp, ring_weight, ut, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace modal

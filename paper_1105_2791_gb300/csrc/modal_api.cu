@@ -293,8 +293,8 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
     if (P < 1 || P > MODAL_MAXP) return set_error(MODAL_EINVAL, "P must be in [1, 16]");
     if (!basis || !C_l || !grid) return set_error(MODAL_EINVAL, "basis, C_l and grid are required");
     if (grid->nrings < lmax + 1) return set_error(MODAL_EINVAL, "nrings must be >= lmax + 1");
-    if (!is_pow2(grid->nphi) || grid->nphi < 2 * lmax + 2 || grid->nphi > 8192)
-        return set_error(MODAL_EINVAL, "nphi must be a power of two in [2 lmax + 2, 8192]");
+    if (!is_pow2(grid->nphi) || grid->nphi < 2 * lmax + 2 || grid->nphi < 16 || grid->nphi > 8192)
+        return set_error(MODAL_EINVAL, "nphi must be a power of two in [max(16, 2 lmax + 2), 8192]");
     if (prec < MODAL_FP32 || prec > MODAL_FP16X3) return set_error(MODAL_EINVAL, "unknown precision");
     for (int l = 0; l <= lmax; ++l)
         if (!std::isfinite(C_l[l])) return set_error(MODAL_EINVAL, "C_l must be finite");
