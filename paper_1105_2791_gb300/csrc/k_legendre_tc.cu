@@ -7,7 +7,7 @@
 // E + O, its mirror south ring E - O (lambda_lm(-mu) = (-1)^{l+m} lambda_lm(mu)).
 //
 // Work item = (m, parity, tile of 128 ring pairs, group of 8 maps).  A persistent CTA
-// loops over items.  Per pipeline stage it holds 128 bytes of K per row:
+// loops over items.  Per pipeline stage (TC_STAGES of them) it holds TC_KB bytes of K per row:
 //   A (lambda, pre-split hi/lo, pre-tiled in HBM): fetched with one cp.async.bulk;
 //   B (filtered a_lm, scaled and split hi/lo): built once per chunk by k_tc_prep_b in
 //      the same layout and shared by all ring tiles; fetched with cp.async.bulk.
@@ -19,7 +19,7 @@
 // form D1 + D2, undo the scaling and write the even (E) or odd (O) row for the ring
 // pairs; the ring FFT forms north = E + O and south = E - O.
 // Operands use the no-swizzle K-major core-matrix layout: element (row r, k) at
-// (r/8)*1024 + (k/(16/E))*128 + (r%8)*16 + (k%(16/E))*E bytes (E = element bytes).
+// (r/8)*TC_SBO + (k/(16/E))*128 + (r%8)*16 + (k%(16/E))*E bytes (E = element bytes).
 //
 // Every mbarrier wait is bounded (~1 s of clock): on expiry the kernel records
 // MODAL_DEVERR_TIMEOUT, the roles drain, in-flight copies are awaited (bounded) and
@@ -86,7 +86,7 @@ __global__ void k_alm_amax(int L, const float* __restrict__ fmax_l, const float2
 
 // ------------------------------------------------------------------ B operand blocks
 // Stage block (g, m, pi, kb) of the filtered a_lm for maps 8g .. 8g+7: [hi tile, lo tile],
-// each N = 16 P rows (b, p, re/im) x 128 bytes of K (KPS values l = m + pi + 2 (kb KPS + k)),
+// each N = 16 P rows (b, p, re/im) x TC_KB bytes of K (KPS values l = m + pi + 2 (kb KPS + k)),
 // the same core-matrix layout the MMA reads.  Built once per chunk and shared by every
 // ring tile.
 struct PrepArgs {
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
     using S = Split<PREC>;
     constexpr bool TF32 = (PREC == MODAL_3XTF32);
     constexpr int KPS = TC_KB / S::E;     // K values per stage
-    constexpr int NKC = TC_KB / 16;       // core matrices along K per stage (8)
+    constexpr int NKC = TC_KB / 16;       // core matrices along K per stage
     const int N = 16 * a.P;               // 2 (re, im) x P x 8 maps
     const int b_tile = N * TC_KB;         // bytes of one B tile
     const uint32_t stage_tx = TC_A_STAGE + 2 * b_tile;
@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
         // ---------------- loader (one thread): A and B stage blocks by cp.async.bulk
         if (lane == 0) {
             uint32_t it = 0;
-            uint32_t last_phase[TC_STAGES] = {0, 0};
-            bool issued[TC_STAGES] = {false, false};
+            uint32_t last_phase[TC_STAGES] = {};
+            bool issued[TC_STAGES] = {};
             for (int64_t item = blockIdx.x; item < a.n_items && !*abort_flag; item += gridDim.x) {
                 int m, pi, rt, g;
                 tc_item(a, item, m, pi, rt, g);

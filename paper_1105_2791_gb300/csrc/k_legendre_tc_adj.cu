@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(TA_THREADS, 1) k_legendre_tc_adj(AdjArgs a) {
     if (warp == 0) {
         if (lane == 0) {
             uint32_t it = 0;
-            uint32_t last_phase[TC_STAGES] = {0, 0};
-            bool issued[TC_STAGES] = {false, false};
+            uint32_t last_phase[TC_STAGES] = {};
+            bool issued[TC_STAGES] = {};
             for (int64_t item = blockIdx.x; item < a.n_items && !*abort_flag; item += gridDim.x) {
                 int m, pi, lt, g;
                 ta_item(a, item, m, pi, lt, g);

@@ -13,10 +13,10 @@ namespace modal {
 constexpr int TC_MAPS = 8;                 // maps per work item (N = 16 P)
 constexpr int TC_PROD_WARPS = 8;           // epilogue warps
 constexpr int TC_THREADS = 32 * (2 + TC_PROD_WARPS);
-constexpr int TC_STAGES = 2;
-constexpr int TC_KB = 128;                 // bytes of K per row per stage (8 core matrices)
+constexpr int TC_STAGES = 4;
+constexpr int TC_KB = 64;                  // bytes of K per row per stage (4 core matrices)
 constexpr int TC_SBO = 8 * TC_KB;          // bytes between 8-row groups
-constexpr int TC_A_TILE = 128 * TC_KB;     // bytes: 128 rows x 128 bytes of K
+constexpr int TC_A_TILE = 128 * TC_KB;     // bytes: 128 rows x TC_KB bytes of K
 constexpr int TC_A_STAGE = 2 * TC_A_TILE;  // hi, lo
 constexpr float TC_LAMBDA_SCALE = 2048.f;  // |lambda| * 2^11 stays inside fp16 range
 constexpr long long TC_WAIT_CYCLES = 1ll << 31;
@@ -67,7 +67,7 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle; LBO = 128 B (next core matrix
-// along K), SBO = 1024 B (next 8-row group), descriptor version 1.
+// along K), SBO = TC_SBO (next 8-row group: 8 rows x TC_KB bytes), descriptor version 1.
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
