@@ -258,11 +258,14 @@ k_ring_c2r(int L, int R, int R_half, int RH, const float2* __restrict__ delta, c
     }
 }
 
-// grid: (ceil(R_half / RPB), nmp).  ut layout [nmp][L+1][2][RH].
+// grid: (ceil(R_half / RPB), nmp).  ut layout [nmp][L+1][2][RH].  If amax is not null,
+// amax[row / P] is raised (atomicMax on the float bits) to the largest |Re| or |Im| this
+// CTA writes: with amax cleared beforehand, it ends up as each map's max over all rows.
 template <int LOG2N>
 __global__ void __launch_bounds__(FFT_THREADS, 2)
-k_ring_r2c(int L, int R, int R_half, int RH, const float* __restrict__ maps, const float* __restrict__ ring_weight,
-           const float2* __restrict__ tw, float2* __restrict__ ut) {
+k_ring_r2c(int L, int R, int R_half, int RH, int P, const float* __restrict__ maps,
+           const float* __restrict__ ring_weight, const float2* __restrict__ tw, float2* __restrict__ ut,
+           unsigned* __restrict__ amax) {
     constexpr int N = 1 << LOG2N;
     constexpr int lgR = 13 - LOG2N;
     constexpr int RPB = 1 << lgR;
@@ -310,6 +313,7 @@ k_ring_r2c(int L, int R, int R_half, int RH, const float* __restrict__ maps, con
     fft_passes<-1, N, 1>(buf + q * NP, tl, tw);
     float2* o = ut + (int64_t)mp * (L + 1) * 2 * RH + j0;
     const int nout = (L + 1) << lgR;
+    float vmax = 0.f;
     for (int i = threadIdx.x; i < nout; i += FFT_THREADS) {
         const int m = i >> lgR, qq = i & (RPB - 1);
         if (qq >= ntr) continue;
@@ -319,8 +323,14 @@ k_ring_r2c(int L, int R, int R_half, int RH, const float* __restrict__ maps, con
         // U~_n = (Z_m + conj Z_{N-m}) / 2 ; U~_s = (Z_m - conj Z_{N-m}) / 2i
         const float2 un = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
         const float2 us = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
-        o[((int64_t)m * 2 + 0) * RH + qq] = cadd(un, us);
-        o[((int64_t)m * 2 + 1) * RH + qq] = csub(un, us);
+        const float2 e = cadd(un, us), od = csub(un, us);
+        o[((int64_t)m * 2 + 0) * RH + qq] = e;
+        o[((int64_t)m * 2 + 1) * RH + qq] = od;
+        vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(e.x), fabsf(e.y)), fmaxf(fabsf(od.x), fabsf(od.y))));
+    }
+    if (amax) {
+        for (int off = 16; off > 0; off >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
+        if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(&amax[mp / P], __float_as_uint(vmax));
     }
 }
 
@@ -346,15 +356,15 @@ static cudaError_t c2r_n(const Plan& pl, const float2* delta, int nmp, float* ma
 
 template <int LOG2N>
 static cudaError_t r2c_n(const Plan& pl, const float* maps, int nmp, const float* ring_weight, float2* ut,
-                         cudaStream_t st) {
+                         unsigned* amax, cudaStream_t st) {
     constexpr int N = 1 << LOG2N;
     const size_t smem = fft_smem(N);
     cudaError_t e = cudaFuncSetAttribute(k_ring_r2c<LOG2N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int RPB = fft_rings_per_block(N);
     dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
-    k_ring_r2c<LOG2N><<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, maps, ring_weight,
-                                                        pl.twiddle, ut);
+    k_ring_r2c<LOG2N><<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, pl.P, maps,
+                                                        ring_weight, pl.twiddle, ut, amax);
     return cudaGetLastError();
 }
 
@@ -376,19 +386,19 @@ cudaError_t launch_ring_c2r(const Plan& pl, const float2* delta, int nmp, float*
 }
 
 cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmp, const float* ring_weight, float2* ut,
-                            cudaStream_t st) {
+                            unsigned* amax, cudaStream_t st) {
     if (nmp == 0) return cudaSuccess;
     switch (ilog2(pl.nphi)) {
-        case 4: return r2c_n<4>(pl, maps, nmp, ring_weight, ut, st);
-        case 5: return r2c_n<5>(pl, maps, nmp, ring_weight, ut, st);
-        case 6: return r2c_n<6>(pl, maps, nmp, ring_weight, ut, st);
-        case 7: return r2c_n<7>(pl, maps, nmp, ring_weight, ut, st);
-        case 8: return r2c_n<8>(pl, maps, nmp, ring_weight, ut, st);
-        case 9: return r2c_n<9>(pl, maps, nmp, ring_weight, ut, st);
-        case 10: return r2c_n<10>(pl, maps, nmp, ring_weight, ut, st);
-        case 11: return r2c_n<11>(pl, maps, nmp, ring_weight, ut, st);
-        case 12: return r2c_n<12>(pl, maps, nmp, ring_weight, ut, st);
-        case 13: return r2c_n<13>(pl, maps, nmp, ring_weight, ut, st);
+        case 4: return r2c_n<4>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 5: return r2c_n<5>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 6: return r2c_n<6>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 7: return r2c_n<7>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 8: return r2c_n<8>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 9: return r2c_n<9>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 10: return r2c_n<10>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 11: return r2c_n<11>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 12: return r2c_n<12>(pl, maps, nmp, ring_weight, ut, amax, st);
+        case 13: return r2c_n<13>(pl, maps, nmp, ring_weight, ut, amax, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -25,6 +25,9 @@ namespace modal {
 
 constexpr int TA_EPI_WARPS = 4;
 constexpr int TA_THREADS = 32 * (2 + 2 * TA_EPI_WARPS);   // same shape as the forward kernel
+// bytes after the operand stages: 2 TC_STAGES + 2 mbarriers, the TMEM slot and the abort
+// flag, rounded up to 16; the epilogue's filter table follows
+constexpr int TA_BAR_BYTES = ((8 * (2 * TC_STAGES + 2) + 8 + 15) / 16) * 16;
 
 __host__ __device__ inline int ta_kpar(int L, int m, int pi) {
     return (L - m - pi >= 0) ? (L - m - pi) / 2 + 1 : 0;       // values of l with this parity
@@ -177,7 +180,8 @@ __global__ void __launch_bounds__(TA_THREADS, 1) k_legendre_tc_adj(AdjArgs a) {
     uint64_t* tmem_empty = tmem_full + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    float* sF = reinterpret_cast<float*>(smem + TC_STAGES * TC_A_STAGE + TC_STAGES * 2 * 256 * TC_KB + 64);  // [128][17]
+    float* sF = reinterpret_cast<float*>(smem + TC_STAGES * TC_A_STAGE + TC_STAGES * 2 * 256 * TC_KB +
+                                         TA_BAR_BYTES);                                              // [128][17]
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t tmem_cols = (2 * N <= 256) ? 256u : 512u;
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(TA_THREADS, 1) k_legendre_tc_adj(AdjArgs a) {
 }
 
 static size_t ta_smem_bytes() {
-    return 1024 + TC_STAGES * TC_A_STAGE + TC_STAGES * 2 * 256 * TC_KB + 64 + 128 * 17 * sizeof(float);
+    return 1024 + TC_STAGES * TC_A_STAGE + TC_STAGES * 2 * 256 * TC_KB + TA_BAR_BYTES + 128 * 17 * sizeof(float);
 }
 
 static int ta_kps(int prec) { return prec == MODAL_3XTF32 ? TC_KB / 4 : TC_KB / 2; }
@@ -412,14 +416,17 @@ static cudaError_t launch_adj(const Plan& pl, const AdjPrepArgs& pa, const AdjAr
     return cudaGetLastError();
 }
 
-cudaError_t launch_legendre_adjoint_tc(const Plan& pl, const float2* ut, int B, float2* grad, cudaStream_t st) {
+cudaError_t launch_legendre_adjoint_tc(const Plan& pl, const float2* ut, int B, float2* grad, bool amax_ready,
+                                       cudaStream_t st) {
     if (B == 0) return cudaSuccess;
     if (B > 4096 || B > pl.chunk) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(pl.tc.d_amax, 0, B * sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
-    k_ut_amax<<<dim3(256, B), 256, 0, st>>>(pl.lmax, pl.P, pl.R_half, pl.RH, ut, pl.tc.d_amax);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (!amax_ready) {
+        cudaError_t e = cudaMemsetAsync(pl.tc.d_amax, 0, B * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        k_ut_amax<<<dim3(256, B), 256, 0, st>>>(pl.lmax, pl.P, pl.R_half, pl.RH, ut, pl.tc.d_amax);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     AdjPrepArgs pa;
     pa.L = pl.lmax;
     pa.P = pl.P;

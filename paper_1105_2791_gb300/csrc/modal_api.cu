@@ -476,7 +476,7 @@ modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void*
     const int step = h->chunk * h->P;   // ut holds chunk*P channels
     for (int b0 = 0; b0 < B; b0 += step) {
         const int nb = std::min(step, B - b0);
-        { STAGE(h, ST_R2C, st); CK(launch_ring_r2c(*h, maps + (size_t)b0 * h->npix, nb, h->wring, h->ut, st), "analyze r2c"); }
+        { STAGE(h, ST_R2C, st); CK(launch_ring_r2c(*h, maps + (size_t)b0 * h->npix, nb, h->wring, h->ut, nullptr, st), "analyze r2c"); }
         { STAGE(h, ST_LEGENDRE_ADJ, st); CK(launch_legendre_adjoint_simt(*h, h->ut, nb, nullptr, 1, out + (size_t)b0 * h->n_alm, st), "analyze legendre"); }
     }
     return MODAL_OK;
@@ -599,13 +599,19 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "backward synthesis");
         { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_weights(*h, g + (size_t)b0 * h->n_max, nb, h->hk, st), "adjoint weights"); }
         { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear, h->maps, st), "adjoint pixel"); }
-        { STAGE(h, ST_R2C, st); CK(launch_ring_r2c(*h, h->maps, nb * h->P, nullptr, h->ut, st), "adjoint r2c"); }
+        {
+            // split precisions: the r2c kernel also records each map's max |U~| for the operand scale
+            STAGE(h, ST_R2C, st);
+            unsigned* amax = (h->prec == MODAL_FP32) ? nullptr : h->tc.d_amax;
+            if (amax) CK(cudaMemsetAsync(amax, 0, nb * sizeof(unsigned), st), "adjoint scale clear");
+            CK(launch_ring_r2c(*h, h->maps, nb * h->P, nullptr, h->ut, amax, st), "adjoint r2c");
+        }
         {
             STAGE(h, ST_LEGENDRE_ADJ, st);
             if (h->prec == MODAL_FP32)
                 CK(launch_legendre_adjoint_simt(*h, h->ut, nb, h->filt, h->P, out + (size_t)b0 * h->n_alm, st), "adjoint legendre");
             else
-                CK(launch_legendre_adjoint_tc(*h, h->ut, nb, out + (size_t)b0 * h->n_alm, st), "adjoint legendre");
+                CK(launch_legendre_adjoint_tc(*h, h->ut, nb, out + (size_t)b0 * h->n_alm, true, st), "adjoint legendre");
         }
     }
     return MODAL_OK;

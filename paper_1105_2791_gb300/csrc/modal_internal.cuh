@@ -130,7 +130,9 @@ size_t tc_b_workspace_bytes(const Plan& pl, int chunk);
 cudaError_t build_tc_adj_tables(Plan& pl, cudaStream_t st);
 void free_tc_adj_tables(Plan& pl);
 size_t tc_adj_workspace_bytes(const Plan& pl, int chunk);
-cudaError_t launch_legendre_adjoint_tc(const Plan& pl, const float2* ut, int B, float2* grad, cudaStream_t st);
+// amax_ready: pl.tc.d_amax already holds each map's max |U~| (from k_ring_r2c).
+cudaError_t launch_legendre_adjoint_tc(const Plan& pl, const float2* ut, int B, float2* grad, bool amax_ready,
+                                       cudaStream_t st);
 void free_tc_tables(Plan& pl);
 // k_legendre_simt.cu
 cudaError_t launch_legendre_simt(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st);
@@ -141,7 +143,7 @@ cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2*
 // k_fft.cu
 cudaError_t launch_ring_c2r(const Plan& pl, const float2* delta, int nmaps_p, float* maps, cudaStream_t st);
 cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmaps_p, const float* ring_weight,
-                            float2* ut, cudaStream_t st);
+                            float2* ut, unsigned* amax, cudaStream_t st);
 // k_cubic.cu
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);

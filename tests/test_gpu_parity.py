@@ -193,6 +193,37 @@ def test_backward_parity(prec, use_linear):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_map_groups_match_single_maps(prec):
+    """20 maps in one pass (three groups of up to 8 maps in the tensor-core work items,
+    the last one partial) give the same beta, linear term and gradient as the maps one at
+    a time, and the batched gradient agrees with the oracle."""
+    M = _cuda_or_skip()
+    L, P, R, nphi, B = 96, 16, 97, 256, 20
+    basis, cl, alm = _case(L, P, B, seed=77)
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec)
+    plan.set_chunk(B)
+    sims = simgen.gaussian_alm(cl, 4, seed=78, stream=simgen.STREAM_LINEAR).astype(np.complex64)
+    plan.linear_term(torch.from_numpy(sims).cuda(), finalize=True)
+    g = np.random.default_rng(79).standard_normal((B, plan.n_max))
+    a = torch.from_numpy(alm).cuda()
+    gd = torch.from_numpy(g).cuda()
+    beta = plan.cubic(a, use_linear=True).cpu().numpy()
+    grad = plan.backward(a, gd, use_linear=True).cpu().numpy()
+    for b in (0, 7, 8, 15, 16, 19):
+        b1 = plan.cubic(a[b:b + 1], use_linear=True).cpu().numpy()[0]
+        g1 = plan.backward(a[b:b + 1], gd[b:b + 1], use_linear=True).cpu().numpy()[0]
+        assert _rel(beta[b], b1) <= 1e-6, b
+        assert _rel(grad[b], g1) <= 1e-6, b
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    pm = om.pair_means([osh.synthesize(s.astype(np.complex128), L, filt, mu, nphi) for s in sims])
+    for b in (3, 19):
+        ref = om.adjoint_grad(alm[b].astype(np.complex128), g[b], L, filt, mu, w, nphi, None, pm)
+        assert _rel(grad[b], ref) <= 1e-5, b
+    plan.close()
+
+
 def test_autograd_function_matches_adjoint():
     M = _cuda_or_skip()
     L, P, R, nphi = 16, 2, 17, 64
