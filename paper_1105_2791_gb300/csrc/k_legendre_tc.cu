@@ -313,7 +313,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
                 inv_lane = exp2f((float)-tc_scale_exp(a.amax[g * TC_MAPS + lane])) * lam_inv;
             bool ok = !*abort_flag && mbar_wait(tmem_full, nitem & 1, abort_flag, a.err);
             ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
+            if (!ok) {                                       // items left undone: never silent
+                if (lane == 0) atomicOr(a.err, MODAL_DEVERR_TIMEOUT);
+                break;
+            }
             tc_fence_after();
             const int jn = rt * 128 + quarter * 32 + lane;   // TMEM lane = ring pair within the tile
             const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);

@@ -284,7 +284,10 @@ __global__ void __launch_bounds__(TA_THREADS, 1) k_legendre_tc_adj(AdjArgs a) {
             for (int t = 0; t < a.P; ++t) my_f[t] = (l <= a.L) ? a.filt[(int64_t)t * (a.L + 1) + l] : 0.f;
             bool ok = !*abort_flag && mbar_wait(tmem_full, nitem & 1, abort_flag, a.err);
             ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
+            if (!ok) {                                       // items left undone: never silent
+                if (lane == 0) atomicOr(a.err, MODAL_DEVERR_TIMEOUT);
+                break;
+            }
             tc_fence_after();
             const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
             float acc_re = 0.f, acc_im = 0.f;

@@ -258,7 +258,10 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
             }
-            if (!ok) break;
+            if (!ok) {                                      // items left undone: never silent
+                if (lane == 0) atomicOr(a.err, MODAL_DEVERR_TIMEOUT);
+                break;
+            }
             const int gr = mt * 128 + row;                  // (map, basis) column of G
             if (gr < a.ncols) {
 #pragma unroll

@@ -221,6 +221,7 @@ def test_map_groups_match_single_maps(prec):
     for b in (3, 19):
         ref = om.adjoint_grad(alm[b].astype(np.complex128), g[b], L, filt, mu, w, nphi, None, pm)
         assert _rel(grad[b], ref) <= 1e-5, b
+    plan.sync()                                  # no kernel left work undone
     plan.close()
 
 
@@ -385,6 +386,7 @@ def test_backward_full_size_l2000_sampled_rings(prec):
     plan = _plan(M, L, P, basis, cl, R, nphi, prec, ring_mask=mask)
     g = np.random.default_rng(2002).standard_normal((2, plan.n_max))
     grad = plan.backward(torch.from_numpy(alm).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
+    plan.sync()
     plan.close()
     mu, w = osh.gl_nodes(R)
     filt = osh.filter_table(basis, cl)
