@@ -193,7 +193,7 @@ modal_status modal_cubic_static(const float* maps, const float* W, long long npi
  * (stage_ms, may be NULL) and the number of kernel launches (launches, may be NULL;
  * counted whether or not profiling is on) since the previous call, then resets both.
  * Stages are numbered 0 .. MODAL_NSTAGES-1; modal_stage_name gives their names. */
-#define MODAL_NSTAGES 12
+#define MODAL_NSTAGES 14
 modal_status modal_set_profiling(modal_h h, int enable);
 modal_status modal_get_profile(modal_h h, double* stage_ms, long long* launches, int nstages);
 const char* modal_stage_name(int stage);

@@ -31,7 +31,7 @@ EXPORTS = [
     "modal_sync", "modal_save_state", "modal_load_state", "modal_selftest_wait", "modal_destroy",
     "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
 ]
-MODAL_NSTAGES = 12
+MODAL_NSTAGES = 14
 
 
 class ModalError(RuntimeError):

@@ -203,6 +203,7 @@ static cudaError_t launch_cubic_pm(Plan& pl, const float* maps, int B, double* p
     dim3 grid(pl.cubic_ctas, B);
     k_cubic<PM><<<grid, ncomp + CUB_TX, smem, st>>>(pl.P, pl.n_pg, pl.n_tiles, nl, ncomp, pl.tiles, pl.modeidx,
                                                     pl.npix, ppc, maps, pl.W, partial, pl.n_max);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -271,6 +272,7 @@ cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* parti
     const int64_t kchunk = ((pl.npix + pl.lin_ksplit - 1) / pl.lin_ksplit + LG_TK - 1) / LG_TK * LG_TK;
     dim3 grid((pl.n_pair + LG_TM - 1) / LG_TM, (ncols + LG_TN - 1) / LG_TN, pl.lin_ksplit);
     k_linear_gemm<<<grid, 256, 0, st>>>(pl.n_pair, ncols, pl.npix, kchunk, pl.pair_mean, pl.W, maps, partial);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -308,6 +310,7 @@ cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* 
     k_beta_finalize<<<(n + 127) / 128, 128, 0, st>>>(pl.P, pl.n_max, B, pl.cubic_ctas, use_linear, pl.lin_ksplit,
                                                       pl.n_pair, pl.modeidx + 16 * 256, pl.modeidx + 16 * 256 + 1024,
                                                       pl.modeidx + 16 * 256 + 2048, cub_partial, lin_partial, beta);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -401,6 +404,7 @@ cudaError_t launch_pair_accumulate(Plan& pl, const float* maps, int B, cudaStrea
     if (B == 0) return cudaSuccess;
     const int64_t nblk = (pl.npix + PA_PIX - 1) / PA_PIX;
     const int grid = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
+    note_launch(pl);
     if (pl.P <= 4)
         k_pair_accumulate<4><<<grid, PA_THREADS, PA_STAGES * 4 * PA_THREADS * 4, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
     else if (pl.P <= 8)
@@ -419,6 +423,7 @@ __global__ void k_pair_finalize(int64_t n, double inv, const double* __restrict_
 cudaError_t launch_pair_finalize(Plan& pl, cudaStream_t st) {
     const int64_t n = (int64_t)pl.n_pair * pl.npix;
     k_pair_finalize<<<152 * 8, 256, 0, st>>>(n, 1.0 / (double)pl.n_lin, pl.pair_sum, pl.pair_mean);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -448,6 +453,7 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
     const int n = B * pl.P * pl.n_pair;
     k_adjoint_weights<<<(n + 127) / 128, 128, 0, st>>>(pl.P, pl.n_pair, pl.n_max, B, pl.modeidx + 16 * 256 + 3072,
                                                         g, hk);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -610,6 +616,7 @@ static cudaError_t launch_adjoint_u_pm(Plan& pl, int B, const float* hk, const f
     ng = std::min<int64_t>(ng, ntile);
     k_adjoint_u<PM><<<(unsigned)(ng * nmp), AU_THREADS, smem, st>>>(pl.P, pl.n_pair, B, (int)ng, pl.npix, hk, pm,
                                                                     pl.W, maps);
+    note_launch(pl);
     return cudaGetLastError();
 }
 

@@ -351,6 +351,7 @@ static cudaError_t c2r_n(const Plan& pl, const float2* delta, int nmp, float* ma
     const int RPB = fft_rings_per_block(N);
     dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
     k_ring_c2r<LOG2N><<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, delta, pl.twiddle, maps);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -365,6 +366,7 @@ static cudaError_t r2c_n(const Plan& pl, const float* maps, int nmp, const float
     dim3 grid((pl.R_half + RPB - 1) / RPB, nmp);
     k_ring_r2c<LOG2N><<<grid, FFT_THREADS, smem, st>>>(pl.lmax, pl.nrings, pl.R_half, pl.RH, pl.P, maps,
                                                         ring_weight, pl.twiddle, ut, amax);
+    note_launch(pl);
     return cudaGetLastError();
 }
 

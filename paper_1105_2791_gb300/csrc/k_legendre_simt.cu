@@ -82,6 +82,7 @@ k_legendre_simt(int L, int P, int R, int R_half, int RH, const float* __restrict
 cudaError_t launch_legendre_simt(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
     dim3 grid((pl.R_half + 127) / 128, pl.lmax + 1, B);
+    note_launch(pl);
     if (pl.P <= 4)
         k_legendre_simt<4><<<grid, 128, 0, st>>>(pl.lmax, pl.P, pl.nrings, pl.R_half, pl.RH, pl.lam, pl.filt,
                                                  alm, pl.n_alm, delta);
@@ -171,6 +172,7 @@ cudaError_t launch_legendre_adjoint_simt(const Plan& pl, const float2* ut, int B
                                          int nt, float2* out, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
     dim3 grid((pl.lmax + 1 + 127) / 128, pl.lmax + 1, B);
+    note_launch(pl);
     if (nt <= 4)
         k_legendre_adj_simt<4><<<grid, 128, 0, st>>>(pl.lmax, nt, pl.R_half, pl.RH, pl.lam, ut, rowfilt, pl.n_alm, out);
     else if (nt <= 8)

@@ -71,14 +71,18 @@ __global__ void k_build_tc_table(int L, int R_half, int RH, int n_rt, const floa
 
 // ------------------------------------------------------------------ per-map scale
 // amax[b] = max_{l,m,p} |f_p(l) a_{b,lm}| as float bits (positive floats order as ints).
-__global__ void k_alm_amax(int L, const float* __restrict__ fmax_l, const float2* __restrict__ alm, int64_t n_alm,
-                           unsigned* __restrict__ amax) {
-    const int m = blockIdx.y, b = blockIdx.z;
-    const int64_t base = d_alm_index(m, m, L);
+// grid (AM_BLOCKS, B): block x takes orders m = x, x + AM_BLOCKS, ...; one atomic per warp.
+constexpr int AM_BLOCKS = 64;
+__global__ void __launch_bounds__(256) k_alm_amax(int L, const float* __restrict__ fmax_l, const float2* __restrict__ alm,
+                                                  int64_t n_alm, unsigned* __restrict__ amax) {
+    const int b = blockIdx.y;
     float v = 0.f;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= L - m; k += gridDim.x * blockDim.x) {
-        const float2 a = alm[(int64_t)b * n_alm + base + k];
-        v = fmaxf(v, fmaxf(fabsf(a.x), fabsf(a.y)) * fmax_l[m + k]);
+    for (int m = blockIdx.x; m <= L; m += gridDim.x) {
+        const float2* row = alm + (int64_t)b * n_alm + d_alm_index(m, m, L);
+        for (int k = threadIdx.x; k <= L - m; k += blockDim.x) {
+            const float2 a = row[k];
+            v = fmaxf(v, fmaxf(fabsf(a.x), fabsf(a.y)) * fmax_l[m + k]);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(&amax[b], __float_as_uint(v));
@@ -447,14 +451,16 @@ void free_tc_tables(Plan& pl) {
 }
 
 template <int PREC>
-static cudaError_t launch_tc(const Plan& pl, const PrepArgs& pa, const TcArgs& args, cudaStream_t st) {
-    {
+static cudaError_t launch_tc(const Plan& pl, const PrepArgs& pa, const TcArgs& args, int part, cudaStream_t st) {
+    if (part & 1) {
         const int maxkb = tc_nkb(pl.lmax, 0, 0, kps_for(pl.prec));
         dim3 grid(std::min(maxkb, 8), 2 * (pl.lmax + 1), pa.n_groups);
         k_tc_prep_b<PREC><<<grid, 256, 0, st>>>(pa);
+        note_launch(pl);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (!(part & 2)) return cudaSuccess;
     const size_t smem = tc_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_legendre_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -462,17 +468,18 @@ static cudaError_t launch_tc(const Plan& pl, const PrepArgs& pa, const TcArgs& a
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl.dev);
     const int grid = (int)std::min<int64_t>(args.n_items, (int64_t)std::max(nsm, 1));
     k_legendre_tc<PREC><<<grid, TC_THREADS, smem, st>>>(args);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st) {
+cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2* delta, int part, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
     if (B > 4096 || B > pl.chunk) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(pl.tc.d_amax, 0, B * sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
-    {
-        dim3 grid(std::max(1, std::min(8, (pl.lmax + 1 + 255) / 256)), pl.lmax + 1, B);
-        k_alm_amax<<<grid, 256, 0, st>>>(pl.lmax, pl.tc.d_fmax, alm, pl.n_alm, pl.tc.d_amax);
+    if (part & 1) {
+        cudaError_t e = cudaMemsetAsync(pl.tc.d_amax, 0, B * sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        k_alm_amax<<<dim3(AM_BLOCKS, B), 256, 0, st>>>(pl.lmax, pl.tc.d_fmax, alm, pl.n_alm, pl.tc.d_amax);
+        note_launch(pl);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -507,10 +514,10 @@ cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2*
     a.delta = delta;
     a.err = pl.d_err;
     switch (pl.prec) {
-        case MODAL_FP16X3: return launch_tc<MODAL_FP16X3>(pl, pa, a, st);
-        case MODAL_BF16X3: return launch_tc<MODAL_BF16X3>(pl, pa, a, st);
-        case MODAL_BF16: return launch_tc<MODAL_BF16>(pl, pa, a, st);
-        case MODAL_3XTF32: return launch_tc<MODAL_3XTF32>(pl, pa, a, st);
+        case MODAL_FP16X3: return launch_tc<MODAL_FP16X3>(pl, pa, a, part, st);
+        case MODAL_BF16X3: return launch_tc<MODAL_BF16X3>(pl, pa, a, part, st);
+        case MODAL_BF16: return launch_tc<MODAL_BF16>(pl, pa, a, part, st);
+        case MODAL_3XTF32: return launch_tc<MODAL_3XTF32>(pl, pa, a, part, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -404,11 +404,16 @@ void free_tc_adj_tables(Plan& pl) {
 }
 
 template <int PREC>
-static cudaError_t launch_adj(const Plan& pl, const AdjPrepArgs& pa, const AdjArgs& a, cudaStream_t st) {
-    dim3 pgrid(std::min(pa.nkb, 8), 2 * (pl.lmax + 1), a.n_groups);
-    k_tc_prep_adj<PREC><<<pgrid, 256, 0, st>>>(pa);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+static cudaError_t launch_adj(const Plan& pl, const AdjPrepArgs& pa, const AdjArgs& a, int part, cudaStream_t st) {
+    cudaError_t e;
+    if (part & 1) {
+        dim3 pgrid(std::min(pa.nkb, 8), 2 * (pl.lmax + 1), a.n_groups);
+        k_tc_prep_adj<PREC><<<pgrid, 256, 0, st>>>(pa);
+        note_launch(pl);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (!(part & 2)) return cudaSuccess;
     const size_t smem = ta_smem_bytes();
     e = cudaFuncSetAttribute(k_legendre_tc_adj<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -416,17 +421,19 @@ static cudaError_t launch_adj(const Plan& pl, const AdjPrepArgs& pa, const AdjAr
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, pl.dev);
     const int grid = (int)std::min<int64_t>(a.n_items, (int64_t)std::max(nsm, 1));
     k_legendre_tc_adj<PREC><<<grid, TA_THREADS, smem, st>>>(a);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_legendre_adjoint_tc(const Plan& pl, const float2* ut, int B, float2* grad, bool amax_ready,
-                                       cudaStream_t st) {
+                                       int part, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
     if (B > 4096 || B > pl.chunk) return cudaErrorInvalidValue;
-    if (!amax_ready) {
+    if (!amax_ready && (part & 1)) {
         cudaError_t e = cudaMemsetAsync(pl.tc.d_amax, 0, B * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
         k_ut_amax<<<dim3(256, B), 256, 0, st>>>(pl.lmax, pl.P, pl.R_half, pl.RH, ut, pl.tc.d_amax);
+        note_launch(pl);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -457,10 +464,10 @@ cudaError_t launch_legendre_adjoint_tc(const Plan& pl, const float2* ut, int B, 
     a.grad = grad;
     a.err = pl.d_err;
     switch (pl.prec) {
-        case MODAL_FP16X3: return launch_adj<MODAL_FP16X3>(pl, pa, a, st);
-        case MODAL_BF16X3: return launch_adj<MODAL_BF16X3>(pl, pa, a, st);
-        case MODAL_BF16: return launch_adj<MODAL_BF16>(pl, pa, a, st);
-        case MODAL_3XTF32: return launch_adj<MODAL_3XTF32>(pl, pa, a, st);
+        case MODAL_FP16X3: return launch_adj<MODAL_FP16X3>(pl, pa, a, part, st);
+        case MODAL_BF16X3: return launch_adj<MODAL_BF16X3>(pl, pa, a, part, st);
+        case MODAL_BF16: return launch_adj<MODAL_BF16>(pl, pa, a, part, st);
+        case MODAL_3XTF32: return launch_adj<MODAL_3XTF32>(pl, pa, a, part, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -304,6 +304,7 @@ cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial
     const int64_t items = (int64_t)a.n_mt * a.n_kr;
     const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(nsm, 1));
     k_linear_tc<<<grid, LT_THREADS, smem, st>>>(a);
+    note_launch(pl);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ cudaError_t launch_cov_accumulate(Plan& pl, const double* beta, int B, cudaStrea
     if (B == 0) return cudaSuccess;
     const int64_t n2 = (int64_t)pl.n_max * pl.n_max;
     k_cov_accumulate<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(pl.n_max, B, beta, pl.S1, pl.S2);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -40,6 +41,7 @@ __global__ void k_zeta(int n, double N, const double* __restrict__ S1, const dou
 cudaError_t launch_zeta(Plan& pl, double* zeta, cudaStream_t st) {
     const int64_t n2 = (int64_t)pl.n_max * pl.n_max;
     k_zeta<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(pl.n_max, (double)pl.n_cov, pl.S1, pl.S2, zeta);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -133,11 +135,14 @@ __global__ void __launch_bounds__(256) k_chol_update(int n, int k0, double* __re
 cudaError_t launch_cholesky(Plan& pl, double* A, int n, cudaStream_t st) {
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
         k_chol_diag<<<1, CH_NB * CH_NB, 0, st>>>(n, k0, A, pl.d_err);
+        note_launch(pl);
         const int below = n - k0 - CH_NB;
         if (below > 0) {
             k_chol_panel<<<(below + 7) / 8, 256, 0, st>>>(n, k0, A, pl.d_err);
+            note_launch(pl);
             const int nt = (below + CH_NB - 1) / CH_NB;
             k_chol_update<<<nt * (nt + 1) / 2, 256, 0, st>>>(n, k0, A, pl.d_err);
+            note_launch(pl);
         }
     }
     return cudaGetLastError();
@@ -162,6 +167,7 @@ __global__ void __launch_bounds__(256) k_solve_rhs(int n, const double* __restri
 cudaError_t launch_solve_rhs(Plan& pl, const double* Lc, int n, double* rhs, int nrhs, cudaStream_t st) {
     if (nrhs == 0) return cudaSuccess;
     k_solve_rhs<<<nrhs, 256, 0, st>>>(n, Lc, rhs);
+    note_launch(pl);
     return cudaGetLastError();
 }
 
@@ -194,6 +200,7 @@ __global__ void __launch_bounds__(256) k_estimates(int n, int B, const double* _
 
 cudaError_t launch_estimates(Plan& pl, const double* rhs, int n, int B, double* out, cudaStream_t st) {
     k_estimates<<<1, 256, 0, st>>>(n, B, rhs, out);
+    note_launch(pl);
     return cudaGetLastError();
 }
 

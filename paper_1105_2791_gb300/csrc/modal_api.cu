@@ -231,13 +231,14 @@ static modal_status check_plan(modal_h h) {
 
 static cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// Brackets one kernel launch: counts it under `stage` and, with profiling on, records
-// CUDA events before and after it on the launching stream.
+// Brackets the launches of one stage: counts the kernels they launch under `stage` and,
+// with profiling on, records CUDA events before and after them on the launching stream.
 struct StageScope {
     modal_plan* pl;
     int stage;
     cudaStream_t st;
     cudaEvent_t a = nullptr;
+    long long k0;                          // plan's kernel count when the scope opened
     static cudaEvent_t take(modal_plan* p) {
         if (!p->prof_pool.empty()) {
             cudaEvent_t e = p->prof_pool.back();
@@ -248,14 +249,14 @@ struct StageScope {
         cudaEventCreate(&e);
         return e;
     }
-    StageScope(modal_plan* p, int s, cudaStream_t stream) : pl(p), stage(s), st(stream) {
-        pl->stage_launches[stage] += 1;
+    StageScope(modal_plan* p, int s, cudaStream_t stream) : pl(p), stage(s), st(stream), k0(p->launch_count) {
         if (pl->prof) {
             a = take(pl);
             cudaEventRecord(a, st);
         }
     }
     ~StageScope() {
+        pl->stage_launches[stage] += pl->launch_count - k0;
         if (pl->prof && a) {
             cudaEvent_t b = take(pl);
             cudaEventRecord(b, st);
@@ -266,14 +267,24 @@ struct StageScope {
 #define STAGE(pl, id, st) StageScope _scope_##id((pl), (id), (st))
 
 // Legendre stage for one chunk: alm -> delta.
+// Legendre stage for one chunk: alm -> delta (tensor-core path: operand preparation and
+// the contraction are timed as separate stages).
 static cudaError_t legendre_forward(modal_plan* pl, const float2* alm, int B, cudaStream_t st) {
-    if (pl->prec == MODAL_FP32) return launch_legendre_simt(*pl, alm, B, pl->delta, st);
-    return launch_legendre_tc(*pl, alm, B, pl->delta, st);
+    if (pl->prec == MODAL_FP32) {
+        STAGE(pl, ST_LEGENDRE, st);
+        return launch_legendre_simt(*pl, alm, B, pl->delta, st);
+    }
+    {
+        STAGE(pl, ST_LEGENDRE_PREP, st);
+        cudaError_t e = launch_legendre_tc(*pl, alm, B, pl->delta, 1, st);
+        if (e != cudaSuccess) return e;
+    }
+    STAGE(pl, ST_LEGENDRE, st);
+    return launch_legendre_tc(*pl, alm, B, pl->delta, 2, st);
 }
 
 static cudaError_t synth_chunk(modal_plan* pl, const float2* alm, int B, float* maps_out, cudaStream_t st) {
     {
-        STAGE(pl, ST_LEGENDRE, st);
         cudaError_t e = legendre_forward(pl, alm, B, st);
         if (e != cudaSuccess) return e;
     }
@@ -606,12 +617,12 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
             if (amax) CK(cudaMemsetAsync(amax, 0, nb * sizeof(unsigned), st), "adjoint scale clear");
             CK(launch_ring_r2c(*h, h->maps, nb * h->P, nullptr, h->ut, amax, st), "adjoint r2c");
         }
-        {
+        if (h->prec == MODAL_FP32) {
             STAGE(h, ST_LEGENDRE_ADJ, st);
-            if (h->prec == MODAL_FP32)
-                CK(launch_legendre_adjoint_simt(*h, h->ut, nb, h->filt, h->P, out + (size_t)b0 * h->n_alm, st), "adjoint legendre");
-            else
-                CK(launch_legendre_adjoint_tc(*h, h->ut, nb, out + (size_t)b0 * h->n_alm, true, st), "adjoint legendre");
+            CK(launch_legendre_adjoint_simt(*h, h->ut, nb, h->filt, h->P, out + (size_t)b0 * h->n_alm, st), "adjoint legendre");
+        } else {
+            { STAGE(h, ST_LEGENDRE_ADJ_PREP, st); CK(launch_legendre_adjoint_tc(*h, h->ut, nb, out + (size_t)b0 * h->n_alm, true, 1, st), "adjoint legendre prep"); }
+            { STAGE(h, ST_LEGENDRE_ADJ, st); CK(launch_legendre_adjoint_tc(*h, h->ut, nb, out + (size_t)b0 * h->n_alm, true, 2, st), "adjoint legendre"); }
         }
     }
     return MODAL_OK;
@@ -810,7 +821,8 @@ modal_status modal_load_state(modal_h h, const char* path) {
 
 static const char* kStageNames[MODAL_NSTAGES] = {
     "legendre", "ring_c2r", "cubic", "linear_gemm", "beta_finalize", "pair_means",
-    "cov_accumulate", "solve", "adjoint_pixel", "ring_r2c", "legendre_adjoint", "other"};
+    "cov_accumulate", "solve", "adjoint_pixel", "ring_r2c", "legendre_adjoint", "other",
+    "legendre_prep", "legendre_adjoint_prep"};
 
 const char* modal_stage_name(int stage) {
     return (stage >= 0 && stage < MODAL_NSTAGES) ? kStageNames[stage] : "";

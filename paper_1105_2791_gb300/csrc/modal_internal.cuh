@@ -109,11 +109,13 @@ struct Plan {
     std::vector<cudaEvent_t> prof_pool;
     double stage_ms[MODAL_NSTAGES] = {};
     long long stage_launches[MODAL_NSTAGES] = {};
+    mutable long long launch_count = 0;   // kernels launched by this plan (note_launch)
 };
 
 enum Stage {
     ST_LEGENDRE = 0, ST_C2R = 1, ST_CUBIC = 2, ST_LINEAR = 3, ST_BETA = 4, ST_PAIRS = 5,
-    ST_COV = 6, ST_SOLVE = 7, ST_ADJ_PIXEL = 8, ST_R2C = 9, ST_LEGENDRE_ADJ = 10, ST_OTHER = 11
+    ST_COV = 6, ST_SOLVE = 7, ST_ADJ_PIXEL = 8, ST_R2C = 9, ST_LEGENDRE_ADJ = 10, ST_OTHER = 11,
+    ST_LEGENDRE_PREP = 12, ST_LEGENDRE_ADJ_PREP = 13
 };
 
 // ---- error reporting (modal_api.cu) ----
@@ -132,14 +134,18 @@ void free_tc_adj_tables(Plan& pl);
 size_t tc_adj_workspace_bytes(const Plan& pl, int chunk);
 // amax_ready: pl.tc.d_amax already holds each map's max |U~| (from k_ring_r2c).
 cudaError_t launch_legendre_adjoint_tc(const Plan& pl, const float2* ut, int B, float2* grad, bool amax_ready,
-                                       cudaStream_t st);
+                                       int part, cudaStream_t st);
 void free_tc_tables(Plan& pl);
 // k_legendre_simt.cu
 cudaError_t launch_legendre_simt(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st);
 cudaError_t launch_legendre_adjoint_simt(const Plan& pl, const float2* ut, int B, const float* rowfilt,
                                          int nfilt, float2* out, cudaStream_t st);
 // k_legendre_tc.cu
-cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2* delta, cudaStream_t st);
+// Every kernel launch of the hot path is counted on its plan.
+inline void note_launch(const Plan& pl) { ++pl.launch_count; }
+
+// part: 1 = operand preparation (per-map scale, split B blocks), 2 = the contraction, 3 = both.
+cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2* delta, int part, cudaStream_t st);
 // k_fft.cu
 cudaError_t launch_ring_c2r(const Plan& pl, const float2* delta, int nmaps_p, float* maps, cudaStream_t st);
 cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmaps_p, const float* ring_weight,
