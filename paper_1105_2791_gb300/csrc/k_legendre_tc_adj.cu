@@ -91,6 +91,9 @@ struct AdjPrepArgs {
 };
 
 // B block (g, m, pi, kb): rows n = (bl, t, re/im), K = ring pairs j = kb KPS + k.
+// A thread takes one (bl, t) and one core-matrix column kc: it reads the CM values of
+// U~ there as 16-byte vectors and writes the hi and lo parts of both the Re row (n = 2q)
+// and the Im row (n = 2q + 1).
 template <int PREC>
 __global__ void __launch_bounds__(256) k_tc_prep_adj(AdjPrepArgs a) {
     using S = Split<PREC>;
@@ -98,8 +101,10 @@ __global__ void __launch_bounds__(256) k_tc_prep_adj(AdjPrepArgs a) {
     constexpr int KPS = TC_KB / S::E;
     constexpr int CM = 16 / S::E;
     constexpr int NKC = TC_KB / 16;
+    static_assert(CM % 2 == 0, "CM values of U~ are read as float4 pairs");
     __shared__ float s_scale[TC_MAPS];
     const int N = 16 * a.P;
+    const int NQ = N / 2;                                  // (bl, t) rows
     const int b_tile = N * TC_KB;
     const int m = blockIdx.y >> 1, pi = blockIdx.y & 1, g = blockIdx.z;
     if (threadIdx.x < TC_MAPS) {
@@ -109,26 +114,48 @@ __global__ void __launch_bounds__(256) k_tc_prep_adj(AdjPrepArgs a) {
     __syncthreads();
     for (int kb = blockIdx.x; kb < a.nkb; kb += gridDim.x) {
         char* bt = a.out + ((((int64_t)g * (a.L + 1) + m) * 2 + pi) * a.nkb + kb) * (int64_t)(2 * b_tile);
-        for (int c = threadIdx.x; c < NKC * N; c += blockDim.x) {
-            const int kc = c / N, n = c % N;
-            const int bl = n / (2 * a.P), t = (n / 2) % a.P, comp = n % 2;
+        for (int c = threadIdx.x; c < NKC * NQ; c += blockDim.x) {
+            const int kc = c / NQ, q = c % NQ;
+            const int bl = q / a.P, t = q % a.P;
             const int b = g * TC_MAPS + bl;
             const float sc = s_scale[bl];
-            const float2* u = a.ut + ((((int64_t)(b * a.P + t)) * (a.L + 1) + m) * 2 + pi) * a.RH;
-            T hv[CM], lv[CM];
+            const int j0 = kb * KPS + kc * CM;
+            float re[CM], im[CM];
+            if (b < a.B && j0 + CM <= a.R_half) {
+                // whole core-matrix row inside the ring range: 16-byte loads (RH is a multiple of 32)
+                const float4* u4 = reinterpret_cast<const float4*>(
+                    a.ut + ((((int64_t)(b * a.P + t)) * (a.L + 1) + m) * 2 + pi) * a.RH + j0);
+#pragma unroll
+                for (int i = 0; i < CM / 2; ++i) {
+                    const float4 v = u4[i];
+                    re[2 * i] = v.x * sc;
+                    im[2 * i] = v.y * sc;
+                    re[2 * i + 1] = v.z * sc;
+                    im[2 * i + 1] = v.w * sc;
+                }
+            } else {
+                const float2* u = a.ut + ((((int64_t)(b * a.P + t)) * (a.L + 1) + m) * 2 + pi) * a.RH;
+#pragma unroll
+                for (int i = 0; i < CM; ++i) {
+                    const int j = j0 + i;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (b < a.B && j < a.R_half) v = u[j];
+                    re[i] = v.x * sc;
+                    im[i] = v.y * sc;
+                }
+            }
+            T hr[CM], lr[CM], hm[CM], lm[CM];
 #pragma unroll
             for (int i = 0; i < CM; ++i) {
-                const int j = kb * KPS + kc * CM + i;
-                float x = 0.f;
-                if (b < a.B && j < a.R_half) {
-                    const float2 v = u[j];
-                    x = (comp ? v.y : v.x) * sc;
-                }
-                S::split(x, hv[i], lv[i]);
+                S::split(re[i], hr[i], lr[i]);
+                S::split(im[i], hm[i], lm[i]);
             }
+            const int n = 2 * q;                             // Re row; the Im row n + 1 is 16 bytes on
             const int off = (n / 8) * TC_SBO + kc * 128 + (n % 8) * 16;
-            *reinterpret_cast<uint4*>(bt + off) = *reinterpret_cast<const uint4*>(hv);
-            *reinterpret_cast<uint4*>(bt + b_tile + off) = *reinterpret_cast<const uint4*>(lv);
+            *reinterpret_cast<uint4*>(bt + off) = *reinterpret_cast<const uint4*>(hr);
+            *reinterpret_cast<uint4*>(bt + off + 16) = *reinterpret_cast<const uint4*>(hm);
+            *reinterpret_cast<uint4*>(bt + b_tile + off) = *reinterpret_cast<const uint4*>(lr);
+            *reinterpret_cast<uint4*>(bt + b_tile + off + 16) = *reinterpret_cast<const uint4*>(lm);
         }
     }
 }

@@ -152,12 +152,16 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
                 if (ok) {
                     char* base = stages + s * LT_STAGE;
                     const int64_t xs = x0 + (int64_t)st * LT_KPX;
-                    // A: 128 rows x 8 chunks of 4 pixels; B: 144 rows x 8 chunks.  Thread ct owns chunk
-                    // column kc = ct % 8 in every row it touches (stride 256 keeps kc fixed), so W is
-                    // read once; all loads of the stage are issued before any value is split.
+                    // A: 128 rows x 8 chunks of 4 pixels; B: 144 rows x 8 chunks.  Chunk index c runs
+                    // over blocks of 8 rows, and within a block kc-major: c = 64 (row / 8) + 8 kc +
+                    // row % 8, so that 8 consecutive threads store the 8 rows of one core matrix (128
+                    // contiguous bytes) and a warp's 16-byte stores are free of bank conflicts.  Thread
+                    // ct owns chunk column kc = (ct / 8) % 8 in every row it touches (stride 256 keeps
+                    // kc fixed), so W is read once; all loads of the stage are issued before any value
+                    // is split.
                     constexpr int NCH = (128 + LT_N) * 8;
                     constexpr int NU = (NCH + 32 * LT_CONV_WARPS - 1) / (32 * LT_CONV_WARPS);
-                    const int kc = ct & 7;
+                    const int kc = (ct >> 3) & 7;
                     const int64_t x = xs + kc * 4;
                     const bool whole = (x + 3 < x1);            // x is a multiple of 4: 16-byte aligned
                     float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
 #pragma unroll
                     for (int u = 0; u < NU; ++u) {
                         const int c = ct + u * 32 * LT_CONV_WARPS;
-                        const int row = c >> 3;
+                        const int row = ((c >> 6) << 3) + (c & 7);
                         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                         const float* src = nullptr;
                         if (c < NCH) {
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
                     for (int u = 0; u < NU; ++u) {
                         const int c = ct + u * 32 * LT_CONV_WARPS;
                         if (c >= NCH) continue;
-                        const int row = c >> 3;
+                        const int row = ((c >> 6) << 3) + (c & 7);
                         float4 v = vals[u];
                         if (row >= 128) {
                             v.x *= wv.x;
