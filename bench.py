@@ -137,6 +137,13 @@ def legendre_flops(P, lmax, nrings):
     return 4.0 * P * n_alm * ((nrings + 1) // 2)
 
 
+# DRAM bytes per launch of the forward Legendre contraction (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu launch at this workload; see
+# profiles/legendre_tc_fp16x3_l1000_b8.md).  Keyed by (precision, lmax, nphi, P, maps per
+# launch); set to None whenever k_legendre_tc changes until it is captured again.
+LEGENDRE_TRAFFIC_GB = {("fp16x3", 2000, 4096, 16, 32): 17.04 + 16.40}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -258,7 +265,10 @@ def run_gpu(args):
         roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(bf16 / per, 1),
                 "unit": "TFLOP/s", "peak_source": "measured bf16 sustained / %g products per useful MAC" % per}
     roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
-    roof["traffic"] = None
+    traffic = LEGENDRE_TRAFFIC_GB.get((prec, L, nphi, P, min(B, args.chunk)))
+    roof["traffic"] = round(traffic, 2) if traffic is not None else None
+    if traffic is not None:
+        roof["traffic_unit"] = "GB per launch (ncu dram bytes read + written)"
     roof["kernel"] = "legendre (forward Legendre sums), %d launches, %.3f ms per launch" % (
         leg_n, leg_ms / max(leg_n, 1))
 
