@@ -198,6 +198,27 @@ modal_status modal_set_profiling(modal_h h, int enable);
 modal_status modal_get_profile(modal_h h, double* stage_ms, long long* launches, int nstages);
 const char* modal_stage_name(int stage);
 
+/* Mixed-l_max batches.  A batch groups plans (typically one per l_max, each with its own
+ * tables and workspace) so that one call runs the coefficient pass (modal_cubic) of all of
+ * them.  Each plan runs on a stream of the batch's own; the caller's stream waits for all
+ * of them before its next work.
+ *   modal_batch_create: plans = host array of nplans >= 1 distinct handles on one device;
+ *     the batch keeps the handles (destroy the batch before any of its plans).  Errors:
+ *     MODAL_EINVAL (null, repeated or mixed-device plans), MODAL_ECUDA.
+ *   modal_batch_cubic: for plan i, alm[i] = dev complex64 [B[i]][n_alm_i] and
+ *     beta[i] = dev double [B[i]][n_max_i] exactly as modal_cubic; alm, B and beta are
+ *     host arrays of nplans entries.  With use_graph != 0 the launches are captured into
+ *     one CUDA graph on the first call and the graph is replayed by later calls with the
+ *     same pointers, counts and use_linear (new contents of the same buffers are read);
+ *     any change re-captures it.  Kernels replayed from a graph are not counted by
+ *     modal_get_profile, and plan profiling is suspended while a graph is captured.
+ *     Errors: as modal_cubic for each plan; MODAL_ECUDA if capture or replay fails. */
+typedef struct modal_batch* modal_batch_h;
+modal_status modal_batch_create(const modal_h* plans, int nplans, modal_batch_h* out);
+modal_status modal_batch_cubic(modal_batch_h bh, const void* const* alm, const int* B, int use_linear,
+                               double* const* beta, int use_graph, void* stream);
+void modal_batch_destroy(modal_batch_h bh);
+
 void modal_destroy(modal_h h);
 const char* modal_last_error(void);
 

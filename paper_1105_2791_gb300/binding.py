@@ -30,6 +30,7 @@ EXPORTS = [
     "modal_get_rings", "modal_get_pair_mean", "modal_get_zeta", "modal_reset", "modal_set_chunk",
     "modal_sync", "modal_save_state", "modal_load_state", "modal_selftest_wait", "modal_destroy",
     "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
+    "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy",
 ]
 MODAL_NSTAGES = 14
 
@@ -92,6 +93,8 @@ def load_library():
         "modal_set_profiling": [H, c_int],
         "modal_get_profile": [H, c_void_p, c_void_p, c_int],
         "modal_cubic_static": [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p],
+        "modal_batch_create": [c_void_p, c_int, POINTER(c_void_p)],
+        "modal_batch_cubic": [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p],
     }
     for name, args in sig.items():
         if name == "modal_cubic_static":
@@ -104,6 +107,8 @@ def load_library():
         fn.restype = c_int
     lib.modal_destroy.argtypes = [H]
     lib.modal_destroy.restype = None
+    lib.modal_batch_destroy.argtypes = [c_void_p]
+    lib.modal_batch_destroy.restype = None
     lib.modal_stage_name.argtypes = [c_int]
     lib.modal_stage_name.restype = c_char_p
     lib.modal_last_error.argtypes = []
@@ -173,6 +178,28 @@ def modal_linear_term(h, alm_sims, B, finalize, stream=None):
 
 def modal_cubic(h, alm, B, use_linear, beta, stream=None):
     _check(load_library().modal_cubic(h, _dev(alm), int(B), int(bool(use_linear)), _dev(beta), _stream(stream)))
+
+
+def modal_batch_create(plans):
+    """plans: sequence of plan handles -> batch handle."""
+    arr = (c_void_p * len(plans))(*plans)
+    out = c_void_p()
+    _check(load_library().modal_batch_create(arr, len(plans), byref(out)))
+    return out.value
+
+
+def modal_batch_cubic(bh, alms, Bs, use_linear, betas, use_graph=True, stream=None):
+    """alms, Bs, betas: one entry per plan of the batch (device tensors or addresses)."""
+    n = len(Bs)
+    a = (c_void_p * n)(*[_dev(x) for x in alms])
+    b = (c_int * n)(*[int(x) for x in Bs])
+    o = (c_void_p * n)(*[_dev(x) for x in betas])
+    _check(load_library().modal_batch_cubic(bh, a, b, int(bool(use_linear)), o, int(bool(use_graph)),
+                                            _stream(stream)))
+
+
+def modal_batch_destroy(bh):
+    load_library().modal_batch_destroy(bh)
 
 
 def modal_cov_accumulate(h, beta, B, stream=None):

@@ -856,4 +856,151 @@ modal_status modal_get_profile(modal_h h, double* stage_ms, long long* launches,
     return MODAL_OK;
 }
 
+// ------------------------------------------------------------------ mixed-l_max batches
+}  // extern "C"
+
+struct modal_batch {
+    std::vector<modal_h> plans;
+    cudaStream_t main = nullptr;                  // the batch's own (capturable) stream
+    std::vector<cudaStream_t> side;               // one per plan
+    std::vector<cudaEvent_t> done;                // one per plan
+    cudaEvent_t fork = nullptr, in = nullptr, out = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // arguments the captured graph was made with
+    std::vector<const void*> key_alm;
+    std::vector<int> key_B;
+    std::vector<double*> key_beta;
+    int key_linear = -1;
+};
+
+static void batch_drop_graph(modal_batch* bh) {
+    if (bh->exec) cudaGraphExecDestroy(bh->exec);
+    if (bh->graph) cudaGraphDestroy(bh->graph);
+    bh->exec = nullptr;
+    bh->graph = nullptr;
+    bh->key_linear = -1;
+}
+
+// Fork to the plans' streams, run every plan's coefficient pass, join back on bh->main.
+static modal_status batch_run(modal_batch* bh, const void* const* alm, const int* B, int use_linear,
+                              double* const* beta) {
+    CK(cudaEventRecord(bh->fork, bh->main), "batch fork");
+    for (size_t i = 0; i < bh->plans.size(); ++i) {
+        CK(cudaStreamWaitEvent(bh->side[i], bh->fork, 0), "batch fork wait");
+        const modal_status r = modal_cubic(bh->plans[i], alm[i], B[i], use_linear, beta[i], bh->side[i]);
+        if (r != MODAL_OK) return r;
+        CK(cudaEventRecord(bh->done[i], bh->side[i]), "batch join");
+        CK(cudaStreamWaitEvent(bh->main, bh->done[i], 0), "batch join wait");
+    }
+    return MODAL_OK;
+}
+
+extern "C" {
+
+modal_status modal_batch_create(const modal_h* plans, int nplans, modal_batch_h* out) {
+    if (!out || !plans || nplans < 1) return set_error(MODAL_EINVAL, "batch needs at least one plan");
+    *out = nullptr;
+    for (int i = 0; i < nplans; ++i) {
+        if (!plans[i]) return set_error(MODAL_EINVAL, "null plan in batch");
+        if (plans[i]->dev != plans[0]->dev) return set_error(MODAL_EINVAL, "batch plans on different devices");
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return set_error(MODAL_EINVAL, "plan repeated in batch");
+    }
+    CK(cudaSetDevice(plans[0]->dev), "set device");
+    auto* bh = new modal_batch();
+    bh->plans.assign(plans, plans + nplans);
+    bool ok = cudaStreamCreateWithFlags(&bh->main, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&bh->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&bh->in, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&bh->out, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < nplans; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (s) bh->side.push_back(s);
+        if (e) bh->done.push_back(e);
+    }
+    if (!ok) {
+        modal_batch_destroy(bh);
+        return set_error(MODAL_ECUDA, std::string("batch streams/events: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    *out = bh;
+    return MODAL_OK;
+}
+
+modal_status modal_batch_cubic(modal_batch_h bh, const void* const* alm, const int* B, int use_linear,
+                               double* const* beta, int use_graph, void* stream) {
+    if (!bh || !alm || !B || !beta) return set_error(MODAL_EINVAL, "null batch argument");
+    const size_t n = bh->plans.size();
+    for (size_t i = 0; i < n; ++i) {
+        if (B[i] < 0) return set_error(MODAL_EINVAL, "B < 0");
+        if (B[i] > 0 && (!alm[i] || !beta[i])) return set_error(MODAL_EINVAL, "null pointer");
+        if (use_linear && !bh->plans[i]->lin_final)
+            return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+    }
+    CK(cudaSetDevice(bh->plans[0]->dev), "set device");
+    const cudaStream_t st = as_stream(stream);
+    CK(cudaEventRecord(bh->in, st), "batch in");
+    CK(cudaStreamWaitEvent(bh->main, bh->in, 0), "batch in wait");
+    if (!use_graph) {
+        const modal_status r = batch_run(bh, alm, B, use_linear, beta);
+        if (r != MODAL_OK) return r;
+    } else {
+        const bool same = bh->exec && bh->key_linear == (use_linear ? 1 : 0) &&
+                          std::equal(bh->key_alm.begin(), bh->key_alm.end(), alm) &&
+                          std::equal(bh->key_B.begin(), bh->key_B.end(), B) &&
+                          std::equal(bh->key_beta.begin(), bh->key_beta.end(), beta);
+        if (!same) {
+            batch_drop_graph(bh);
+            std::vector<int> prof(n);
+            for (size_t i = 0; i < n; ++i) {
+                prof[i] = bh->plans[i]->prof;
+                bh->plans[i]->prof = 0;                  // no timing events inside a graph
+            }
+            CK(cudaStreamBeginCapture(bh->main, cudaStreamCaptureModeThreadLocal), "begin capture");
+            const modal_status r = batch_run(bh, alm, B, use_linear, beta);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(bh->main, &g);
+            for (size_t i = 0; i < n; ++i) bh->plans[i]->prof = prof[i];
+            if (r != MODAL_OK) {
+                if (g) cudaGraphDestroy(g);
+                return r;
+            }
+            if (ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return set_error(MODAL_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+            }
+            bh->graph = g;
+            const cudaError_t ie = cudaGraphInstantiate(&bh->exec, bh->graph, 0);
+            if (ie != cudaSuccess) {
+                batch_drop_graph(bh);
+                return set_error(MODAL_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+            }
+            bh->key_alm.assign(alm, alm + n);
+            bh->key_B.assign(B, B + n);
+            bh->key_beta.assign(beta, beta + n);
+            bh->key_linear = use_linear ? 1 : 0;
+        }
+        CK(cudaGraphLaunch(bh->exec, bh->main), "graph launch");
+    }
+    CK(cudaEventRecord(bh->out, bh->main), "batch out");
+    CK(cudaStreamWaitEvent(st, bh->out, 0), "batch out wait");
+    return MODAL_OK;
+}
+
+void modal_batch_destroy(modal_batch_h bh) {
+    if (!bh) return;
+    if (bh->main) cudaStreamSynchronize(bh->main);
+    batch_drop_graph(bh);
+    for (cudaStream_t s : bh->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : bh->done) cudaEventDestroy(e);
+    if (bh->fork) cudaEventDestroy(bh->fork);
+    if (bh->in) cudaEventDestroy(bh->in);
+    if (bh->out) cudaEventDestroy(bh->out);
+    if (bh->main) cudaStreamDestroy(bh->main);
+    delete bh;
+}
+
 }  // extern "C"

@@ -128,3 +128,36 @@ class ModalBeta(torch.autograd.Function):
 
 def modal_beta(alm, plan, use_linear=False):
     return ModalBeta.apply(alm, plan, use_linear)
+
+
+class Batch:
+    """Plans of different l_max run as one coefficient pass (modal_batch_cubic).
+
+    The output tensors are owned by the batch and reused while the map counts stay the
+    same, so that with graph=True the captured CUDA graph is replayed; copy a result to
+    keep it past the next call."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self.h = B.modal_batch_create([p.h for p in self.plans])
+        self._out = None
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            B.modal_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cubic(self, alms, use_linear=False, graph=True):
+        counts = [int(a.shape[0]) for a in alms]
+        if self._out is None or [o.shape[0] for o in self._out] != counts:
+            self._out = [torch.empty((n, p.n_max), dtype=torch.float64, device=a.device)
+                         for n, p, a in zip(counts, self.plans, alms)]
+        B.modal_batch_cubic(self.h, alms, counts, use_linear, self._out, graph)
+        return self._out
+
