@@ -150,8 +150,23 @@ modal_status modal_alpha_local(modal_h h, const double* C_signal, double* alpha)
 modal_status modal_get_info(modal_h h, modal_info* info);
 /* Ring nodes mu_j = cos(theta_j) and weights w_j: host [nrings] each (either may be NULL). */
 modal_status modal_get_rings(modal_h h, double* mu, double* w);
-/* Copy <M_p M_r>_x (after finalize) to dev out [n_pair][nrings*nphi] float32. */
+/* Copy <M_p M_r>_x (after finalize) to dev out [n_pair][nrings*nphi] float32; in ring mode
+ * (modal_set_linear_mode) the ring means, dev out [n_pair][nrings] float32. */
 modal_status modal_get_pair_mean(modal_h h, float* out, void* stream);
+
+/* Linear-term mode (a refinement the paper's axisymmetric noise and mask allow, not part of
+ * its method as printed).  MODAL_LINEAR_PIXEL (default): the Monte Carlo pair means are kept
+ * per pixel, [n_pair][npix].  MODAL_LINEAR_RING: per ring, [n_pair][nrings], the mean over
+ * the simulations and over the longitudes of each ring,
+ *   <M_a M_b>_j = (1 / (N_lin nphi)) sum_sims sum_k M_a M_b (theta_j, phi_k),
+ * which equals the pixel mean in expectation when the weights, noise and mask depend on the
+ * ring alone; the linear term of modal_cubic and the adjoint then use it for every pixel of
+ * the ring.  Refused (MODAL_EINVAL) for a plan built with a pixel mask.  Setting a mode
+ * clears the linear-term sums (n_lin = 0, not finalised).  Checkpoints record the mode's
+ * sums and load only into a plan in the same mode. */
+#define MODAL_LINEAR_PIXEL 0
+#define MODAL_LINEAR_RING 1
+modal_status modal_set_linear_mode(modal_h h, int mode);
 /* zeta = covariance / 6 of the accumulated beta: host [n_max][n_max]. Synchronises. */
 modal_status modal_get_zeta(modal_h h, double* zeta);
 /* Clear accumulators: what & 1 -> linear-term sums, what & 2 -> covariance sums. */

@@ -16,6 +16,11 @@ What each function follows:
                    with <.> the Monte Carlo mean over Gaussian simulations (Sec. II).
   pair_means       the Monte Carlo mean <M_p M_r>_x of Sec. II ("calculated from Monte
                    Carlo simulations of Gaussian maps").
+  ring_pair_means  the same mean averaged over the longitudes of each ring: for weights,
+                   noise and mask that depend on the ring alone (the anisotropic noise
+                   and band mask of App. A) the pixel mean is a function of the ring in
+                   expectation, so the ring average estimates it with N_phi times as many
+                   samples (a reading, not printed in the paper).
   covariance_zeta  zeta = <beta beta^T> / 6 (Eq. linearterm, Sec. II with p! = 6),
                    read as the unbiased sample covariance divided by 6.
   solve_fnl        Eq. modalest and Eq. modalvariance via the Cholesky rotation
@@ -83,6 +88,13 @@ def pair_means(map_batches) -> np.ndarray:
         acc = pp if acc is None else acc + pp
         n += 1
     return acc / n
+
+
+def ring_pair_means(pairmean: np.ndarray) -> np.ndarray:
+    """Longitude average of <M_p M_r> on every ring, repeated over the ring's pixels;
+    [N_pair][nrings][nphi] -> the same shape."""
+    ring = pairmean.mean(axis=-1, keepdims=True)
+    return np.repeat(ring, pairmean.shape[-1], axis=-1)
 
 
 def cubic_beta(maps: np.ndarray, W: np.ndarray, pairmean=None) -> np.ndarray:

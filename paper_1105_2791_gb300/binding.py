@@ -30,7 +30,7 @@ EXPORTS = [
     "modal_get_rings", "modal_get_pair_mean", "modal_get_zeta", "modal_reset", "modal_set_chunk",
     "modal_sync", "modal_save_state", "modal_load_state", "modal_selftest_wait", "modal_destroy",
     "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
-    "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy",
+    "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
 ]
 MODAL_NSTAGES = 14
 
@@ -94,6 +94,7 @@ def load_library():
         "modal_get_profile": [H, c_void_p, c_void_p, c_int],
         "modal_cubic_static": [c_void_p, c_void_p, c_longlong, c_int, c_int, c_void_p, c_void_p],
         "modal_batch_create": [c_void_p, c_int, POINTER(c_void_p)],
+        "modal_set_linear_mode": [H, c_int],
         "modal_batch_cubic": [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p],
     }
     for name, args in sig.items():
@@ -178,6 +179,14 @@ def modal_linear_term(h, alm_sims, B, finalize, stream=None):
 
 def modal_cubic(h, alm, B, use_linear, beta, stream=None):
     _check(load_library().modal_cubic(h, _dev(alm), int(B), int(bool(use_linear)), _dev(beta), _stream(stream)))
+
+
+LINEAR_MODES = {"pixel": 0, "ring": 1}
+
+
+def modal_set_linear_mode(h, mode):
+    """mode: "pixel" (per-pixel Monte Carlo pair means) or "ring" (per-ring means)."""
+    _check(load_library().modal_set_linear_mode(h, LINEAR_MODES[mode]))
 
 
 def modal_batch_create(plans):

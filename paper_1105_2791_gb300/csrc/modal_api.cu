@@ -164,6 +164,7 @@ static void free_workspace(modal_plan* pl) {
     dfree(pl->ut); pl->ut = nullptr;
     dfree(pl->partial); pl->partial = nullptr;
     dfree(pl->hk); pl->hk = nullptr;
+    dfree(pl->vring); pl->vring = nullptr;
     dfree(pl->tc.bops); pl->tc.bops = nullptr;
     dfree(pl->tca.bops); pl->tca.bops = nullptr;
     pl->device_bytes -= pl->workspace_bytes;
@@ -179,6 +180,7 @@ static modal_status alloc_workspace(modal_plan* pl, int chunk) {
     CK(dalloc(pl, &pl->maps, (size_t)chunk * pl->P * pl->npix), "workspace maps");
     CK(dalloc(pl, &pl->ut, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace ut");
     CK(dalloc(pl, &pl->hk, (size_t)chunk * pl->P * pl->n_pair), "workspace hk");
+    CK(dalloc(pl, &pl->vring, (size_t)chunk * pl->P * pl->nrings), "workspace vring");
     // cubic partials: [chunk][cubic_ctas][n_max]; linear partials: [ksplit][n_pair][chunk*P]
     const size_t cub = (size_t)chunk * pl->cubic_ctas * pl->n_max;
     const size_t lin = (size_t)pl->lin_ksplit * pl->n_pair * chunk * pl->P;
@@ -207,6 +209,16 @@ static modal_status ensure_pair_buffers(modal_plan* pl) {
     return MODAL_OK;
 }
 
+static modal_status ensure_ring_buffers(modal_plan* pl) {
+    if (pl->ring_sum) return MODAL_OK;
+    const size_t n = (size_t)pl->n_pair * pl->nrings;
+    CK(dalloc(pl, &pl->ring_sum, n), "ring pair sums");
+    CK(dalloc(pl, &pl->ring_mean, n), "ring pair means");
+    CK(cudaMemset(pl->ring_sum, 0, n * sizeof(double)), "ring pair sums clear");
+    CK(cudaMemset(pl->ring_mean, 0, n * sizeof(double)), "ring pair means clear");
+    return MODAL_OK;
+}
+
 static void destroy_plan(modal_plan* pl) {
     if (!pl) return;
     cudaDeviceSynchronize();
@@ -214,6 +226,7 @@ static void destroy_plan(modal_plan* pl) {
     dfree(pl->lam); dfree(pl->filt); dfree(pl->W); dfree(pl->wring); dfree(pl->twiddle);
     dfree(pl->modeidx); dfree(pl->tiles); dfree(pl->pair_ab);
     dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->S1); dfree(pl->S2);
+    dfree(pl->ring_sum); dfree(pl->ring_mean);
     dfree(pl->solve_ws); dfree(pl->d_err);
     free_tc_tables(*pl);
     free_tc_adj_tables(*pl);
@@ -317,6 +330,7 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
     cudaGetDevice(&dev);
     pl->dev = dev;
     pl->lmax = lmax; pl->P = P; pl->nrings = grid->nrings; pl->nphi = grid->nphi; pl->prec = prec;
+    pl->has_pix_mask = grid->pix_mask ? 1 : 0;
     pl->R_half = (grid->nrings + 1) / 2;
     pl->RH = (pl->R_half + 31) / 32 * 32;
     pl->n_alm = (lmax + 1) * (lmax + 2) / 2;
@@ -458,6 +472,17 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
 
 void modal_destroy(modal_h h) { destroy_plan(h); }
 
+modal_status modal_set_linear_mode(modal_h h, int mode) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (mode != MODAL_LINEAR_PIXEL && mode != MODAL_LINEAR_RING) return set_error(MODAL_EINVAL, "unknown linear-term mode");
+    if (mode == MODAL_LINEAR_RING && h->has_pix_mask)
+        return set_error(MODAL_EINVAL, "ring-only linear term needs weights that depend on the ring alone (no pixel mask)");
+    const modal_status r = modal_reset(h, 1);
+    if (r != MODAL_OK) return r;
+    h->lin_mode = mode;
+    return MODAL_OK;
+}
+
 modal_status modal_set_chunk(modal_h h, int chunk) {
     if (check_plan(h)) return MODAL_EINVAL;
     if (chunk < 1 || chunk > 4096) return set_error(MODAL_EINVAL, "chunk must be in [1, 4096]");
@@ -497,19 +522,24 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
     if (check_plan(h)) return MODAL_EINVAL;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B > 0 && !alm_sims) return set_error(MODAL_EINVAL, "null pointer");
-    modal_status s = ensure_pair_buffers(h);
+    const bool ring = h->lin_mode == MODAL_LINEAR_RING;
+    modal_status s = ring ? ensure_ring_buffers(h) : ensure_pair_buffers(h);
     if (s != MODAL_OK) return s;
     cudaStream_t st = as_stream(stream);
     const float2* a = static_cast<const float2*>(alm_sims);
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "linear-term synthesis");
-        { STAGE(h, ST_PAIRS, st); CK(launch_pair_accumulate(*h, h->maps, nb, st), "pair accumulate"); }
+        STAGE(h, ST_PAIRS, st);
+        if (ring) CK(launch_pair_ring(*h, h->maps, nb, st), "ring pair sums");
+        else CK(launch_pair_accumulate(*h, h->maps, nb, st), "pair accumulate");
     }
     h->n_lin += B;
     if (finalize) {
         if (h->n_lin < 1) return set_error(MODAL_ESTATE, "finalize with no linear-term simulations");
-        { STAGE(h, ST_PAIRS, st); CK(launch_pair_finalize(*h, st), "pair finalize"); }
+        STAGE(h, ST_PAIRS, st);
+        if (ring) CK(launch_ring_finalize(*h, st), "ring pair means");
+        else CK(launch_pair_finalize(*h, st), "pair finalize");
         h->lin_final = 1;
     }
     return MODAL_OK;
@@ -528,12 +558,20 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
         const int nb = std::min(h->chunk, B - b0);
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "cubic synthesis");
         { STAGE(h, ST_CUBIC, st); CK(launch_cubic(*h, h->maps, nb, cub, st), "cubic"); }
+        int splits = h->lin_ksplit;
         if (use_linear) {
             STAGE(h, ST_LINEAR, st);
-            if (h->prec == MODAL_FP32) CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm");
-            else CK(launch_linear_tc(*h, h->maps, nb, lin, st), "linear gemm");
+            if (h->lin_mode == MODAL_LINEAR_RING) {
+                // ring sums of the maps from the m = 0 Legendre sums still in h->delta
+                CK(launch_linear_ring(*h, nb, lin, st), "linear term (ring)");
+                splits = 1;
+            } else if (h->prec == MODAL_FP32) {
+                CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm");
+            } else {
+                CK(launch_linear_tc(*h, h->maps, nb, lin, st), "linear gemm");
+            }
         }
-        { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, beta + (size_t)b0 * h->n_max, st), "beta finalize"); }
+        { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, splits, beta + (size_t)b0 * h->n_max, st), "beta finalize"); }
     }
     return MODAL_OK;
 }
@@ -609,7 +647,13 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
         const int nb = std::min(h->chunk, B - b0);
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "backward synthesis");
         { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_weights(*h, g + (size_t)b0 * h->n_max, nb, h->hk, st), "adjoint weights"); }
-        { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear, h->maps, st), "adjoint pixel"); }
+        {
+            STAGE(h, ST_ADJ_PIXEL, st);
+            const bool ring = use_linear && h->lin_mode == MODAL_LINEAR_RING;
+            if (ring) CK(launch_vring(*h, h->hk, nb, h->vring, st), "adjoint ring term");
+            CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear && !ring, ring ? h->vring : nullptr, h->maps, st),
+               "adjoint pixel");
+        }
         {
             // split precisions: the r2c kernel also records each map's max |U~| for the operand scale
             STAGE(h, ST_R2C, st);
@@ -693,6 +737,10 @@ modal_status modal_get_pair_mean(modal_h h, float* out, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
     if (!out) return set_error(MODAL_EINVAL, "out is NULL");
     if (!h->lin_final) return set_error(MODAL_ESTATE, "pair mean not finalised");
+    if (h->lin_mode == MODAL_LINEAR_RING) {
+        CK(launch_ring_mean_float(*h, out, as_stream(stream)), "ring pair means copy");
+        return MODAL_OK;
+    }
     CK(cudaMemcpyAsync(out, h->pair_mean, (size_t)h->n_pair * h->npix * sizeof(float), cudaMemcpyDeviceToDevice,
                        as_stream(stream)), "pair mean copy");
     return MODAL_OK;
@@ -715,8 +763,9 @@ modal_status modal_get_zeta(modal_h h, double* zeta) {
 modal_status modal_reset(modal_h h, int what) {
     if (check_plan(h)) return MODAL_EINVAL;
     CK(cudaDeviceSynchronize(), "reset sync");
-    if ((what & 1) && h->pair_sum) {
-        CK(cudaMemset(h->pair_sum, 0, (size_t)h->n_pair * h->npix * sizeof(double)), "reset pair sums");
+    if (what & 1) {
+        if (h->pair_sum) CK(cudaMemset(h->pair_sum, 0, (size_t)h->n_pair * h->npix * sizeof(double)), "reset pair sums");
+        if (h->ring_sum) CK(cudaMemset(h->ring_sum, 0, (size_t)h->n_pair * h->nrings * sizeof(double)), "reset ring sums");
         h->n_lin = 0;
         h->lin_final = 0;
     }
@@ -760,7 +809,8 @@ modal_status modal_save_state(modal_h h, const char* path) {
     StateHeader hd{};
     std::memcpy(hd.magic, "MODALST1", 8);
     hd.lmax = h->lmax; hd.P = h->P; hd.nrings = h->nrings; hd.nphi = h->nphi;
-    hd.n_lin = h->n_lin; hd.n_cov = h->n_cov; hd.lin_final = h->lin_final; hd.has_pairs = h->pair_sum ? 1 : 0;
+    hd.n_lin = h->n_lin; hd.n_cov = h->n_cov; hd.lin_final = h->lin_final;
+    hd.has_pairs = (h->lin_mode == MODAL_LINEAR_RING) ? (h->ring_sum ? 2 : 0) : (h->pair_sum ? 1 : 0);
     bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
     auto dump = [&](const double* d, size_t n) {
         std::vector<double> buf(std::min<size_t>(n, (size_t)1 << 24));
@@ -770,7 +820,8 @@ modal_status modal_save_state(modal_h h, const char* path) {
             else ok = std::fwrite(buf.data(), sizeof(double), m, f) == m;
         }
     };
-    if (hd.has_pairs) dump(h->pair_sum, (size_t)h->n_pair * h->npix);
+    if (hd.has_pairs == 1) dump(h->pair_sum, (size_t)h->n_pair * h->npix);
+    if (hd.has_pairs == 2) dump(h->ring_sum, (size_t)h->n_pair * h->nrings);
     dump(h->S1, h->n_max);
     dump(h->S2, (size_t)h->n_max * h->n_max);
     ok = (std::fclose(f) == 0) && ok;
@@ -791,8 +842,12 @@ modal_status modal_load_state(modal_h h, const char* path) {
         return set_error(MODAL_EINVAL, "state file does not match this plan");
     }
     CK(cudaDeviceSynchronize(), "load sync");
+    if (hd.has_pairs && (hd.has_pairs == 2) != (h->lin_mode == MODAL_LINEAR_RING)) {
+        std::fclose(f);
+        return set_error(MODAL_EINVAL, "state file holds the other linear-term mode");
+    }
     if (hd.has_pairs) {
-        modal_status s = ensure_pair_buffers(h);
+        modal_status s = (hd.has_pairs == 2) ? ensure_ring_buffers(h) : ensure_pair_buffers(h);
         if (s != MODAL_OK) { std::fclose(f); return s; }
     }
     auto load = [&](double* d, size_t n) {
@@ -803,7 +858,8 @@ modal_status modal_load_state(modal_h h, const char* path) {
                  cudaMemcpy(d + off, buf.data(), m * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
         }
     };
-    if (hd.has_pairs) load(h->pair_sum, (size_t)h->n_pair * h->npix);
+    if (hd.has_pairs == 1) load(h->pair_sum, (size_t)h->n_pair * h->npix);
+    if (hd.has_pairs == 2) load(h->ring_sum, (size_t)h->n_pair * h->nrings);
     load(h->S1, h->n_max);
     load(h->S2, (size_t)h->n_max * h->n_max);
     std::fclose(f);
@@ -812,7 +868,8 @@ modal_status modal_load_state(modal_h h, const char* path) {
     h->n_cov = hd.n_cov;
     h->lin_final = 0;
     if (hd.has_pairs && hd.lin_final && h->n_lin > 0) {
-        CK(launch_pair_finalize(*h, 0), "pair finalize");
+        if (hd.has_pairs == 2) CK(launch_ring_finalize(*h, 0), "ring pair means");
+        else CK(launch_pair_finalize(*h, 0), "pair finalize");
         CK(cudaDeviceSynchronize(), "load sync");
         h->lin_final = 1;
     }

@@ -97,6 +97,12 @@ struct Plan {
     int cubic_ctas = 0;          // CTAs per map in the cubic kernel
     int lin_ksplit = 0;          // K splits in the linear-term GEMM
     float* hk = nullptr;         // [chunk][P][n_pair] adjoint weights
+    // ring-only linear term (modal_set_linear_mode)
+    int lin_mode = 0;            // MODAL_LINEAR_PIXEL or MODAL_LINEAR_RING
+    int has_pix_mask = 0;        // W varies along rings: ring mode refused
+    double* ring_sum = nullptr;  // [n_pair][nrings]
+    double* ring_mean = nullptr; // [n_pair][nrings]
+    float* vring = nullptr;      // [chunk][P][nrings] adjoint pair-mean term
     double* solve_ws = nullptr;  // [n_max][n_max] + vectors
     int* d_err = nullptr;        // device error word
     size_t device_bytes = 0;
@@ -154,13 +160,22 @@ cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmaps_p, cons
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);   // k_linear_tc.cu
+// lin_splits: K splits summed from lin_partial ([lin_splits][n_pair][B P])
 cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* cub_partial,
-                                 const double* lin_partial, double* beta, cudaStream_t st);
+                                 const double* lin_partial, int lin_splits, double* beta, cudaStream_t st);
 cudaError_t launch_pair_accumulate(Plan& pl, const float* maps, int B, cudaStream_t st);
 cudaError_t launch_pair_finalize(Plan& pl, cudaStream_t st);
 cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, cudaStream_t st);
+// pair-mean term: per pixel from pl.pair_mean (use_linear, pixel mode) or per ring from
+// vring [B][P][nrings] (ring mode, use_linear = 0); neither when both are off.
 cudaError_t launch_adjoint_u(Plan& pl, const float* maps, int B, const float* hk, int use_linear,
-                             float* u, cudaStream_t st);
+                             const float* vring, float* u, cudaStream_t st);
+// k_ring_linear.cu
+cudaError_t launch_pair_ring(Plan& pl, const float* maps, int B, cudaStream_t st);
+cudaError_t launch_ring_finalize(Plan& pl, cudaStream_t st);
+cudaError_t launch_linear_ring(Plan& pl, int B, double* lin, cudaStream_t st);
+cudaError_t launch_vring(Plan& pl, const float* hk, int B, float* vring, cudaStream_t st);
+cudaError_t launch_ring_mean_float(Plan& pl, float* out, cudaStream_t st);
 // k_solve.cu
 cudaError_t launch_cov_accumulate(Plan& pl, const double* beta, int B, cudaStream_t st);
 cudaError_t launch_zeta(Plan& pl, double* zeta, cudaStream_t st);

@@ -20,6 +20,7 @@ class Plan:
         self.lmax, self.P, self.nrings, self.nphi = info.lmax, info.P, info.nrings, info.nphi
         self.n_alm, self.n_max, self.n_pair, self.npix = info.n_alm, info.n_max, info.n_pair, info.npix
         self.prec = info.prec
+        self.linear_mode = "pixel"
 
     # -- lifecycle
     def close(self):
@@ -35,6 +36,12 @@ class Plan:
 
     def info(self):
         return B.modal_get_info(self.h)
+
+    def set_linear_mode(self, mode):
+        """"pixel" (default) or "ring": how the Monte Carlo pair means of the linear term
+        are kept (clears the linear-term sums)."""
+        B.modal_set_linear_mode(self.h, mode)
+        self.linear_mode = mode
 
     # -- per-map stages
     def synthesize(self, alm, out=None):
@@ -84,7 +91,9 @@ class Plan:
         return B.modal_get_rings(self.h)
 
     def pair_mean(self, device="cuda"):
-        out = torch.empty((self.n_pair, self.npix), dtype=torch.float32, device=device)
+        """[n_pair][npix] (pixel mode) or [n_pair][nrings] (ring mode) float32."""
+        n = self.nrings if self.linear_mode == "ring" else self.npix
+        out = torch.empty((self.n_pair, n), dtype=torch.float32, device=device)
         B.modal_get_pair_mean(self.h, out)
         return out
 

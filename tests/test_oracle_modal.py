@@ -337,3 +337,51 @@ def test_planted_alpha_mistake_is_caught():
     bad = np.array([16 * math.pi ** 2 * np.sum(wx * (A[p] * A[r] * D[s] + A[p] * D[r] * A[s]))
                     for (p, r, s) in modal.mode_list(P)])        # one permutation dropped
     assert np.max(np.abs(bad - ref)) > 1e-3 * np.max(np.abs(ref))
+
+
+def _ring_parseval(D: np.ndarray) -> np.ndarray:
+    """Longitude mean of M_a M_b on each ring from the Fourier coefficients alone:
+    D_a0 D_b0 + 2 Re sum_{m>=1} D_am conj(D_bm) (Parseval on N_phi > 2 l_max points)."""
+    P = D.shape[0]
+    out = []
+    for (a, b) in modal.pair_list(P):
+        v = np.real(D[a, 0]) * np.real(D[b, 0]) + 2.0 * np.real(np.sum(D[a, 1:] * np.conj(D[b, 1:]), axis=0))
+        out.append(v)
+    return np.stack(out)                                   # [N_pair][R]
+
+
+def test_ring_pair_means_match_parseval_on_each_ring():
+    """The ring-only pair means (pixel means averaged over longitudes) equal the Fourier-
+    space form of the same ring average for every ring and pair."""
+    L, P, R, nphi = 20, 4, 21, 64
+    basis, cl = simgen.shifted_legendre_basis(L, P), simgen.cl_model(L)
+    filt = sht.filter_table(basis, cl)
+    mu, _ = sht.gl_nodes(R)
+    sims = simgen.gaussian_alm(cl, 3, seed=17, stream=simgen.STREAM_LINEAR)
+    pm = modal.pair_means([sht.synthesize(a, L, filt, mu, nphi) for a in sims])
+    ring = modal.ring_pair_means(pm)
+    assert ring.shape == pm.shape
+    expect = np.mean([_ring_parseval(sht.legendre_sums(a, L, filt, mu)) for a in sims], axis=0)
+    np.testing.assert_allclose(ring[:, :, 0], expect, rtol=1e-12, atol=1e-12 * np.abs(expect).max())
+    assert np.all(ring == ring[:, :, :1])                  # constant along each ring
+    # a planted mistake (averaging over rings instead of longitudes) fails the pin
+    wrong = np.repeat(pm.mean(axis=1, keepdims=True), R, axis=1)
+    assert not np.allclose(wrong[:, :, 0], expect, rtol=1e-6)
+
+
+def test_ring_pair_means_equal_pixel_means_for_axisymmetric_sims():
+    """Simulations with a_lm = 0 for m > 0 are constant along rings, so the ring-only and
+    the pixel means coincide, and so do the two linear terms of beta."""
+    L, P, R, nphi = 16, 3, 17, 64
+    basis, cl = simgen.shifted_legendre_basis(L, P), simgen.cl_model(L)
+    filt = sht.filter_table(basis, cl)
+    mu, w = sht.gl_nodes(R)
+    sims = simgen.gaussian_alm(cl, 2, seed=18, stream=simgen.STREAM_LINEAR)
+    m_of = np.concatenate([np.full(L - m + 1, m) for m in range(L + 1)])
+    sims[:, m_of > 0] = 0.0
+    pm = modal.pair_means([sht.synthesize(a, L, filt, mu, nphi) for a in sims])
+    np.testing.assert_allclose(modal.ring_pair_means(pm), pm, rtol=1e-12, atol=1e-14 * np.abs(pm).max())
+    maps = sht.synthesize(simgen.gaussian_alm(cl, 1, seed=19)[0], L, filt, mu, nphi)
+    W = modal.pixel_weights(w, nphi)
+    np.testing.assert_allclose(modal.cubic_beta(maps, W, modal.ring_pair_means(pm)), modal.cubic_beta(maps, W, pm),
+                               rtol=1e-10, atol=1e-12)
