@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-rings", type=int, default=8, help="rings in the CPU-baseline sample")
     ap.add_argument("--lmax", type=int, default=2000, help="smaller l_max for profiler captures only")
     ap.add_argument("--chunk", type=int, default=32, help="maps per internal pass of the library")
+    ap.add_argument("--linear", choices=["pixel", "ring"], default="pixel",
+                    help="Monte Carlo pair means per pixel (default) or per ring (axisymmetric weights)")
     return ap.parse_args()
 
 
@@ -178,6 +180,8 @@ def run_gpu(args):
                 return None
             raise
         plan.set_chunk(min(args.chunk, B))
+        if args.linear == "ring":
+            plan.set_linear_mode("ring")
         plan.linear_term(lin_sims, finalize=True)      # a mean to subtract from the first step on
         return plan
 
@@ -280,7 +284,8 @@ def run_gpu(args):
         "config": {"workload": "lmax=%d GL %dx%d, P=%d (n_max=%d), batch %d maps/step/GPU, %s" % (
                        L, R, nphi, P, plan.n_max, B, prec),
                    "lmax": L, "nrings": R, "nphi": nphi, "P": P, "n_max": plan.n_max, "batch_per_gpu": B,
-                   "precision": prec, "l2": "inputs and intermediates > L2 (no flush)",
+                   "precision": prec, "linear_means": args.linear,
+                   "l2": "inputs and intermediates > L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk,
         "gpu_launches": int(launches),
