@@ -1,0 +1,123 @@
+"""The adjoint and precision-sweep workloads at their full sizes.
+
+Adjoint: l_max = 1000 on 1001 x 2048 rings, P = 12 (364 coefficients), 32 maps of signal
+plus anisotropic noise on a band-masked sky, linear term from noisy simulations; the
+gradient of L = sum_n w_n beta_n from the hand-written adjoint against central finite
+differences of L in 64 random coefficients.  beta is exactly cubic in a_lm, so the
+central difference has no truncation error from the quadratic part and its cubic part
+(h^2/6 times the third derivative along one coefficient) is negligible; the step is
+10 sigma_lm so that the difference stands well above FP32 rounding of beta.
+
+Precision sweep: l_max = 2000, 2001 x 4096, P = 16, Gaussian maps G and non-Gaussian maps
+T = G + 50 (G^2 - <G^2>) built on the GPU grid; beta on sampled rings (ring mask) in every
+precision against the FP64 oracle on a subset of maps.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import simgen
+from oracle import modal as om, sht as osh
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [p for p in os.environ.get("MODAL_TEST_PRECS", "fp32,fp16x3,3xtf32").split(",") if p]
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _plan(M, L, P, basis, cl, R, nphi, prec, **kw):
+    try:
+        return M.Plan(L, P, basis, cl, R, nphi, prec=prec, **kw)
+    except M.ModalError as e:
+        if prec != "fp32" and "not supported" in str(e):
+            pytest.skip("precision %s not built" % prec)
+        raise
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_adjoint_workload_against_finite_differences(prec):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1105_2791_gb300 as M
+    L, P, R, nphi, nb = 1000, 12, 1001, 2048, 32
+    basis, cl = simgen.shifted_legendre_basis(L, P), simgen.cl_model(L)
+    s0 = 0.1 * cl[L]
+    sig = simgen.noise_sigma_rings(R, s0)
+    cl_tot = cl + np.where(np.arange(L + 1) >= 2, 2 * s0, 0.0)
+    mask = simgen.band_mask(R, 20.0)
+    plan = _plan(M, L, P, basis, cl_tot, R, nphi, prec, ring_mask=mask)
+    mu, w = plan.rings()
+    omega = w * 2 * math.pi / nphi
+
+    def noisy(n, seed, stream):
+        sa = torch.from_numpy(simgen.gaussian_alm(cl, n, seed=seed, stream=stream).astype(np.complex64)).cuda()
+        xi = simgen.pixel_normals(R, nphi, n, seed=seed, stream=simgen.STREAM_NOISE)
+        nmap = (sig / np.sqrt(omega))[None, :, None] * xi
+        return (sa + plan.analyze(torch.from_numpy(nmap.astype(np.float32)).cuda())).contiguous()
+
+    plan.linear_term(noisy(8, 101, simgen.STREAM_LINEAR), finalize=True)
+    a = noisy(nb, 102, simgen.STREAM_DATA)
+    wts = torch.from_numpy(np.random.default_rng(103).standard_normal((nb, plan.n_max))).cuda()
+    grad = plan.backward(a, wts, use_linear=True)
+    # 64 random coefficients of map 5 (real parts; m >= 2 so that C_l > 0)
+    l_of, m_of = simgen.lm_arrays(L)
+    cand = np.nonzero(l_of >= 2)[0]
+    idx = simgen.random_subset(len(cand), 64, seed=104)
+    idx = cand[idx]
+    b0 = 5
+    h = 10.0 * np.sqrt(cl_tot[l_of[idx]] / np.where(m_of[idx] > 0, 2.0, 1.0))
+    pert = a[b0:b0 + 1].repeat(2 * len(idx), 1).clone()
+    hh = torch.from_numpy(np.concatenate([h, -h]).astype(np.float32)).cuda()
+    ii = torch.from_numpy(np.concatenate([idx, idx])).cuda()
+    pert[torch.arange(2 * len(idx), device="cuda"), ii] += hh.to(torch.complex64)
+    beta = plan.cubic(pert.contiguous(), use_linear=True).double()
+    Lval = (beta * wts[b0:b0 + 1]).sum(dim=1).cpu().numpy()
+    fd = (Lval[:len(idx)] - Lval[len(idx):]) / (2.0 * h)
+    g = grad[b0, torch.from_numpy(idx).cuda()].real.double().cpu().numpy()
+    plan.sync()
+    plan.close()
+    err = np.max(np.abs(g - fd)) / np.max(np.abs(fd))
+    print("adjoint workload lmax=1000 P=12 %s: max |grad - central difference| / max |cd| = %.3g" % (prec, err))
+    assert err <= 1e-3
+
+
+@pytest.mark.parametrize("prec,bound", [(p, 1e-5) for p in PRECS] + [("bf16x3", 1e-2), ("bf16", 1e-1)])
+def test_precision_sweep_gaussian_and_nongaussian_lmax2000(prec, bound):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1105_2791_gb300 as M
+    L, P, R, nphi = 2000, 16, 2001, 4096
+    cl = simgen.cl_model(L)
+    # G on the grid: a one-mode plan whose filter is 1 (basis sqrt(C_l)) synthesises the raw map
+    raw = M.Plan(L, 1, np.sqrt(cl)[None, :], cl, R, nphi, prec="fp32")
+    aG = torch.from_numpy(simgen.gaussian_alm(cl, 2, seed=2002, stream=simgen.STREAM_NG).astype(np.complex64)).cuda()
+    G = raw.synthesize(aG)[:, 0].double()
+    mu, w = raw.rings()
+    g2 = float(np.sum((2 * np.arange(L + 1) + 1) / (4 * math.pi) * cl))
+    T = G + 50.0 * (G * G - g2)
+    aT = raw.analyze(T.float().contiguous())
+    raw.close()
+    alm = torch.cat([aG, aT]).contiguous()                # two Gaussian, two non-Gaussian maps
+    rings = np.array([0, 3, 517, 1000, 1998])
+    mask = np.zeros(R)
+    mask[rings] = 1.0
+    basis = simgen.shifted_legendre_basis(L, P)
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec, ring_mask=mask)
+    beta = plan.cubic(alm).cpu().numpy()
+    plan.sync()
+    plan.close()
+    filt = osh.filter_table(basis, cl)
+    W = om.pixel_weights(w[rings], nphi)
+    host = alm.cpu().numpy().astype(np.complex128)
+    errs = []
+    for b in range(4):
+        ref = om.cubic_beta(osh.synthesize(host[b], L, filt, mu[rings], nphi), W)
+        errs.append(_rel(beta[b], ref))
+    print("precision sweep lmax=2000 %s: beta rel err G %s, T = G + 50 (G^2 - <G^2>) %s" % (prec, errs[:2], errs[2:]))
+    assert max(errs) <= bound
