@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=32, help="maps per internal pass of the library")
     ap.add_argument("--linear", choices=["pixel", "ring"], default="pixel",
                     help="Monte Carlo pair means per pixel (default) or per ring (axisymmetric weights)")
+    ap.add_argument("--workload", choices=["l2000", "mixed"], default="l2000",
+                    help="l2000: the headline step; mixed: the batched Monte Carlo coefficient pass over "
+                         "l_max 500 / 1000 / 2000 maps (2:1:1, 512 per step) as one captured graph")
     return ap.parse_args()
 
 
@@ -345,6 +348,84 @@ def cpu_baseline(nring_sample):
                       "cubic with linear term, adjoint; %.1f s, extrapolated by ring count" % (k, dt)}
 
 
+def run_mixed(args):
+    """Batched Monte Carlo coefficient pass: 256 maps at l_max = 500, 128 at 1000 and 128 at
+    2000 per step (P = 16, 20-degree band mask, linear term), one plan per l_max grouped in a
+    modal batch and replayed as one CUDA graph."""
+    import torch
+    import torch.distributed as dist
+
+    import simgen
+    import paper_1105_2791_gb300 as M
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P = 16
+    prec = "fp16x3" if args.prec == "auto" else args.prec
+    mix = [(500, 256), (1000, 128), (2000, 128)]
+    plans, alms = [], []
+    for i, (L, nb) in enumerate(mix):
+        R, nphi = L + 1, 1 << int(math.ceil(math.log2(2 * L + 2)))
+        cl = simgen.cl_model(L)
+        pl = M.Plan(L, P, simgen.shifted_legendre_basis(L, P), cl, R, nphi, prec=prec,
+                    ring_mask=simgen.band_mask(R, 20.0))
+        pl.set_chunk(min(args.chunk, nb))
+        pl.linear_term(torch.from_numpy(simgen.gaussian_alm(cl, 4, seed=50 + i, stream=simgen.STREAM_LINEAR)
+                                        .astype(np.complex64)).to(dev), finalize=True)
+        plans.append(pl)
+        alms.append(torch.from_numpy(simgen.gaussian_alm(cl, nb, seed=60 + i + 1000 * rank).astype(np.complex64)).to(dev))
+    batch = M.Batch(plans)
+    n_maps = sum(nb for _, nb in mix)
+    K, W = args.steps, args.warmup
+    for _ in range(W):
+        batch.cubic(alms, use_linear=True, graph=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    for pl in plans:
+        M.modal_get_profile(pl.h)
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        ev0.record(st)
+        for _ in range(K):
+            batch.cubic(alms, use_linear=True, graph=True)
+        ev1.record(st)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    value = job_throughput(n_maps, K, world, ms)
+    # kernels per step: one direct (uncaptured) pass, counted by the plans
+    for pl in plans:
+        M.modal_get_profile(pl.h)
+    batch.cubic(alms, use_linear=True, graph=False)
+    torch.cuda.synchronize()
+    launches = sum(sum(n for (_, n) in M.modal_get_profile(pl.h).values()) for pl in plans)
+    for pl in plans:
+        pl.sync()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "maps/s, mixed l_max 500/1000/2000 (2:1:1) coefficient pass with linear term, P=16",
+            "value": round(value, 3), "unit": "maps/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(ms / K, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "3xtf32": "tf32x3", "fp16x3": "f16x3", "bf16x3": "bf16x3", "bf16": "bf16"}[prec],
+            "data": "synthetic",
+            "config": {"workload": "batched Monte Carlo: 256 @ l_max 500, 128 @ 1000, 128 @ 2000 per step, "
+                                   "P=16, band mask, one captured CUDA graph", "maps_per_step": n_maps,
+                       "precision": prec, "l2": "inputs and intermediates > L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clocks.summary(), "gpu_launches": int(launches) * K,
+            "roofline": None, "e2e": None,
+        }), flush=True)
+    batch.close()
+    for pl in plans:
+        pl.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -376,6 +457,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     else:
         run_gpu(args)
 
