@@ -34,6 +34,11 @@ What each function follows:
                    m >= 0 (not in the paper; chain rule through cubic_beta and synthesis).
   bivector_*       Eq. ic_bivector, ic_bivectorinv, bivecvariance and the analytic
                    Cholesky factor of Sec. III.B.
+  bivector_fit,    the bivector model with an ideal covariance zeta0 = L0 L0^T (full sky,
+  solve_fnl_bivector  homogeneous noise): zeta ~ L0 (I + bt bt^T) L0^T, bt = sqrt(l1) u1 from
+                   the largest eigenpair of L0^-1 zeta L0^-T - I (a reading: Sec. III.B says
+                   only that bt is estimated from simulations), and the estimate of Eq.
+                   modalest with the inverse of Eq. ic_bivectorinv in the whitened basis.
 
 Pins: tests/test_oracle_modal.py (Gaunt brute force on an exact-cubic grid,
 closed-form covariance and mean, zero mean, larger variance without the linear
@@ -274,3 +279,31 @@ def bivector_variance(alpha: np.ndarray, bt: np.ndarray) -> float:
     a2 = alpha @ alpha
     ab = alpha @ bt
     return (1.0 / a2) * (1.0 + ab * ab / (a2 * (1.0 + bt @ bt) - ab * ab))
+
+
+def bivector_fit(zeta: np.ndarray, zeta0: np.ndarray) -> np.ndarray:
+    """bt with zeta ~ L0 (I + bt bt^T) L0^T: largest eigenpair (l1, u1) of the whitened
+    L0^-1 zeta L0^-T - I, bt = sqrt(max(l1, 0)) u1, sign fixed by a non-negative sum."""
+    L0 = np.linalg.cholesky(zeta0)
+    Y = solve_triangular(L0, zeta, lower=True)
+    Zw = solve_triangular(L0, Y.T, lower=True)
+    Zw = 0.5 * (Zw + Zw.T) - np.eye(zeta.shape[0])
+    lam, vec = np.linalg.eigh(Zw)
+    u = vec[:, -1]
+    if u.sum() < 0:
+        u = -u
+    return math.sqrt(max(lam[-1], 0.0)) * u
+
+
+def solve_fnl_bivector(zeta0: np.ndarray, bt: np.ndarray, alpha: np.ndarray, betas: np.ndarray):
+    """Eq. modalest with zeta = L0 (I + bt bt^T) L0^T: alpha' = L0^-1 alpha, beta' = L0^-1 beta,
+    the inverse of Eq. ic_bivectorinv, E = alpha'^T Z^-1 beta' / alpha'^T Z^-1 alpha', and
+    sigma^2 = 6 x the variance of Eq. bivecvariance (zeta = <beta beta^T> / 6)."""
+    L0 = np.linalg.cholesky(zeta0)
+    a = solve_triangular(L0, alpha, lower=True)
+    B = solve_triangular(L0, np.atleast_2d(betas).T, lower=True)          # [n][B]
+    Zinv = bivector_inverse(bt)
+    norm = a @ Zinv @ a
+    fnl = (a @ Zinv @ B) / norm
+    return fnl, math.sqrt(6.0 * bivector_variance(a, bt))
+

@@ -385,3 +385,27 @@ def test_ring_pair_means_equal_pixel_means_for_axisymmetric_sims():
     W = modal.pixel_weights(w, nphi)
     np.testing.assert_allclose(modal.cubic_beta(maps, W, modal.ring_pair_means(pm)), modal.cubic_beta(maps, W, pm),
                                rtol=1e-10, atol=1e-12)
+
+
+def test_bivector_fit_and_solve_reduce_to_the_full_solve():
+    """For a covariance that is exactly L0 (I + b b^T) L0^T the fit returns b, and the
+    bivector estimate and sigma equal the general Cholesky solve of Eq. modalest."""
+    g = np.random.default_rng(21)
+    n = 9
+    A = g.standard_normal((n, n))
+    zeta0 = A @ A.T + n * np.eye(n)
+    b = np.abs(g.standard_normal(n)) + 0.1                # positive sum fixes the sign convention
+    L0 = np.linalg.cholesky(zeta0)
+    zeta = L0 @ (np.eye(n) + np.outer(b, b)) @ L0.T
+    np.testing.assert_allclose(modal.bivector_fit(zeta, zeta0), b, rtol=1e-10, atol=1e-12)
+    alpha = g.standard_normal(n)
+    betas = g.standard_normal((4, n))
+    fnl, sigma = modal.solve_fnl_bivector(zeta0, b, alpha, betas)
+    fnl_ref, sigma_ref = modal.solve_fnl(zeta, alpha, betas)
+    np.testing.assert_allclose(fnl, fnl_ref, rtol=1e-10, atol=1e-12)
+    assert sigma == pytest.approx(sigma_ref, rel=1e-10)
+    # a planted mistake (the inverse without the 1 + |b|^2 denominator) fails the pin
+    wrong = np.eye(n) - np.outer(b, b)
+    a = np.linalg.solve(L0, alpha)
+    B = np.linalg.solve(L0, betas.T)
+    assert not np.allclose((a @ wrong @ B) / (a @ wrong @ a), fnl_ref, rtol=1e-6)
