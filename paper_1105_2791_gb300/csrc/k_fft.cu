@@ -183,6 +183,62 @@ __device__ __forceinline__ void fft_passes(float2* buf, int tl, const float2* __
     }
 }
 
+// The last pass of an N-point transform (NS = N / R) with its outputs handed to
+// store(index, value) instead of shared memory: thread tl holds elements j + r NS of
+// butterflies j = tl + T u, so the threads of a warp store consecutive indices.
+template <int SIGN, int N, int NS, class Store>
+__device__ __forceinline__ void fft_passes_out(float2* buf, int tl, const float2* __restrict__ tw, Store store) {
+    constexpr int R = (N / NS >= 16) ? 16 : N / NS;
+    if constexpr (NS * R < N) {
+        stockham_pass<SIGN, R, N, NS>(buf, tl, tw);
+        fft_passes_out<SIGN, N, NS * R>(buf, tl, tw + (R - 1) * NS, store);
+    } else {
+        constexpr int NB = 16 / R;
+        constexpr int T = N / 16;
+        float2 v[16];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int j = tl + T * u;
+            const int k = j & (NS - 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 x = buf[pad_at<NS>(j, r)];
+                if (r > 0 && NS > 1) {
+                    float2 w = __ldg(&tw[(r - 1) * NS + k]);
+                    if (SIGN < 0) w.y = -w.y;
+                    x = cmul(x, w);
+                }
+                v[u * R + r] = x;
+            }
+            dft<SIGN, R>(v + u * R);
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int j = tl + T * u;
+            const int k = j & (NS - 1);
+            const int d = R * (j - k) + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) store(d + r * NS, v[u * R + r]);
+        }
+    }
+}
+
+// The first pass (radix 16, NS = 1) with its inputs taken from load(index) instead of
+// shared memory (thread tl reads elements tl + r N / 16: consecutive across a warp), then
+// the remaining passes in shared memory.
+template <int SIGN, int N, class Load>
+__device__ __forceinline__ void fft_passes_in(float2* buf, int tl, const float2* __restrict__ tw, Load load) {
+    constexpr int T = N / 16;
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = load(tl + r * T);
+    dft<SIGN, 16>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[pad16(16 * tl) + r] = v[r];
+    __syncthreads();
+    fft_passes<SIGN, N, 16>(buf, tl, tw + 15);
+}
+
 // Padded transform stride in float2: N + N/16 for the in-transform padding, + 4 so that
 // the transforms of one CTA start 8 banks apart (the (m, ring pair) loads and the
 // U~ reads, where the ring pair varies fastest, are then free of bank conflicts).
@@ -244,18 +300,15 @@ k_ring_c2r(int L, int R, int R_half, int RH, const float2* __restrict__ delta, c
     }
     __syncthreads();
     const int q = threadIdx.x / T, tl = threadIdx.x % T;
-    fft_passes<+1, N, 1>(buf + q * NP, tl, tw);
-    // four consecutive longitudes per thread: four 8-byte shared loads, two 16-byte stores
-    float* out = maps + (int64_t)mp * R * N;
-    const int n4 = (ntr * N) >> 2;
-    for (int i = threadIdx.x; i < n4; i += FFT_THREADS) {
-        const int qq = (4 * i) >> LOG2N, k = (4 * i) & (N - 1);
-        const int jn = j0 + qq, js = R - 1 - jn;
-        const float2* b = buf + qq * NP + pad16(k);      // k .. k+3 lie in one padded group of 16
-        const float2 z0 = b[0], z1 = b[1], z2 = b[2], z3 = b[3];
-        *reinterpret_cast<float4*>(out + (int64_t)jn * N + k) = make_float4(z0.x, z1.x, z2.x, z3.x);
-        if (js != jn) *reinterpret_cast<float4*>(out + (int64_t)js * N + k) = make_float4(z0.y, z1.y, z2.y, z3.y);
-    }
+    // the last pass stores the north (Re) and south (Im) rings straight to global memory
+    const int jn = j0 + q, js = R - 1 - jn;
+    const bool valid = q < ntr, south = valid && js != jn;
+    float* on = maps + ((int64_t)mp * R + (valid ? jn : 0)) * N;
+    float* os = maps + ((int64_t)mp * R + (south ? js : 0)) * N;
+    fft_passes_out<+1, N, 1>(buf + q * NP, tl, tw, [&](int k, float2 z) {
+        if (valid) on[k] = z.x;
+        if (south) os[k] = z.y;
+    });
 }
 
 // grid: (ceil(R_half / RPB), nmp).  ut layout [nmp][L+1][2][RH].  If amax is not null,
@@ -275,42 +328,20 @@ k_ring_r2c(int L, int R, int R_half, int RH, int P, const float* __restrict__ ma
     const int mp = blockIdx.y;
     const int j0 = blockIdx.x * RPB;
     const int ntr = min(RPB, R_half - j0);
-    const float* in = maps + (int64_t)mp * R * N;
-    // (ring pair, 4 consecutive longitudes) items: two 16-byte loads each, FFT_LB items
-    // per thread loaded before any is stored.
-    constexpr int nitem = (RPB * N) >> 2;
-    for (int i0 = threadIdx.x; i0 < nitem; i0 += FFT_LB * FFT_THREADS) {
-        float4 xn[FFT_LB], xs[FFT_LB];
-#pragma unroll
-        for (int u = 0; u < FFT_LB; ++u) {
-            const int i = i0 + u * FFT_THREADS;
-            const int qq = (4 * i) >> LOG2N, k = (4 * i) & (N - 1);
-            const int jn = j0 + qq, js = R - 1 - jn;
-            xn[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            xs[u] = xn[u];
-            if (i < nitem && qq < ntr) {
-                xn[u] = *reinterpret_cast<const float4*>(in + (int64_t)jn * N + k);
-                if (js != jn) xs[u] = *reinterpret_cast<const float4*>(in + (int64_t)js * N + k);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < FFT_LB; ++u) {
-            const int i = i0 + u * FFT_THREADS;
-            if (i >= nitem) break;
-            const int qq = (4 * i) >> LOG2N, k = (4 * i) & (N - 1);
-            const int jn = j0 + qq, js = R - 1 - jn;
-            const float wn = (ring_weight && qq < ntr) ? ring_weight[jn] : 1.f;
-            const float ws = (ring_weight && qq < ntr) ? ring_weight[js] : 1.f;
-            float2* b = buf + qq * NP + pad16(k);
-            b[0] = make_float2(wn * xn[u].x, ws * xs[u].x);
-            b[1] = make_float2(wn * xn[u].y, ws * xs[u].y);
-            b[2] = make_float2(wn * xn[u].z, ws * xs[u].z);
-            b[3] = make_float2(wn * xn[u].w, ws * xs[u].w);
-        }
-    }
-    __syncthreads();
     const int q = threadIdx.x / T, tl = threadIdx.x % T;
-    fft_passes<-1, N, 1>(buf + q * NP, tl, tw);
+    {
+        // the first pass reads the two rings of its pair straight from global memory,
+        // packed as north + i south and scaled by the ring weights
+        const int jn = j0 + q, js = R - 1 - jn;
+        const bool valid = q < ntr, south = valid && js != jn;
+        const float* in_n = maps + ((int64_t)mp * R + (valid ? jn : 0)) * N;
+        const float* in_s = maps + ((int64_t)mp * R + (south ? js : 0)) * N;
+        const float wn = (ring_weight && valid) ? ring_weight[jn] : 1.f;
+        const float ws = (ring_weight && south) ? ring_weight[js] : 1.f;
+        fft_passes_in<-1, N>(buf + q * NP, tl, tw, [&](int k) {
+            return make_float2(valid ? wn * __ldg(in_n + k) : 0.f, south ? ws * __ldg(in_s + k) : 0.f);
+        });
+    }
     float2* o = ut + (int64_t)mp * (L + 1) * 2 * RH + j0;
     const int nout = (L + 1) << lgR;
     float vmax = 0.f;
