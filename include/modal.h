@@ -57,7 +57,8 @@ typedef enum {
     MODAL_ECUDA = 3,     /* CUDA runtime error (launch or asynchronous fault) */
     MODAL_ENOTPD = 4,    /* zeta is not positive definite (Cholesky pivot <= 0) */
     MODAL_ETIMEOUT = 5,  /* a bounded device-side wait hit its limit */
-    MODAL_ESTATE = 6     /* call out of order (e.g. solve before 2 covariance sims) */
+    MODAL_ESTATE = 6,    /* call out of order (e.g. solve before 2 covariance sims) */
+    MODAL_ENOCONV = 7    /* an iteration (the bivector power iteration) did not converge */
 } modal_status;
 
 /* Arithmetic of the Legendre contraction (the dominant step).  FP32 is the plain
@@ -133,6 +134,39 @@ modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* st
  * Synchronises. */
 modal_status modal_solve(modal_h h, const double* alpha, const double* beta, int B,
                          double* fnl, double* sigma, void* stream);
+
+/* Bivector form of the covariance (Sec. III.B, Eqs. ic_bivector, ic_bivectorinv,
+ * bivecvariance).  Given an ideal covariance zeta0 = L0 L0^T (e.g. full sky with
+ * homogeneous noise, where it is cheap to know), the Monte Carlo zeta is modelled as
+ * L0 (I + bt bt^T) L0^T: bt = sqrt(max(l1, 0)) u1 from the largest eigenpair (l1, u1) of
+ * the whitened L0^-1 zeta L0^-T - I, found by FP64 power iteration on the GPU (sign:
+ * sum(bt) >= 0).
+ *   zeta0: host [n_max][n_max] float64, symmetric positive definite (read only);
+ *   bt: host out [n_max] (whitened basis); lambda1: host out l1 (may be NULL).
+ * Errors: MODAL_ESTATE with fewer than 2 covariance sims; MODAL_ENOTPD if zeta0 is not
+ * positive definite; MODAL_ENOCONV if the residual has not fallen below 1e-12 |1 + l1|
+ * within 20000 steps (a near-degenerate top eigenvalue).  Synchronises. */
+modal_status modal_bivector_fit(modal_h h, const double* zeta0, double* bt, double* lambda1, void* stream);
+
+/* Eq. modalest with zeta = L0 (I + bt bt^T) L0^T: alpha' = L0^-1 alpha, beta'_b = L0^-1
+ * beta_b, the inverse (I + bt bt^T)^-1 = I - bt bt^T / (1 + |bt|^2) (Eq. ic_bivectorinv),
+ * fnl_b = alpha'^T (I + bt bt^T)^-1 beta'_b / N, N = alpha'^T (I + bt bt^T)^-1 alpha',
+ * sigma = sqrt(6 / N) (Eq. bivecvariance with zeta = <beta beta^T>/6).  Needs no
+ * covariance sims.  zeta0: host [n_max][n_max]; bt: host [n_max] (from
+ * modal_bivector_fit); alpha: host [n_max]; beta: dev [B][n_max] float64; fnl: host [B];
+ * sigma: host (may be NULL).  MODAL_ENOTPD if zeta0 or N is not positive.  Synchronises. */
+modal_status modal_solve_bivector(modal_h h, const double* zeta0, const double* bt, const double* alpha,
+                                  const double* beta, int B, double* fnl, double* sigma, void* stream);
+
+/* Rotation into the orthonormal frame of the bivector model (Sec. III.B, analytic Cholesky):
+ * out_b = Lt^-1 L0^-1 x_b, where zeta0 = L0 L0^T and Lt is the closed-form lower Cholesky
+ * factor of I + bt bt^T (diagonal sqrt(S_i/S_{i-1}), below it b_i b_k / sqrt(S_{k-1} S_k),
+ * S_i = 1 + sum_{j<=i} b_j^2), applied in O(n_max) per vector.  In that frame the
+ * estimator is alpha''.beta'' / |alpha''|^2.  zeta0: host [n_max][n_max]; bt: host [n_max];
+ * x, out: dev [B][n_max] float64 (out may equal x).  MODAL_ENOTPD if zeta0 is not
+ * positive definite.  Synchronises. */
+modal_status modal_bivector_rotate(modal_h h, const double* zeta0, const double* bt, const double* x, int B,
+                                   double* out, void* stream);
 
 /* Adjoint (not in the paper): for L = sum_n g_n beta_n, grad_lm = dL/dRe a_lm
  * + i dL/dIm a_lm for the stored m >= 0 entries (Im part of m = 0 is zero).

@@ -16,12 +16,12 @@ import numpy as np
 
 from . import build as _build
 
-MODAL_OK, MODAL_EINVAL, MODAL_ENOMEM, MODAL_ECUDA, MODAL_ENOTPD, MODAL_ETIMEOUT, MODAL_ESTATE = range(7)
+MODAL_OK, MODAL_EINVAL, MODAL_ENOMEM, MODAL_ECUDA, MODAL_ENOTPD, MODAL_ETIMEOUT, MODAL_ESTATE, MODAL_ENOCONV = range(8)
 MODAL_FP32, MODAL_3XTF32, MODAL_BF16X3, MODAL_BF16, MODAL_FP16X3 = range(5)
 PREC = {"fp32": MODAL_FP32, "3xtf32": MODAL_3XTF32, "bf16x3": MODAL_BF16X3, "bf16": MODAL_BF16,
         "fp16x3": MODAL_FP16X3}
 STATUS_NAMES = ["MODAL_OK", "MODAL_EINVAL", "MODAL_ENOMEM", "MODAL_ECUDA", "MODAL_ENOTPD",
-                "MODAL_ETIMEOUT", "MODAL_ESTATE"]
+                "MODAL_ETIMEOUT", "MODAL_ESTATE", "MODAL_ENOCONV"]
 
 # Every symbol include/modal.h declares.
 EXPORTS = [
@@ -31,6 +31,7 @@ EXPORTS = [
     "modal_sync", "modal_save_state", "modal_load_state", "modal_selftest_wait", "modal_destroy",
     "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
     "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
+    "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate",
 ]
 MODAL_NSTAGES = 14
 
@@ -78,6 +79,9 @@ def load_library():
         "modal_cubic": [H, c_void_p, c_int, c_int, c_void_p, c_void_p],
         "modal_cov_accumulate": [H, c_void_p, c_int, c_void_p],
         "modal_solve": [H, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
+        "modal_bivector_fit": [H, c_void_p, c_void_p, c_void_p, c_void_p],
+        "modal_solve_bivector": [H, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
+        "modal_bivector_rotate": [H, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p],
         "modal_backward": [H, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p],
         "modal_alpha_local": [H, c_void_p, c_void_p],
         "modal_get_info": [H, POINTER(modal_info)],
@@ -223,6 +227,34 @@ def modal_solve(h, alpha, beta, B, stream=None):
     _check(load_library().modal_solve(h, a_ptr, _dev(beta), int(B), fnl.ctypes.data_as(c_void_p), byref(sigma),
                                       _stream(stream)))
     return fnl[: int(B)], sigma.value
+
+
+def modal_bivector_fit(h, zeta0, stream=None):
+    """Returns (bt [n_max] numpy, lambda1)."""
+    info = modal_get_info(h)
+    z_arr, z_ptr = _host(zeta0, np.float64)
+    bt = np.zeros(info.n_max)
+    lam = c_double(0.0)
+    _check(load_library().modal_bivector_fit(h, z_ptr, bt.ctypes.data_as(c_void_p), byref(lam), _stream(stream)))
+    return bt, lam.value
+
+
+def modal_solve_bivector(h, zeta0, bt, alpha, beta, B, stream=None):
+    """Returns (fnl [B] numpy, sigma)."""
+    z_arr, z_ptr = _host(zeta0, np.float64)
+    b_arr, b_ptr = _host(bt, np.float64)
+    a_arr, a_ptr = _host(alpha, np.float64)
+    fnl = np.zeros(max(int(B), 1))
+    sigma = c_double(0.0)
+    _check(load_library().modal_solve_bivector(h, z_ptr, b_ptr, a_ptr, _dev(beta), int(B),
+                                               fnl.ctypes.data_as(c_void_p), byref(sigma), _stream(stream)))
+    return fnl[: int(B)], sigma.value
+
+
+def modal_bivector_rotate(h, zeta0, bt, x, B, out, stream=None):
+    z_arr, z_ptr = _host(zeta0, np.float64)
+    b_arr, b_ptr = _host(bt, np.float64)
+    _check(load_library().modal_bivector_rotate(h, z_ptr, b_ptr, _dev(x), int(B), _dev(out), _stream(stream)))
 
 
 def modal_backward(h, alm, B, g, use_linear, grad_alm, stream=None):

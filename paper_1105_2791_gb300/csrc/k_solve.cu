@@ -204,6 +204,149 @@ cudaError_t launch_estimates(Plan& pl, const double* rhs, int n, int B, double* 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- bivector form (Sec. III.B)
+// zeta ~ L0 (I + bt bt^T) L0^T with an ideal covariance zeta0 = L0 L0^T.
+
+__global__ void k_transpose(int n, const double* __restrict__ in, double* __restrict__ out) {
+    __shared__ double tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = by + k, c = bx + threadIdx.x;
+        if (r < n && c < n) tile[k][threadIdx.x] = in[(int64_t)r * n + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = bx + k, c = by + threadIdx.x;
+        if (r < n && c < n) out[(int64_t)r * n + c] = tile[threadIdx.x][k];
+    }
+}
+
+cudaError_t launch_transpose(Plan& pl, int n, const double* in, double* out, cudaStream_t st) {
+    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+    k_transpose<<<grid, block, 0, st>>>(n, in, out);
+    note_launch(pl);
+    return cudaGetLastError();
+}
+
+// Power iteration on the whitened Z (eigenvalues 1 + l_i > 0, so the dominant one is
+// the largest): w = Z v, one warp per row.
+__global__ void __launch_bounds__(256) k_matvec(int n, const double* __restrict__ Z, const double* __restrict__ v,
+                                                double* __restrict__ w) {
+    const int row = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s = fma(Z[(int64_t)row * n + j], v[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[row] = s;
+}
+
+__device__ __forceinline__ double block_sum256(double x, double* red) {
+    red[threadIdx.x] = x;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// One CTA: lam = v.w (the Rayleigh quotient of the unit v), res = |w - lam v|, then v = w / |w|.
+// stat = {lam, res}.
+__global__ void __launch_bounds__(256) k_normalize(int n, const double* __restrict__ w, double* __restrict__ v,
+                                                   double* __restrict__ stat) {
+    __shared__ double red[256];
+    double s = 0.0, d = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        s = fma(w[i], w[i], s);
+        d = fma(v[i], w[i], d);
+    }
+    const double ww = block_sum256(s, red), lam = block_sum256(d, red);
+    double r = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double e = w[i] - lam * v[i];
+        r = fma(e, e, r);
+    }
+    const double rr = block_sum256(r, red);
+    if (threadIdx.x == 0) {
+        stat[0] = lam;
+        stat[1] = sqrt(rr);
+    }
+    const double inv = ww > 0.0 ? 1.0 / sqrt(ww) : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
+}
+
+cudaError_t launch_power_step(Plan& pl, int n, const double* Z, double* v, double* w, double* stat, cudaStream_t st) {
+    k_matvec<<<(n + 7) / 8, 256, 0, st>>>(n, Z, v, w);
+    note_launch(pl);
+    k_normalize<<<1, 256, 0, st>>>(n, w, v, stat);
+    note_launch(pl);
+    return cudaGetLastError();
+}
+
+// rhs = [alpha'; beta'_0; ...] (whitened), bt: out[0] = alpha'^T Z^-1 alpha' and
+// out[1 + b] = alpha'^T Z^-1 beta'_b / out[0], Z^-1 = I - bt bt^T / (1 + |bt|^2) (Eq. ic_bivectorinv).
+__global__ void __launch_bounds__(256) k_bivector_estimates(int n, int B, const double* __restrict__ rhs,
+                                                            const double* __restrict__ bt, double* __restrict__ out) {
+    __shared__ double red[256];
+    const double* a = rhs;
+    double bb = 0.0, ab = 0.0, aa = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        bb = fma(bt[i], bt[i], bb);
+        ab = fma(a[i], bt[i], ab);
+        aa = fma(a[i], a[i], aa);
+    }
+    bb = block_sum256(bb, red);
+    ab = block_sum256(ab, red);
+    aa = block_sum256(aa, red);
+    const double norm = aa - ab * ab / (1.0 + bb);
+    if (threadIdx.x == 0) out[0] = norm;
+    for (int b = 0; b < B; ++b) {
+        const double* y = rhs + (int64_t)(b + 1) * n;
+        double ay = 0.0, by = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            ay = fma(a[i], y[i], ay);
+            by = fma(bt[i], y[i], by);
+        }
+        ay = block_sum256(ay, red);
+        by = block_sum256(by, red);
+        if (threadIdx.x == 0) out[1 + b] = (ay - ab * by / (1.0 + bb)) / norm;
+    }
+}
+
+cudaError_t launch_bivector_estimates(Plan& pl, const double* rhs, int n, int B, const double* bt, double* out,
+                                      cudaStream_t st) {
+    k_bivector_estimates<<<1, 256, 0, st>>>(n, B, rhs, bt, out);
+    note_launch(pl);
+    return cudaGetLastError();
+}
+
+// x <- Lt^-1 x for the analytic Cholesky factor Lt of I + bt bt^T (Sec. III.B):
+// with S_0 = 1, S_i = S_{i-1} + b_i^2, Lt_ii = sqrt(S_i / S_{i-1}) and
+// Lt_ik = b_i b_k / sqrt(S_{k-1} S_k) (k < i), forward substitution needs only the running
+// sum t_i = sum_{k<i} b_k y_k / sqrt(S_{k-1} S_k): O(n) per vector, one thread each.
+__global__ void k_bivector_rotate(int n, int B, const double* __restrict__ bt, double* __restrict__ x) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double* v = x + (int64_t)b * n;
+    double S = 1.0, t = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double bi = bt[i], Sn = fma(bi, bi, S);
+        const double y = (v[i] - bi * t) * sqrt(S / Sn);
+        t = fma(bi * y, 1.0 / sqrt(S * Sn), t);
+        v[i] = y;
+        S = Sn;
+    }
+}
+
+cudaError_t launch_bivector_rotate(Plan& pl, int n, int B, const double* bt, double* x, cudaStream_t st) {
+    if (B == 0) return cudaSuccess;
+    k_bivector_rotate<<<(B + 63) / 64, 64, 0, st>>>(n, B, bt, x);
+    note_launch(pl);
+    return cudaGetLastError();
+}
+
 // Bounded wait on a flag that nothing sets: after spin_limit polls the thread records
 // MODAL_DEVERR_TIMEOUT and returns (no trap, no fault).
 __global__ void k_wait_selftest(int* err, int spin_limit) {

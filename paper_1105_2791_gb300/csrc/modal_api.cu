@@ -634,6 +634,143 @@ modal_status modal_solve(modal_h h, const double* alpha, const double* beta, int
     return s;
 }
 
+// Power iteration of the bivector fit: stop when |Z v - lam v| <= kPowerTol |lam|, checked
+// every kPowerCheck steps (the error of v is about that residual over the eigenvalue gap).
+constexpr int kPowerMaxIters = 20000, kPowerCheck = 16;
+constexpr double kPowerTol = 1e-12;
+
+// Copies the host zeta0 into A and factors it in place (lower triangle = L0).
+static modal_status factor_zeta0(modal_h h, const double* zeta0, double* A, cudaStream_t st) {
+    const int n = h->n_max;
+    CK(cudaMemcpyAsync(A, zeta0, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, st), "zeta0 copy");
+    { STAGE(h, ST_SOLVE, st); CK(launch_cholesky(*h, A, n, st), "cholesky of zeta0"); }
+    modal_status es = read_device_error(h, st);
+    if (es == MODAL_ENOTPD) return set_error(MODAL_ENOTPD, "zeta0 is not positive definite");
+    return es;
+}
+
+modal_status modal_bivector_fit(modal_h h, const double* zeta0, double* bt, double* lambda1, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!zeta0 || !bt) return set_error(MODAL_EINVAL, "null pointer");
+    if (h->n_cov < 2) return set_error(MODAL_ESTATE, "need at least 2 covariance simulations");
+    cudaStream_t st = as_stream(stream);
+    const int n = h->n_max;
+    double* ws = nullptr;
+    CK(cudaMallocAsync(&ws, ((size_t)3 * n * n + 2 * (size_t)n + 2) * sizeof(double), st), "fit workspace");
+    double* L0 = ws;
+    double* Z = L0 + (size_t)n * n;
+    double* T = Z + (size_t)n * n;
+    double* v = T + (size_t)n * n;
+    double* w = v + n;
+    double* stat = w + n;
+    auto run = [&]() -> modal_status {
+        modal_status s = factor_zeta0(h, zeta0, L0, st);
+        if (s != MODAL_OK) return s;
+        {
+            // whitened Z = L0^-1 zeta L0^-T: the rows of zeta (= its columns) are solved
+            // against L0, giving (L0^-1 zeta)^T; its transpose's rows are solved again.
+            STAGE(h, ST_SOLVE, st);
+            CK(launch_zeta(*h, Z, st), "zeta");
+            CK(launch_solve_rhs(*h, L0, n, Z, n, st), "whitening solve");
+            CK(launch_transpose(*h, n, Z, T, st), "transpose");
+            CK(launch_solve_rhs(*h, L0, n, T, n, st), "whitening solve");
+        }
+        std::vector<double> hv(n, 1.0 / std::sqrt((double)n));
+        CK(cudaMemcpyAsync(v, hv.data(), n * sizeof(double), cudaMemcpyHostToDevice, st), "start vector");
+        double hs[2] = {0.0, 0.0};
+        bool converged = false;
+        for (int it = 0; it < kPowerMaxIters && !converged; it += kPowerCheck) {
+            {
+                STAGE(h, ST_SOLVE, st);
+                for (int k = 0; k < kPowerCheck; ++k) CK(launch_power_step(*h, n, T, v, w, stat, st), "power step");
+            }
+            CK(cudaMemcpyAsync(hs, stat, sizeof(hs), cudaMemcpyDeviceToHost, st), "eigenvalue read");
+            CK(cudaStreamSynchronize(st), "sync");
+            if (!std::isfinite(hs[0])) return set_error(MODAL_ENOTPD, "power iteration produced a non-finite value");
+            converged = hs[1] <= kPowerTol * std::fabs(hs[0]);
+        }
+        if (!converged) return set_error(MODAL_ENOCONV, "power iteration for the bivector did not converge");
+        // v was renormalised after the last residual: |Z v_old| v = Z v_old, the same direction
+        CK(cudaMemcpyAsync(hv.data(), v, n * sizeof(double), cudaMemcpyDeviceToHost, st), "eigenvector read");
+        CK(cudaStreamSynchronize(st), "sync");
+        const double l1 = hs[0] - 1.0;
+        double sum = 0.0;
+        for (int i = 0; i < n; ++i) sum += hv[i];
+        const double scale = std::sqrt(std::max(l1, 0.0)) * (sum < 0.0 ? -1.0 : 1.0);
+        for (int i = 0; i < n; ++i) bt[i] = scale * hv[i];
+        if (lambda1) *lambda1 = l1;
+        return MODAL_OK;
+    };
+    modal_status s = run();
+    cudaFreeAsync(ws, st);
+    cudaStreamSynchronize(st);
+    return s;
+}
+
+modal_status modal_solve_bivector(modal_h h, const double* zeta0, const double* bt, const double* alpha,
+                                  const double* beta, int B, double* fnl, double* sigma, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!zeta0 || !bt || !alpha || B < 0 || (B > 0 && (!beta || !fnl))) return set_error(MODAL_EINVAL, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    const int n = h->n_max;
+    double* ws = nullptr;
+    CK(cudaMallocAsync(&ws, ((size_t)n * n + (size_t)(B + 2) * n + (B + 1)) * sizeof(double), st), "solve workspace");
+    double* L0 = ws;
+    double* rhs = L0 + (size_t)n * n;
+    double* dbt = rhs + (size_t)(B + 1) * n;
+    double* est = dbt + n;
+    auto run = [&]() -> modal_status {
+        modal_status s = factor_zeta0(h, zeta0, L0, st);
+        if (s != MODAL_OK) return s;
+        CK(cudaMemcpyAsync(rhs, alpha, n * sizeof(double), cudaMemcpyHostToDevice, st), "alpha copy");
+        if (B > 0) CK(cudaMemcpyAsync(rhs + n, beta, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice, st), "beta copy");
+        CK(cudaMemcpyAsync(dbt, bt, n * sizeof(double), cudaMemcpyHostToDevice, st), "bt copy");
+        {
+            STAGE(h, ST_SOLVE, st);
+            CK(launch_solve_rhs(*h, L0, n, rhs, B + 1, st), "triangular solve");
+            CK(launch_bivector_estimates(*h, rhs, n, B, dbt, est, st), "bivector estimates");
+        }
+        std::vector<double> out(B + 1);
+        CK(cudaMemcpyAsync(out.data(), est, (B + 1) * sizeof(double), cudaMemcpyDeviceToHost, st), "estimates copy");
+        CK(cudaStreamSynchronize(st), "solve sync");
+        if (!(out[0] > 0.0)) return set_error(MODAL_ENOTPD, "alpha'^T (I + bt bt^T)^-1 alpha' is not positive");
+        if (sigma) *sigma = std::sqrt(6.0 / out[0]);
+        for (int b = 0; b < B; ++b) fnl[b] = out[1 + b];
+        return MODAL_OK;
+    };
+    modal_status s = run();
+    cudaFreeAsync(ws, st);
+    cudaStreamSynchronize(st);
+    return s;
+}
+
+modal_status modal_bivector_rotate(modal_h h, const double* zeta0, const double* bt, const double* x, int B,
+                                   double* out, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!zeta0 || !bt || B < 0 || (B > 0 && (!x || !out))) return set_error(MODAL_EINVAL, "bad arguments");
+    cudaStream_t st = as_stream(stream);
+    const int n = h->n_max;
+    double* ws = nullptr;
+    CK(cudaMallocAsync(&ws, ((size_t)n * n + n) * sizeof(double), st), "rotate workspace");
+    double* L0 = ws;
+    double* dbt = L0 + (size_t)n * n;
+    auto run = [&]() -> modal_status {
+        modal_status s = factor_zeta0(h, zeta0, L0, st);
+        if (s != MODAL_OK) return s;
+        CK(cudaMemcpyAsync(dbt, bt, n * sizeof(double), cudaMemcpyHostToDevice, st), "bt copy");
+        if (B > 0 && out != x)
+            CK(cudaMemcpyAsync(out, x, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy");
+        STAGE(h, ST_SOLVE, st);
+        CK(launch_solve_rhs(*h, L0, n, out, B, st), "triangular solve");
+        CK(launch_bivector_rotate(*h, n, B, dbt, out, st), "bivector rotation");
+        return MODAL_OK;
+    };
+    modal_status s = run();
+    cudaFreeAsync(ws, st);
+    CK(cudaStreamSynchronize(st), "rotate sync");
+    return s;
+}
+
 modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, int use_linear, void* grad_alm,
                             void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;

@@ -183,5 +183,11 @@ cudaError_t launch_cholesky(Plan& pl, double* A, int n, cudaStream_t st);
 cudaError_t launch_solve_rhs(Plan& pl, const double* Lc, int n, double* rhs, int nrhs, cudaStream_t st);
 cudaError_t launch_estimates(Plan& pl, const double* rhs, int n, int B, double* out, cudaStream_t st);
 cudaError_t launch_wait_selftest(int* d_err, int spin_limit, cudaStream_t st);
+// bivector form of the covariance (k_solve.cu)
+cudaError_t launch_transpose(Plan& pl, int n, const double* in, double* out, cudaStream_t st);
+cudaError_t launch_power_step(Plan& pl, int n, const double* Z, double* v, double* w, double* stat, cudaStream_t st);
+cudaError_t launch_bivector_estimates(Plan& pl, const double* rhs, int n, int B, const double* bt, double* out,
+                                      cudaStream_t st);
+cudaError_t launch_bivector_rotate(Plan& pl, int n, int B, const double* bt, double* x, cudaStream_t st);
 
 }  // namespace modal

@@ -76,6 +76,21 @@ class Plan:
         nb = 0 if beta is None else beta.shape[0]
         return B.modal_solve(self.h, alpha, beta, nb)
 
+    def bivector_fit(self, zeta0):
+        """(bt, l1): the Monte Carlo zeta fitted as L0 (I + bt bt^T) L0^T, zeta0 = L0 L0^T."""
+        return B.modal_bivector_fit(self.h, zeta0)
+
+    def solve_bivector(self, zeta0, bt, alpha, beta=None):
+        nb = 0 if beta is None else beta.shape[0]
+        return B.modal_solve_bivector(self.h, zeta0, bt, alpha, beta, nb)
+
+    def bivector_rotate(self, zeta0, bt, x, out=None):
+        """Lt^-1 L0^-1 x for dev x [B][n_max] float64 (the orthonormal frame of the bivector model)."""
+        if out is None:
+            out = torch.empty_like(x)
+        B.modal_bivector_rotate(self.h, zeta0, bt, x, x.shape[0], out)
+        return out
+
     def backward(self, alm, g, use_linear=False, out=None):
         nb = alm.shape[0]
         if out is None:
