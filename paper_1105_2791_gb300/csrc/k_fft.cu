@@ -19,8 +19,11 @@
 // block-wide sync separates loads from stores.  Shared-memory index i is padded to
 // i + i / 16 to spread the strided stores over the banks.  A CTA of 512 threads holds
 // 8192 / N transforms (two ring pairs at N = 4096, 70 KB of shared memory), so that two
-// CTAs share an SM and one's global loads and stores overlap the other's passes; the
-// E/O rows and the U~ rows of neighbouring CTAs share 32-byte sectors, which L2 merges.
+// CTAs share an SM and one's global loads and stores overlap the other's passes.  The
+// synthesis transform's last pass writes the rings and the analysis transform's first
+// pass reads them straight from global memory; the E/O rows read by the synthesis and
+// the U~ rows written by the analysis are shared with neighbouring CTAs at 32-byte-sector
+// granularity, which L2 merges.
 #include "modal_internal.cuh"
 
 namespace modal {
@@ -118,6 +121,39 @@ __device__ __forceinline__ void dft(float2* x) {
     }
 }
 
+// Twiddles e^{SIGN 2 pi i r k / (R NS)}, r = 1..R-1, of one butterfly of a pass.  The
+// table holds, per pass with NS > 1 and per k, w_1, w_2, w_3, w_4, w_8 and w_12 (three
+// 16-byte blocks of NS entries each, so a warp's loads are contiguous); w_r for r = a + 4 b
+// is w_a w_4b, one complex product of two correctly rounded values.
+template <int SIGN, int R>
+struct PassTwiddles {
+    float2 w1, w2, w3, w4, w8, w12;
+    __device__ __forceinline__ void load(const float4* __restrict__ tw, int NS, int k) {
+        const float4 a = __ldg(&tw[k]);
+        w1 = make_float2(a.x, SIGN * a.y);
+        w2 = make_float2(a.z, SIGN * a.w);
+        if (R > 2) {
+            const float4 b = __ldg(&tw[NS + k]);
+            w3 = make_float2(b.x, SIGN * b.y);
+            w4 = make_float2(b.z, SIGN * b.w);
+        }
+        if (R > 8) {
+            const float4 c = __ldg(&tw[2 * NS + k]);
+            w8 = make_float2(c.x, SIGN * c.y);
+            w12 = make_float2(c.z, SIGN * c.w);
+        }
+    }
+    // r is a compile-time constant after unrolling, so the selections fold away
+    __device__ __forceinline__ float2 get(int r) const {
+        const int a = r & 3, b = r >> 2;
+        const float2 wa = (a == 1) ? w1 : (a == 2) ? w2 : w3;
+        const float2 wb = (b == 1) ? w4 : (b == 2) ? w8 : w12;
+        if (a == 0) return wb;
+        if (b == 0) return wa;
+        return cmul(wa, wb);
+    }
+};
+
 // Padded shared-memory index of element base + r * STRIDE.  When STRIDE is a multiple of
 // 16 the padding of the r-th element is that of `base` plus r * STRIDE / 16, so every
 // access of a pass is a per-thread base plus a compile-time offset.
@@ -133,7 +169,7 @@ __device__ __forceinline__ int pad_at(int base, int r) {
 // e^{SIGN 2 pi i r k / (R NS)} (k = j mod NS), transforms, and writes element r of
 // butterfly j to R (j - k) + k + r NS.
 template <int SIGN, int R, int N, int NS>
-__device__ __forceinline__ void stockham_pass(float2* buf, int tl, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stockham_pass(float2* buf, int tl, const float4* __restrict__ tw) {
     constexpr int NB = 16 / R;                   // butterflies per thread
     constexpr int T = N / 16;
     constexpr int NR = N / R;
@@ -143,14 +179,12 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int tl, const float2*
     for (int u = 0; u < NB; ++u) {
         const int j = tl + T * u;
         const int k = j & (NS - 1);
+        PassTwiddles<SIGN, R> w;
+        if (NS > 1) w.load(tw, NS, k);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             float2 x = buf[pad_at<NR>(j, r)];
-            if (r > 0 && NS > 1) {
-                float2 w = __ldg(&tw[(r - 1) * NS + k]);
-                if (SIGN < 0) w.y = -w.y;
-                x = cmul(x, w);
-            }
+            if (r > 0 && NS > 1) x = cmul(x, w.get(r));
             v[u * R + r] = x;
         }
         dft<SIGN, R>(v + u * R);
@@ -170,16 +204,14 @@ __device__ __forceinline__ void stockham_pass(float2* buf, int tl, const float2*
     __syncthreads();
 }
 
-// Twiddle table, one block per pass in pass order: for the pass of radix R at
-// sub-transform length NS, entries (r - 1) NS + k = e^{2 pi i r k / (R NS)}, r = 1..R-1,
-// k = 0..NS-1 (N - 1 entries in all), so that the threads of a warp read consecutive
-// entries.  Passes: radix 16 while at least 16 remain, then the remainder (8, 4 or 2).
+// Passes: radix 16 while at least 16 remain, then the remainder (8, 4 or 2).  The twiddle
+// table holds 3 NS float4 per pass with NS > 1, in pass order (PassTwiddles).
 template <int SIGN, int N, int NS>
-__device__ __forceinline__ void fft_passes(float2* buf, int tl, const float2* __restrict__ tw) {
+__device__ __forceinline__ void fft_passes(float2* buf, int tl, const float4* __restrict__ tw) {
     if constexpr (NS < N) {
         constexpr int R = (N / NS >= 16) ? 16 : N / NS;
         stockham_pass<SIGN, R, N, NS>(buf, tl, tw);
-        fft_passes<SIGN, N, NS * R>(buf, tl, tw + (R - 1) * NS);
+        fft_passes<SIGN, N, NS * R>(buf, tl, tw + (NS > 1 ? 3 * NS : 0));
     }
 }
 
@@ -187,11 +219,11 @@ __device__ __forceinline__ void fft_passes(float2* buf, int tl, const float2* __
 // store(index, value) instead of shared memory: thread tl holds elements j + r NS of
 // butterflies j = tl + T u, so the threads of a warp store consecutive indices.
 template <int SIGN, int N, int NS, class Store>
-__device__ __forceinline__ void fft_passes_out(float2* buf, int tl, const float2* __restrict__ tw, Store store) {
+__device__ __forceinline__ void fft_passes_out(float2* buf, int tl, const float4* __restrict__ tw, Store store) {
     constexpr int R = (N / NS >= 16) ? 16 : N / NS;
     if constexpr (NS * R < N) {
         stockham_pass<SIGN, R, N, NS>(buf, tl, tw);
-        fft_passes_out<SIGN, N, NS * R>(buf, tl, tw + (R - 1) * NS, store);
+        fft_passes_out<SIGN, N, NS * R>(buf, tl, tw + (NS > 1 ? 3 * NS : 0), store);
     } else {
         constexpr int NB = 16 / R;
         constexpr int T = N / 16;
@@ -200,14 +232,12 @@ __device__ __forceinline__ void fft_passes_out(float2* buf, int tl, const float2
         for (int u = 0; u < NB; ++u) {
             const int j = tl + T * u;
             const int k = j & (NS - 1);
+            PassTwiddles<SIGN, R> w;
+            if (NS > 1) w.load(tw, NS, k);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 float2 x = buf[pad_at<NS>(j, r)];
-                if (r > 0 && NS > 1) {
-                    float2 w = __ldg(&tw[(r - 1) * NS + k]);
-                    if (SIGN < 0) w.y = -w.y;
-                    x = cmul(x, w);
-                }
+                if (r > 0 && NS > 1) x = cmul(x, w.get(r));
                 v[u * R + r] = x;
             }
             dft<SIGN, R>(v + u * R);
@@ -227,7 +257,7 @@ __device__ __forceinline__ void fft_passes_out(float2* buf, int tl, const float2
 // shared memory (thread tl reads elements tl + r N / 16: consecutive across a warp), then
 // the remaining passes in shared memory.
 template <int SIGN, int N, class Load>
-__device__ __forceinline__ void fft_passes_in(float2* buf, int tl, const float2* __restrict__ tw, Load load) {
+__device__ __forceinline__ void fft_passes_in(float2* buf, int tl, const float4* __restrict__ tw, Load load) {
     constexpr int T = N / 16;
     float2 v[16];
 #pragma unroll
@@ -236,7 +266,7 @@ __device__ __forceinline__ void fft_passes_in(float2* buf, int tl, const float2*
 #pragma unroll
     for (int r = 0; r < 16; ++r) buf[pad16(16 * tl) + r] = v[r];
     __syncthreads();
-    fft_passes<SIGN, N, 16>(buf, tl, tw + 15);
+    fft_passes<SIGN, N, 16>(buf, tl, tw);
 }
 
 // Padded transform stride in float2: N + N/16 for the in-transform padding, + 4 so that
@@ -249,7 +279,7 @@ __host__ __device__ constexpr int fft_stride(int N) { return N + (N >> 4) + 4; }
 // north = E + O, south = E - O.
 template <int LOG2N>
 __global__ void __launch_bounds__(FFT_THREADS, 2)
-k_ring_c2r(int L, int R, int R_half, int RH, const float2* __restrict__ delta, const float2* __restrict__ tw,
+k_ring_c2r(int L, int R, int R_half, int RH, const float2* __restrict__ delta, const float4* __restrict__ tw,
            float* __restrict__ maps) {
     constexpr int N = 1 << LOG2N;
     constexpr int lgR = 13 - LOG2N;                      // RPB = 2^lgR transforms per CTA
@@ -317,7 +347,7 @@ k_ring_c2r(int L, int R, int R_half, int RH, const float2* __restrict__ delta, c
 template <int LOG2N>
 __global__ void __launch_bounds__(FFT_THREADS, 2)
 k_ring_r2c(int L, int R, int R_half, int RH, int P, const float* __restrict__ maps,
-           const float* __restrict__ ring_weight, const float2* __restrict__ tw, float2* __restrict__ ut,
+           const float* __restrict__ ring_weight, const float4* __restrict__ tw, float2* __restrict__ ut,
            unsigned* __restrict__ amax) {
     constexpr int N = 1 << LOG2N;
     constexpr int lgR = 13 - LOG2N;

@@ -279,7 +279,6 @@ struct StageScope {
 };
 #define STAGE(pl, id, st) StageScope _scope_##id((pl), (id), (st))
 
-// Legendre stage for one chunk: alm -> delta.
 // Legendre stage for one chunk: alm -> delta (tensor-core path: operand preparation and
 // the contraction are timed as separate stages).
 static cudaError_t legendre_forward(modal_plan* pl, const float2* alm, int B, cudaStream_t st) {
@@ -404,28 +403,35 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
         CKI(cudaMemcpy(pl->W, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice), "weights copy");
         CKI(dalloc(pl, &pl->wring, wr.size()), "ring weights");
         CKI(cudaMemcpy(pl->wring, wr.data(), wr.size() * sizeof(float), cudaMemcpyHostToDevice), "ring weights copy");
-        // per-pass twiddles of the ring FFT: radix-16 passes, then one of radix 8, 4 or 2;
-        // pass (R, Ns) holds e^{2 pi i r k / (R Ns)} at (r - 1) Ns + k
-        std::vector<float2> tw(pl->nphi, make_float2(0.f, 0.f));
+        // per-pass twiddles of the ring FFT (radix-16 passes, then one of radix 8, 4 or 2):
+        // for each pass (R, Ns) with Ns > 1, three blocks of Ns float4 holding
+        // (w_1, w_2), (w_3, w_4), (w_8, w_12) at k, w_r = e^{2 pi i r k / (R Ns)}
+        std::vector<float4> tw;
         {
             int lg = 0;
             while ((1 << lg) < pl->nphi) ++lg;
-            size_t off = 0;
+            auto w = [](int r, int k, int R, int Ns) {
+                const double a = 2.0 * M_PI * (double)((long long)r * k) / (double)((long long)R * Ns);
+                return make_float2((float)std::cos(a), (float)std::sin(a));
+            };
             for (int Ns = 1, left = lg; left > 0;) {
                 const int lr = left >= 4 ? 4 : left;
                 const int R = 1 << lr;
-                for (int r = 1; r < R; ++r)
-                    for (int k = 0; k < Ns; ++k) {
-                        const double a = 2.0 * M_PI * (double)(r * k) / (double)(R * Ns);
-                        tw[off + (size_t)(r - 1) * Ns + k] = make_float2((float)std::cos(a), (float)std::sin(a));
-                    }
-                off += (size_t)(R - 1) * Ns;
+                if (Ns > 1) {
+                    const int pairs[3][2] = {{1, 2}, {3, 4}, {8, 12}};
+                    for (int blk = 0; blk < 3; ++blk)
+                        for (int k = 0; k < Ns; ++k) {
+                            const float2 x = w(pairs[blk][0], k, R, Ns), y = w(pairs[blk][1], k, R, Ns);
+                            tw.push_back(make_float4(x.x, x.y, y.x, y.y));
+                        }
+                }
                 Ns *= R;
                 left -= lr;
             }
+            if (tw.empty()) tw.push_back(make_float4(1.f, 0.f, 1.f, 0.f));
         }
         CKI(dalloc(pl, &pl->twiddle, tw.size()), "twiddles");
-        CKI(cudaMemcpy(pl->twiddle, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice), "twiddles copy");
+        CKI(cudaMemcpy(pl->twiddle, tw.data(), tw.size() * sizeof(float4), cudaMemcpyHostToDevice), "twiddles copy");
     }
     // mode / pair / tile tables
     {

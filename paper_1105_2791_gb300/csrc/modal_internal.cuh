@@ -71,7 +71,7 @@ struct Plan {
     float* filt = nullptr;       // [P][lmax+1]
     float* W = nullptr;          // [nrings*nphi] pixel weights with mask
     float* wring = nullptr;      // [nrings] w_j 2 pi / nphi (no mask)
-    float2* twiddle = nullptr;   // [nphi - 1] ring-FFT twiddles, one block per Stockham pass
+    float4* twiddle = nullptr;   // ring-FFT twiddles: 3 Ns float4 per Stockham pass with Ns > 1
     int* modeidx = nullptr;      // [n_pair_colex_pad][16] -> mode index or -1 (cubic tiles)
     int* tiles = nullptr;        // [n_tiles] packed (pair group, s quad)
     int n_tiles = 0, n_pg = 0, n_sq = 0;

@@ -100,6 +100,30 @@ def test_analysis_parity():
     plan.close()
 
 
+@pytest.mark.parametrize("log2n", list(range(4, 14)))
+def test_ring_fft_every_length(log2n):
+    """Synthesis and analysis at every ring-FFT length the library compiles (16 .. 8192),
+    at the largest l_max each allows (capped at 40; longer rings are oversampled), against
+    the oracle's direct Fourier sums."""
+    M = _cuda_or_skip()
+    nphi = 1 << log2n
+    L = min(nphi // 2 - 1, 40)
+    R = L + 2
+    basis, cl, alm = _case(L, 2, 2, seed=40 + log2n)
+    plan = _plan(M, L, 2, basis, cl, R, nphi, "fp32")
+    maps = plan.synthesize(torch.from_numpy(alm).cuda()).cpu().numpy()
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    xi = simgen.pixel_normals(R, nphi, 2, seed=log2n)
+    got = plan.analyze(torch.from_numpy(xi.astype(np.float32)).cuda()).cpu().numpy()
+    for b in range(2):
+        ref = osh.synthesize(alm[b].astype(np.complex128), L, filt, mu, nphi)
+        assert np.max(np.abs(maps[b] - ref)) / np.max(np.abs(ref)) <= 1e-5
+        aref = osh.analyze(xi[b].astype(np.float32).astype(np.float64), L, mu, w, nphi)
+        assert _rel(got[b], aref) <= 1e-5
+    plan.close()
+
+
 def _noise_alm_gpu(plan, xi, sigma_ring):
     mu, w = plan.rings()
     omega = w * 2 * math.pi / plan.nphi
