@@ -4,7 +4,8 @@ Test infrastructure only (see the package header).
 
 Orderings shared with the library:
   * modes n <-> (p, r, s), p <= r <= s, lexicographic; n_max = C(P+2, 3);
-  * pairs (p, r), p <= r, lexicographic; N_pair = P (P + 1) / 2.
+  * pairs (p, r), p <= r, lexicographic; N_pair = P (P + 1) / 2;
+  * quartic modes (p, r, s, u), p <= r <= s <= u, lexicographic; C(P+3, 4) of them.
 
 What each function follows:
   cubic_beta       Eq. bbispect: beta_n = sum G (a a a - 3 C a) R_n / sqrt(CCC).
@@ -30,6 +31,10 @@ What each function follows:
                    sum h^2 F G H = 8 pi^2 int f g h dmu (h from Sec. III.A).
   zeta_closed_form the full-sky covariance of beta for Gaussian maps (six cross
                    pairings of Eq. linearterm), by the same identity.
+  quartic_tau      the trispectrum modes of Sec. IV (the B term of its estimator with the
+                   four-harmonic Gaunt integral): sum_x W [M_p M_r M_s M_u - sum over the 6
+                   single pairs <ab> M_c M_d + sum over the 3 pair splits <ab><cd>], the
+                   "-6 C a a" and "+3 C C" of Sec. IV symmetrised over the ordered quadruple.
   adjoint_grad     derivative of sum_n g_n beta_n with respect to (Re a_lm, Im a_lm),
                    m >= 0 (not in the paper; chain rule through cubic_beta and synthesis).
   bivector_*       Eq. ic_bivector, ic_bivectorinv, bivecvariance and the analytic
@@ -43,7 +48,9 @@ What each function follows:
 Pins: tests/test_oracle_modal.py (Gaunt brute force on an exact-cubic grid,
 closed-form covariance and mean, zero mean, larger variance without the linear
 term, invariance under mode transforms, finite differences for the adjoint,
-bivector identities).
+bivector identities; for the quartic modes: the four-harmonic Gaunt brute force on an
+exact-quartic grid, the multivariate Hermite polynomial for constant fields, and an
+imaginary-shift identity for the single-pair term).
 """
 from __future__ import annotations
 
@@ -119,6 +126,50 @@ def cubic_beta(maps: np.ndarray, W: np.ndarray, pairmean=None) -> np.ndarray:
             pm = pairmean.reshape(pairmean.shape[0], -1)
             val -= np.sum(flatW * (pm[pidx[(p, r)]] * M[s] + pm[pidx[(p, s)]] * M[r]
                                    + pm[pidx[(r, s)]] * M[p]))
+        out[n] = val
+    return out
+
+
+def quad_list(P: int):
+    """(p, r, s, u), p <= r <= s <= u, lexicographic."""
+    return [(p, r, s, u) for p in range(P) for r in range(p, P) for s in range(r, P) for u in range(s, P)]
+
+
+def n_quads(P: int) -> int:
+    return P * (P + 1) * (P + 2) * (P + 3) // 24
+
+
+# the six ways to pick one pair of the four indices (the rest is the other pair) and the
+# three ways to split them into two pairs
+_QUAD_SPLITS = ((0, 1, 2, 3), (0, 2, 1, 3), (0, 3, 1, 2), (1, 2, 0, 3), (1, 3, 0, 2), (2, 3, 0, 1))
+_QUAD_MATCHINGS = ((0, 1, 2, 3), (0, 2, 1, 3), (0, 3, 1, 2))
+
+
+def quartic_tau(maps: np.ndarray, W: np.ndarray, pairmean=None) -> np.ndarray:
+    """Trispectrum modal coefficients (Sec. IV, the B term of the quartic estimator);
+    [n_quads].  With R_n = q_p q_r q_s q_u and v_l = 1 the four-harmonic Gaunt sum is the
+    sphere integral of M_p M_r M_s M_u, taken as the grid sum with W_x; the -6 C a a and
+    +3 C C terms, symmetrised over the ordered quadruple, become the six single-pair and
+    the three two-pair contractions with the Monte Carlo means:
+      tau = sum_x W [M_p M_r M_s M_u - sum_6 <ab> M_c M_d + sum_3 <ab> <cd>].
+    maps [P][...] (complex allowed); W like one map; pairmean [N_pair][...] or None."""
+    P = maps.shape[0]
+    pidx = {pr: i for i, pr in enumerate(pair_list(P))}
+    M = maps.reshape(P, -1)
+    flatW = W.ravel()
+    pm = None if pairmean is None else pairmean.reshape(pairmean.shape[0], -1)
+
+    def mean(a, b):
+        return pm[pidx[(min(a, b), max(a, b))]]
+
+    out = np.empty(n_quads(P), dtype=np.result_type(M.dtype, np.float64))
+    for n, q in enumerate(quad_list(P)):
+        val = np.sum(flatW * M[q[0]] * M[q[1]] * M[q[2]] * M[q[3]])
+        if pm is not None:
+            for (i, j, k, l) in _QUAD_SPLITS:
+                val -= np.sum(flatW * mean(q[i], q[j]) * M[q[k]] * M[q[l]])
+            for (i, j, k, l) in _QUAD_MATCHINGS:
+                val += np.sum(flatW * mean(q[i], q[j]) * mean(q[k], q[l]))
         out[n] = val
     return out
 

@@ -84,3 +84,43 @@ def gaunt_beta(alm: np.ndarray, lmax: int, filt: np.ndarray) -> np.ndarray:
                 T += gv * np.einsum("a,b,c->abc", F[:, i1], F[:, i2], F[:, i3])
     out = [T[p, r, s].real for p in range(P) for r in range(p, P) for s in range(r, P)]
     return np.array(out)
+
+
+def gaunt4(l1, l2, l3, l4, m1, m2, m3, m4) -> float:
+    """int Y_l1m1 Y_l2m2 Y_l3m3 Y_l4m4 dOmega (Sec. IV): expand Y_l1m1 Y_l2m2 in Y_LM,
+    whose coefficient is int Y_l1m1 Y_l2m2 conj(Y_LM) = (-1)^M G^{l1 l2 L}_{m1 m2 -M}, and
+    integrate each term against Y_l3m3 Y_l4m4 (M = m1 + m2)."""
+    if m1 + m2 + m3 + m4 != 0:
+        return 0.0
+    M = m1 + m2
+    s = 0.0
+    for L in range(max(abs(l1 - l2), abs(l3 - l4), abs(M)), min(l1 + l2, l3 + l4) + 1):
+        s += (-1) ** (M % 2) * gaunt(l1, l2, L, m1, m2, -M) * gaunt(L, l3, l4, M, m3, m4)
+    return s
+
+
+def gaunt_tau(alm: np.ndarray, lmax: int, filt: np.ndarray) -> np.ndarray:
+    """Quartic modes by the brute-force four-harmonic Gaunt sum (no Monte Carlo terms):
+    sum_{l_i m_i} G4 F_p F_r F_s F_u; [C(P+3, 4)], p <= r <= s <= u lexicographic."""
+    filt = np.atleast_2d(filt)
+    P = filt.shape[0]
+    lm, F = full_m_coefficients(alm, lmax, filt)
+    live = [i for i, (l, _) in enumerate(lm) if np.any(filt[:, l] != 0.0)]
+    index = {key: i for i, key in enumerate(lm)}
+    T = np.zeros((P, P, P, P), dtype=np.complex128)
+    for i1 in live:
+        l1, m1 = lm[i1]
+        for i2 in live:
+            l2, m2 = lm[i2]
+            for i3 in live:
+                l3, m3 = lm[i3]
+                m4 = -m1 - m2 - m3
+                for l4 in range(abs(m4), lmax + 1):
+                    i4 = index[(l4, m4)]
+                    if i4 not in live or (l1 + l2 + l3 + l4) % 2:
+                        continue
+                    gv = gaunt4(l1, l2, l3, l4, m1, m2, m3, m4)
+                    if gv != 0.0:
+                        T += gv * np.einsum("a,b,c,d->abcd", F[:, i1], F[:, i2], F[:, i3], F[:, i4])
+    out = [T[p, r, s, u].real for p in range(P) for r in range(p, P) for s in range(r, P) for u in range(s, P)]
+    return np.array(out)

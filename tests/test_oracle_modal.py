@@ -409,3 +409,117 @@ def test_bivector_fit_and_solve_reduce_to_the_full_solve():
     a = np.linalg.solve(L0, alpha)
     B = np.linalg.solve(L0, betas.T)
     assert not np.allclose((a @ wrong @ B) / (a @ wrong @ a), fnl_ref, rtol=1e-6)
+
+
+# ---------------------------------------------------------------- quartic (trispectrum) modes
+
+def test_gaunt4_matches_direct_quadrature():
+    """The four-harmonic Gaunt integral against a Gauss-Legendre x uniform-phi quadrature
+    of scipy's Y_lm product (exact for these degrees)."""
+    from scipy.special import sph_harm_y
+    nr, nphi = 12, 32
+    mu, w = sht.gl_nodes(nr)
+    th = np.arccos(mu)[:, None]
+    ph = (2 * np.pi * np.arange(nphi) / nphi)[None, :]
+    g = np.random.default_rng(5)
+    checked = 0
+    while checked < 12:
+        ls = g.integers(0, 5, size=4)
+        ms = [int(g.integers(-l, l + 1)) for l in ls[:3]]
+        ms.append(-sum(ms))
+        if abs(ms[3]) > ls[3] or sum(ls) % 2:
+            continue
+        prod = np.ones((nr, nphi), dtype=complex)
+        for l, m in zip(ls, ms):
+            prod = prod * sph_harm_y(int(l), int(m), th, ph)
+        ref = np.sum(w[:, None] * (2 * np.pi / nphi) * prod)
+        assert wigner.gaunt4(*[int(v) for v in ls], *ms) == pytest.approx(ref.real, abs=1e-12)
+        assert abs(ref.imag) < 1e-12
+        checked += 1
+
+
+def test_quartic_grid_sum_equals_gaunt_bruteforce():
+    """On an exact-quartic grid (R >= 2L + 1 rings, nphi >= 4L + 1) the grid sum of
+    M_p M_r M_s M_u equals the four-harmonic Gaunt sum of Sec. IV."""
+    L, P = 5, 2
+    nr, nphi = 2 * L + 1, 32
+    mu, w, W = _grid(nr, nphi)
+    cl = simgen.cl_model(L)
+    filt = sht.filter_table(simgen.shifted_legendre_basis(L, P), cl)
+    a = simgen.gaussian_alm(cl, 1, seed=44)[0]
+    got = modal.quartic_tau(sht.synthesize(a, L, filt, mu, nphi), W)
+    ref = wigner.gaunt_tau(a, L, filt)
+    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def _quad_multiplicity(q):
+    c = np.bincount(np.asarray(q), minlength=4)
+    return math.factorial(4) // int(np.prod([math.factorial(int(k)) for k in c]))
+
+
+def _hermite_check(tau_fn, P=3, seed=6):
+    """Constant fields M_a = m_a, <ab> = C_ab: for every direction t the full symmetric
+    contraction sum t_p t_r t_s t_u tau equals sum_x W (t'Ct)^2 He4(t.m / sqrt(t'Ct)),
+    He4 the probabilists' Hermite polynomial (Isserlis' theorem); the values on all t
+    determine the symmetric tensor, so every coefficient and index is checked."""
+    from numpy.polynomial import hermite_e
+    g = np.random.default_rng(seed)
+    nr, nphi = 5, 16
+    W = g.uniform(0.5, 1.5, size=(nr, nphi))
+    m = g.standard_normal(P)
+    A = g.standard_normal((P, P))
+    C = A @ A.T + 0.5 * np.eye(P)
+    maps = np.broadcast_to(m[:, None, None], (P, nr, nphi)).copy()
+    pm = np.stack([np.full((nr, nphi), C[a, b]) for (a, b) in modal.pair_list(P)])
+    tau = tau_fn(maps, W, pm)
+    worst = 0.0
+    for _ in range(8):
+        t = g.standard_normal(P)
+        lhs = sum(_quad_multiplicity(q) * t[q[0]] * t[q[1]] * t[q[2]] * t[q[3]] * tau[n]
+                  for n, q in enumerate(modal.quad_list(P)))
+        s = t @ C @ t
+        rhs = W.sum() * s * s * hermite_e.hermeval((t @ m) / math.sqrt(s), [0, 0, 0, 0, 1])
+        worst = max(worst, abs(lhs - rhs) / max(abs(rhs), 1e-300))
+    return worst
+
+
+def test_quartic_constant_fields_give_the_hermite_polynomial():
+    assert _hermite_check(modal.quartic_tau) < 1e-12
+
+
+def test_quartic_single_pair_term_by_imaginary_shift():
+    """Re prod_i (M + i M')_i = M^4 - sum_6 M'M' M M + M'^4, so over the simulations that
+    define <ab>:  tau(M) = mean_i Re Q(M + i M'_i) - mean_i Q(M'_i) + tau(0), with Q the
+    quartic sum alone and tau(0) = sum_x W sum_3 <ab><cd>."""
+    M, sims, W, P = _antithetic_setup(P=3)
+    pm = modal.pair_means(sims)
+    lhs = modal.quartic_tau(M, W, pm)
+    rhs = (np.mean([modal.quartic_tau(M + 1j * s, W).real for s in sims], axis=0)
+           - np.mean([modal.quartic_tau(s, W) for s in sims], axis=0)
+           + modal.quartic_tau(np.zeros_like(M), W, pm))
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-10, atol=1e-11 * np.abs(lhs).max())
+
+
+def test_planted_quartic_mistakes_are_caught():
+    """Copies of quartic_tau with one mistake each fail the Hermite pin."""
+    def variant(kind):
+        def fn(maps, W, pairmean):
+            P = maps.shape[0]
+            pidx = {pr: i for i, pr in enumerate(modal.pair_list(P))}
+            Mf, pmf, Wf = maps.reshape(P, -1), pairmean.reshape(pairmean.shape[0], -1), W.ravel()
+            mean = lambda a, b: pmf[pidx[(min(a, b), max(a, b))]]
+            splits = modal._QUAD_SPLITS[:3] if kind == "three_splits" else modal._QUAD_SPLITS
+            match = ((0, 1, 2, 3),) * 3 if kind == "one_matching" else modal._QUAD_MATCHINGS
+            sign = -1.0 if kind == "matching_sign" else 1.0
+            out = []
+            for q in modal.quad_list(P):
+                v = np.sum(Wf * Mf[q[0]] * Mf[q[1]] * Mf[q[2]] * Mf[q[3]])
+                for (i, j, k, l) in splits:
+                    v -= np.sum(Wf * mean(q[i], q[j]) * Mf[q[k]] * Mf[q[l]])
+                for (i, j, k, l) in match:
+                    v += sign * np.sum(Wf * mean(q[i], q[j]) * mean(q[k], q[l]))
+                out.append(v)
+            return np.array(out)
+        return fn
+    for kind in ("three_splits", "one_matching", "matching_sign"):
+        assert _hermite_check(variant(kind)) > 1e-3, kind
