@@ -89,6 +89,7 @@ typedef struct {
     int lin_final;           /* 1 once the linear-term mean has been formed   */
     int chunk;               /* maps per internal pass                        */
     size_t device_bytes;     /* device memory held by the plan                */
+    int n_quad;              /* trispectrum modes C(P+3, 4) (modal_quartic)   */
 } modal_info;
 
 /* Build a plan: Gauss-Legendre nodes and weights (FP64 Newton on the host), the
@@ -123,6 +124,18 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
 
 /* Covariance sums over simulations (Eq. linearterm): S1 += sum_b beta_b,
  * S2 += sum_b beta_b beta_b^T (FP64).  dev beta [B][n_max]. */
+/* Trispectrum modal coefficients (Sec. IV: the B term of the quartic estimator with the
+ * four-harmonic Gaunt integral, separable modes q_p q_r q_s q_u, v_l = 1), on the plan's
+ * grid:  tau_prsu = sum_x W_x [M_p M_r M_s M_u - sum over the 6 single pairs <ab> M_c M_d
+ *                              + sum over the 3 pair splits <ab> <cd>]
+ * for p <= r <= s <= u (lexicographic, n_quad = C(P+3, 4) of them); the -6 C a a and +3 C C
+ * terms of Sec. IV symmetrised over the ordered quadruple, with the Monte Carlo pair means
+ * <ab> of modal_linear_term (per pixel, or per ring in MODAL_LINEAR_RING mode).
+ * use_linear = 0 gives the quartic sum alone; otherwise the means must be finalised
+ * (MODAL_ESTATE).  dev alm [B][n_alm] complex64; dev tau [B][n_quad] float64.  The first
+ * call allocates the quartic tables and buffers (about chunk x 0.5 MB x cubic CTAs). */
+modal_status modal_quartic(modal_h h, const void* alm, int B, int use_linear, double* tau, void* stream);
+
 modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* stream);
 
 /* Estimator (Eq. modalest, Eq. modalvariance, Eq. Cholrot): zeta = sample covariance
@@ -242,7 +255,7 @@ modal_status modal_cubic_static(const float* maps, const float* W, long long npi
  * (stage_ms, may be NULL) and the number of kernel launches (launches, may be NULL;
  * counted whether or not profiling is on) since the previous call, then resets both.
  * Stages are numbered 0 .. MODAL_NSTAGES-1; modal_stage_name gives their names. */
-#define MODAL_NSTAGES 14
+#define MODAL_NSTAGES 15
 modal_status modal_set_profiling(modal_h h, int enable);
 modal_status modal_get_profile(modal_h h, double* stage_ms, long long* launches, int nstages);
 const char* modal_stage_name(int stage);

@@ -31,9 +31,9 @@ EXPORTS = [
     "modal_sync", "modal_save_state", "modal_load_state", "modal_selftest_wait", "modal_destroy",
     "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
     "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
-    "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate",
+    "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate", "modal_quartic",
 ]
-MODAL_NSTAGES = 14
+MODAL_NSTAGES = 15
 
 
 class ModalError(RuntimeError):
@@ -51,7 +51,7 @@ class modal_info(ctypes.Structure):
     _fields_ = [("lmax", c_int), ("P", c_int), ("nrings", c_int), ("nphi", c_int), ("prec", c_int),
                 ("n_alm", c_int), ("n_max", c_int), ("n_pair", c_int), ("npix", c_longlong),
                 ("n_lin", c_longlong), ("n_cov", c_longlong), ("lin_final", c_int), ("chunk", c_int),
-                ("device_bytes", c_size_t)]
+                ("device_bytes", c_size_t), ("n_quad", c_int)]
 
 
 _LIB = None
@@ -82,6 +82,7 @@ def load_library():
         "modal_bivector_fit": [H, c_void_p, c_void_p, c_void_p, c_void_p],
         "modal_solve_bivector": [H, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
         "modal_bivector_rotate": [H, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p],
+        "modal_quartic": [H, c_void_p, c_int, c_int, c_void_p, c_void_p],
         "modal_backward": [H, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p],
         "modal_alpha_local": [H, c_void_p, c_void_p],
         "modal_get_info": [H, POINTER(modal_info)],
@@ -183,6 +184,10 @@ def modal_linear_term(h, alm_sims, B, finalize, stream=None):
 
 def modal_cubic(h, alm, B, use_linear, beta, stream=None):
     _check(load_library().modal_cubic(h, _dev(alm), int(B), int(bool(use_linear)), _dev(beta), _stream(stream)))
+
+
+def modal_quartic(h, alm, B, use_linear, tau, stream=None):
+    _check(load_library().modal_quartic(h, _dev(alm), int(B), int(bool(use_linear)), _dev(tau), _stream(stream)))
 
 
 LINEAR_MODES = {"pixel": 0, "ring": 1}

@@ -228,6 +228,8 @@ static void destroy_plan(modal_plan* pl) {
     dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->S1); dfree(pl->S2);
     dfree(pl->ring_sum); dfree(pl->ring_mean);
     dfree(pl->solve_ws); dfree(pl->d_err);
+    dfree(pl->qt.tiles); dfree(pl->qt.idx); dfree(pl->qt.modes); dfree(pl->qt.pa); dfree(pl->qt.pb);
+    dfree(pl->qt.partial); dfree(pl->qt.rq); dfree(pl->qt.h); dfree(pl->qt.k3); dfree(pl->qt.kmat);
     free_tc_tables(*pl);
     free_tc_adj_tables(*pl);
     for (auto& pe : pl->prof_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -582,6 +584,48 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
     return MODAL_OK;
 }
 
+// Quartic tables once per plan; partial sums, ring sums and the single-pair term sized
+// for the current chunk (the pixel-mode single-pair term holds every K split).
+static modal_status ensure_quartic(modal_plan* h) {
+    if (!h->qt.tiles) {
+        CK(quartic_tables(*h), "quartic tables");
+        CK(dalloc(h, &h->qt.k3, (size_t)h->qt.n_quad), "quartic two-pair term");
+        CK(dalloc(h, &h->qt.kmat, (size_t)std::max(h->lin_ksplit, 1) * h->n_pair * h->n_pair), "quartic two-pair sums");
+    }
+    if (h->qt.chunk == h->chunk) return MODAL_OK;
+    dfree(h->qt.partial); dfree(h->qt.rq); dfree(h->qt.h);
+    h->qt.partial = h->qt.rq = h->qt.h = nullptr;
+    h->qt.chunk = 0;
+    const size_t np = h->n_pair, ch = h->chunk;
+    const size_t hring = ch * np * np, hpix = (size_t)h->lin_ksplit * np * ch * np;
+    CK(dalloc(h, &h->qt.partial, ch * h->cubic_ctas * h->qt.n_quad), "quartic partial sums");
+    CK(dalloc(h, &h->qt.rq, ch * np * h->nrings), "quartic ring sums");
+    CK(dalloc(h, &h->qt.h, std::max(hring, hpix)), "quartic single-pair term");
+    h->qt.chunk = h->chunk;
+    return MODAL_OK;
+}
+
+modal_status modal_quartic(modal_h h, const void* alm, int B, int use_linear, double* tau, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && (!alm || !tau)) return set_error(MODAL_EINVAL, "null pointer");
+    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "Monte Carlo terms requested before modal_linear_term(finalize)");
+    if (B == 0) return MODAL_OK;
+    modal_status s = ensure_quartic(h);
+    if (s != MODAL_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    const float2* a = static_cast<const float2*>(alm);
+    if (use_linear) { STAGE(h, ST_LINEAR, st); CK(launch_quartic_k3(*h, st), "quartic two-pair term"); }
+    for (int b0 = 0; b0 < B; b0 += h->chunk) {
+        const int nb = std::min(h->chunk, B - b0);
+        CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "quartic synthesis");
+        { STAGE(h, ST_QUARTIC, st); CK(launch_quartic(*h, h->maps, nb, h->qt.partial, st), "quartic"); }
+        if (use_linear) { STAGE(h, ST_LINEAR, st); CK(launch_quartic_linear(*h, h->maps, nb, st), "quartic single-pair term"); }
+        { STAGE(h, ST_BETA, st); CK(launch_quartic_finalize(*h, nb, use_linear, tau + (size_t)b0 * h->qt.n_quad, st), "quartic finalize"); }
+    }
+    return MODAL_OK;
+}
+
 modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
@@ -866,6 +910,7 @@ modal_status modal_get_info(modal_h h, modal_info* info) {
     info->n_alm = h->n_alm; info->n_max = h->n_max; info->n_pair = h->n_pair; info->npix = h->npix;
     info->n_lin = h->n_lin; info->n_cov = h->n_cov; info->lin_final = h->lin_final; info->chunk = h->chunk;
     info->device_bytes = h->device_bytes;
+    info->n_quad = h->P * (h->P + 1) * (h->P + 2) * (h->P + 3) / 24;
     return MODAL_OK;
 }
 
@@ -1022,7 +1067,7 @@ modal_status modal_load_state(modal_h h, const char* path) {
 static const char* kStageNames[MODAL_NSTAGES] = {
     "legendre", "ring_c2r", "cubic", "linear_gemm", "beta_finalize", "pair_means",
     "cov_accumulate", "solve", "adjoint_pixel", "ring_r2c", "legendre_adjoint", "other",
-    "legendre_prep", "legendre_adjoint_prep"};
+    "legendre_prep", "legendre_adjoint_prep", "quartic"};
 
 const char* modal_stage_name(int stage) {
     return (stage >= 0 && stage < MODAL_NSTAGES) ? kStageNames[stage] : "";

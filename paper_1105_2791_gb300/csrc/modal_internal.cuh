@@ -55,6 +55,22 @@ struct TcAdjTable {
     size_t bytes = 0;
 };
 
+// Trispectrum (quartic) modes: tables built and buffers sized on first use.
+struct QuarticState {
+    int n_quad = 0, ntiles = 0, n_sq = 0;
+    int* tiles = nullptr;         // [ntiles] packed (colex pair group | lexicographic pair quad << 8)
+    int* idx = nullptr;           // [8 n_pg][4 n_sq] quadruple index or -1
+    int* modes = nullptr;         // [n_quad][4] (p, r, s, u)
+    int* pa = nullptr;            // [n_pair] lexicographic pair -> a
+    int* pb = nullptr;            // [n_pair] lexicographic pair -> b
+    double* partial = nullptr;    // [chunk][cubic_ctas][n_quad]
+    double* rq = nullptr;         // [chunk][n_pair][nrings] ring sums of pair products
+    double* h = nullptr;          // single-pair term: ring [chunk][n_pair][n_pair] or pixel [ksplit][n_pair][chunk n_pair]
+    double* kmat = nullptr;       // two-pair sums [ksplit or 1][n_pair][n_pair]
+    double* k3 = nullptr;         // [n_quad] two-pair term
+    int chunk = 0;                // maps the buffers were sized for
+};
+
 struct Plan {
     int lmax = 0, P = 0, nrings = 0, nphi = 0, prec = 0, dev = 0;
     int R_half = 0;          // ring pairs (north rings incl. the equator)
@@ -116,12 +132,13 @@ struct Plan {
     double stage_ms[MODAL_NSTAGES] = {};
     long long stage_launches[MODAL_NSTAGES] = {};
     mutable long long launch_count = 0;   // kernels launched by this plan (note_launch)
+    QuarticState qt;
 };
 
 enum Stage {
     ST_LEGENDRE = 0, ST_C2R = 1, ST_CUBIC = 2, ST_LINEAR = 3, ST_BETA = 4, ST_PAIRS = 5,
     ST_COV = 6, ST_SOLVE = 7, ST_ADJ_PIXEL = 8, ST_R2C = 9, ST_LEGENDRE_ADJ = 10, ST_OTHER = 11,
-    ST_LEGENDRE_PREP = 12, ST_LEGENDRE_ADJ_PREP = 13
+    ST_LEGENDRE_PREP = 12, ST_LEGENDRE_ADJ_PREP = 13, ST_QUARTIC = 14
 };
 
 // ---- error reporting (modal_api.cu) ----
@@ -183,6 +200,12 @@ cudaError_t launch_cholesky(Plan& pl, double* A, int n, cudaStream_t st);
 cudaError_t launch_solve_rhs(Plan& pl, const double* Lc, int n, double* rhs, int nrhs, cudaStream_t st);
 cudaError_t launch_estimates(Plan& pl, const double* rhs, int n, int B, double* out, cudaStream_t st);
 cudaError_t launch_wait_selftest(int* d_err, int spin_limit, cudaStream_t st);
+// trispectrum modes (k_quartic.cu)
+cudaError_t quartic_tables(Plan& pl);
+cudaError_t launch_quartic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
+cudaError_t launch_quartic_linear(Plan& pl, const float* maps, int B, cudaStream_t st);
+cudaError_t launch_quartic_k3(Plan& pl, cudaStream_t st);
+cudaError_t launch_quartic_finalize(Plan& pl, int B, int use_linear, double* tau, cudaStream_t st);
 // bivector form of the covariance (k_solve.cu)
 cudaError_t launch_transpose(Plan& pl, int n, const double* in, double* out, cudaStream_t st);
 cudaError_t launch_power_step(Plan& pl, int n, const double* Z, double* v, double* w, double* stat, cudaStream_t st);

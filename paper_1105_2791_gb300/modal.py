@@ -19,6 +19,7 @@ class Plan:
         info = B.modal_get_info(self.h)
         self.lmax, self.P, self.nrings, self.nphi = info.lmax, info.P, info.nrings, info.nphi
         self.n_alm, self.n_max, self.n_pair, self.npix = info.n_alm, info.n_max, info.n_pair, info.npix
+        self.n_quad = info.n_quad
         self.prec = info.prec
         self.linear_mode = "pixel"
 
@@ -67,6 +68,14 @@ class Plan:
         if out is None:
             out = torch.empty((nb, self.n_max), dtype=torch.float64, device=alm.device)
         B.modal_cubic(self.h, alm, nb, use_linear, out)
+        return out
+
+    def quartic(self, alm, use_linear=False, out=None):
+        """Trispectrum modal coefficients tau [B][n_quad] float64 (modal_quartic)."""
+        nb = alm.shape[0]
+        if out is None:
+            out = torch.empty((nb, self.n_quad), dtype=torch.float64, device=alm.device)
+        B.modal_quartic(self.h, alm, nb, use_linear, out)
         return out
 
     def cov_accumulate(self, beta):
