@@ -49,9 +49,11 @@ def parse():
     ap.add_argument("--chunk", type=int, default=32, help="maps per internal pass of the library")
     ap.add_argument("--linear", choices=["pixel", "ring"], default="pixel",
                     help="Monte Carlo pair means per pixel (default) or per ring (axisymmetric weights)")
-    ap.add_argument("--workload", choices=["l2000", "mixed"], default="l2000",
+    ap.add_argument("--workload", choices=["l2000", "mixed", "trispectrum"], default="l2000",
                     help="l2000: the headline step; mixed: the batched Monte Carlo coefficient pass over "
-                         "l_max 500 / 1000 / 2000 maps (2:1:1, 512 per step) as one captured graph")
+                         "l_max 500 / 1000 / 2000 maps (2:1:1, 512 per step) as one captured graph; "
+                         "trispectrum: the quartic modal coefficients (3876 modes) with per-ring Monte Carlo "
+                         "terms on a band-masked sky")
     return ap.parse_args()
 
 
@@ -426,6 +428,126 @@ def run_mixed(args):
         dist.destroy_process_group()
 
 
+def run_trispectrum(args):
+    """Trispectrum modal coefficients (Sec. IV) at l_max = 2000, 16 basis functions (3876
+    quartic modes), 20-degree band mask, per-ring Monte Carlo means: one step = B maps
+    through synthesis and modal_quartic with the single-pair and two-pair terms."""
+    import torch
+    import torch.distributed as dist
+
+    import simgen
+    import paper_1105_2791_gb300 as M
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L, P = args.lmax, WORKLOAD["P"]
+    R, nphi = L + 1, 1 << int(math.ceil(math.log2(2 * L + 2)))
+    B = args.batch
+    prec = "fp16x3" if args.prec == "auto" else args.prec
+    cl = simgen.cl_model(L)
+    plan = M.Plan(L, P, simgen.shifted_legendre_basis(L, P), cl, R, nphi, prec=prec,
+                  ring_mask=simgen.band_mask(R, 20.0))
+    plan.set_chunk(min(args.chunk, B))
+    plan.set_linear_mode("ring")
+    plan.linear_term(torch.from_numpy(simgen.gaussian_alm(cl, 4, seed=70 + 1000 * rank, stream=simgen.STREAM_LINEAR)
+                                      .astype(np.complex64)).to(dev), finalize=True)
+    alm_pinned = torch.from_numpy(simgen.gaussian_alm(cl, B, seed=71 + 1000 * rank).astype(np.complex64)).pin_memory()
+    alm = alm_pinned.to(dev)
+    tau = torch.empty((B, plan.n_quad), dtype=torch.float64, device=dev)
+    tau_host = torch.empty((B, plan.n_quad), dtype=torch.float64).pin_memory()
+
+    def timed(a, steps, warmup, e2e=False, profile=False):
+        for _ in range(warmup):
+            plan.quartic(a, use_linear=True, out=tau)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        M.modal_get_profile(plan.h)
+        M.modal_set_profiling(plan.h, profile)
+        st = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(st)
+        for _ in range(steps):
+            if e2e:
+                a.copy_(alm_pinned, non_blocking=True)
+            plan.quartic(a, use_linear=True, out=tau)
+            if e2e:
+                tau_host.copy_(tau, non_blocking=True)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        prof = M.modal_get_profile(plan.h)
+        M.modal_set_profiling(plan.h, False)
+        return max_over_ranks(ev0.elapsed_time(ev1), dev), prof
+
+    K, W = args.steps, args.warmup
+    with ClockSampler(local) as clocks:
+        ms, prof0 = timed(alm, K, W)
+    n_prof = max(1, K // 2)
+    _, prof = timed(alm, n_prof, 1, profile=True)
+    e2e_ms, _ = timed(torch.empty_like(alm), K, 1, e2e=True)
+    value = job_throughput(B, K, world, ms)
+    q_ms, q_n = prof["quartic"]
+    npix = R * nphi
+    useful = 2.0 * plan.n_quad * npix * B * n_prof
+    achieved = useful / (q_ms / 1e3) / 1e12
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "quartic (sum_x W M_p M_r M_s M_u, 3876 modes), %d launches, %.3f ms per launch; useful "
+                      "flops 2 x n_quad x npix per map" % (q_n, q_ms / max(q_n, 1))}
+    result = {
+        "metric": "maps/s, trispectrum modal coefficients at l_max=2000, 3876 modes, per-ring MC terms",
+        "value": round(value, 3), "unit": "maps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(ms / K, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "3xtf32": "tf32x3", "fp16x3": "f16x3", "bf16x3": "bf16x3", "bf16": "bf16"}[prec],
+        "data": "synthetic",
+        "config": {"workload": "trispectrum: lmax=%d GL %dx%d, P=%d (3876 quartic modes), band mask 20 deg, "
+                               "per-ring means, batch %d maps/step/GPU, %s synthesis" % (L, R, nphi, P, B, prec),
+                   "lmax": L, "nrings": R, "nphi": nphi, "P": P, "n_quad": plan.n_quad, "batch_per_gpu": B,
+                   "precision": prec, "l2": "inputs and intermediates > L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clocks.summary(),
+        "gpu_launches": int(sum(n for (_, n) in prof0.values())),
+        "e2e": {"value": round(job_throughput(B, K, world, e2e_ms), 3), "unit": "maps/s",
+                "h2d_bytes_per_step": int(alm.numel() * 8), "d2h_bytes_per_step": int(tau.numel() * 8)},
+        "roofline": roof,
+        "stage_ms_per_step": {k: round(v[0] / n_prof, 3) for k, v in prof.items() if v[1]},
+    }
+    if rank == 0 and not args.no_baseline:
+        result["cpu_baseline"] = cpu_baseline_trispectrum(args.cpu_rings)
+    if rank == 0:
+        print(json.dumps(result))
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline_trispectrum(nring_sample, seed=71):
+    """The oracle's synthesis and quartic_tau (with ring means of the same rings) for one
+    map at l_max = 2000 on `nring_sample` rings, extrapolated by ring count."""
+    import simgen
+    from oracle import modal as om, sht as osh
+
+    L, R, nphi, P = WORKLOAD["lmax"], WORKLOAD["nrings"], WORKLOAD["nphi"], WORKLOAD["P"]
+    cl = simgen.cl_model(L)
+    filt = osh.filter_table(simgen.shifted_legendre_basis(L, P), cl)
+    a = simgen.gaussian_alm(cl, 1, seed=seed)[0]
+    mu, w = osh.gl_nodes(R)
+    rings = np.unique(np.linspace(0, R // 2, nring_sample).astype(int))
+    t0 = time.perf_counter()
+    maps = osh.synthesize(a, L, filt, mu[rings], nphi)
+    om.quartic_tau(maps, om.pixel_weights(w[rings], nphi), om.ring_pair_means(om.pair_means([maps])))
+    dt = time.perf_counter() - t0
+    return {"value": round(len(rings) / (dt * R), 8), "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "1 map at lmax=2000 (P=16, 3876 quartic modes) on %d of 2001 rings: synthesis and quartic "
+                      "modes with the Monte Carlo terms; %.1f s, extrapolated by ring count" % (len(rings), dt)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -459,6 +581,8 @@ def main():
         run_reference(args)
     elif args.workload == "mixed":
         run_mixed(args)
+    elif args.workload == "trispectrum":
+        run_trispectrum(args)
     else:
         run_gpu(args)
 

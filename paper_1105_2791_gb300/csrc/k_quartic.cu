@@ -293,8 +293,8 @@ cudaError_t quartic_tables(Plan& pl) {
 __device__ __forceinline__ int qt_pair_lex(int p, int r, int P) { return p * P - (p * (p - 1)) / 2 + (r - p); }
 
 // Ring sums of the pair products of each map: rq[b][(ab)][j] = sum_k M_a M_b (j, k).
-// One CTA per (ring, map); FP32 per-thread sums over the ring's longitudes, FP64 CTA sum
-// in a fixed order.
+// One CTA per (ring, map); FP32 per-thread sums over the ring's longitudes, then one warp
+// per pair reduces them by a fixed shuffle tree; stored in FP64.
 constexpr int QR_THREADS = 128;
 
 template <int PM>
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(QR_THREADS)
 k_pair_ring_maps(int P, int nphi, int64_t npix, int nrings, int n_pair, const float* __restrict__ maps,
                  double* __restrict__ rq) {
     constexpr int NPM = PM * (PM + 1) / 2;
-    extern __shared__ float qr_red[];                        // [NPM][QR_THREADS + 1]
+    extern __shared__ __align__(16) float qr_red[];          // [NPM][QR_THREADS + 4]
     const int j = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
     float acc[NPM];
 #pragma unroll
@@ -322,15 +322,21 @@ k_pair_ring_maps(int P, int nphi, int64_t npix, int nrings, int n_pair, const fl
             }
     }
 #pragma unroll
-    for (int c = 0; c < NPM; ++c) qr_red[c * (QR_THREADS + 1) + tid] = acc[c];
+    for (int c = 0; c < NPM; ++c) qr_red[c * (QR_THREADS + 4) + tid] = acc[c];
     __syncthreads();
-    for (int c = tid; c < NPM; c += QR_THREADS) {
+    // one warp per pair row: four partial sums per lane, then a shuffle tree (FP32, fixed
+    // order), stored in FP64
+    const int warp = tid / 32, lane = tid % 32;
+    for (int c = warp; c < NPM; c += QR_THREADS / 32) {
+        const float4 v = *reinterpret_cast<const float4*>(qr_red + c * (QR_THREADS + 4) + 4 * lane);
+        float t = (v.x + v.y) + (v.z + v.w);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane != 0) continue;
         int p = 0, cc = c;
         while (cc >= PM - p) { cc -= PM - p; ++p; }
         const int r = p + cc;
         if (r >= P) continue;
-        double s = 0.0;
-        for (int t = 0; t < QR_THREADS; ++t) s += (double)qr_red[c * (QR_THREADS + 1) + t];
+        const double s = (double)t;
         rq[((int64_t)b * n_pair + qt_pair_lex(p, r, P)) * nrings + j] = s;
     }
 }
@@ -509,7 +515,7 @@ cudaError_t launch_quartic_linear(Plan& pl, const float* maps, int B, cudaStream
     if (pl.lin_mode == MODAL_LINEAR_RING) {
         const int PM = quartic_pm(pl.P);
         const int npm = PM * (PM + 1) / 2;
-        const size_t smem = (size_t)npm * (QR_THREADS + 1) * sizeof(float);
+        const size_t smem = (size_t)npm * (QR_THREADS + 4) * sizeof(float);
         dim3 grid(pl.nrings, B);
         cudaError_t e;
         if (PM == 4) {

@@ -15,7 +15,8 @@ __device__ __forceinline__ int rl_pair_lex(int p, int r, int P) { return p * P -
 
 // ring_sum[c][j] += sum_b sum_k M_a M_b (j, k), c = (a <= b) lexicographic.  One CTA per
 // ring: each thread sums the products of its longitudes over all maps in FP32 registers,
-// then the CTA reduces the threads' sums in FP64 in a fixed order (deterministic).
+// then one warp per pair reduces the threads' sums by a fixed shuffle tree (deterministic)
+// and adds the result to the FP64 sums.
 constexpr int RP_THREADS = 128;
 
 template <int PM>
@@ -23,7 +24,7 @@ __global__ void __launch_bounds__(RP_THREADS)
 k_pair_ring(int P, int B, int nphi, int64_t npix, int nrings, const float* __restrict__ maps,
             double* __restrict__ ring_sum) {
     constexpr int NPM = PM * (PM + 1) / 2;
-    extern __shared__ float rp_red[];                        // [NPM][RP_THREADS + 1]
+    extern __shared__ __align__(16) float rp_red[];          // [NPM][RP_THREADS + 4]
     const int j = blockIdx.x, tid = threadIdx.x;
     float acc[NPM];
 #pragma unroll
@@ -45,15 +46,21 @@ k_pair_ring(int P, int B, int nphi, int64_t npix, int nrings, const float* __res
         }
     }
 #pragma unroll
-    for (int c = 0; c < NPM; ++c) rp_red[c * (RP_THREADS + 1) + tid] = acc[c];
+    for (int c = 0; c < NPM; ++c) rp_red[c * (RP_THREADS + 4) + tid] = acc[c];
     __syncthreads();
-    for (int c = tid; c < NPM; c += RP_THREADS) {
+    // one warp per pair row: four partial sums per lane, then a shuffle tree (FP32, fixed
+    // order), stored in FP64
+    const int warp = tid / 32, lane = tid % 32;
+    for (int c = warp; c < NPM; c += RP_THREADS / 32) {
+        const float4 v = *reinterpret_cast<const float4*>(rp_red + c * (RP_THREADS + 4) + 4 * lane);
+        float t = (v.x + v.y) + (v.z + v.w);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane != 0) continue;
         int p = 0, cc = c;
         while (cc >= PM - p) { cc -= PM - p; ++p; }
         const int r = p + cc;
         if (r >= P) continue;
-        double s = 0.0;
-        for (int t = 0; t < RP_THREADS; ++t) s += (double)rp_red[c * (RP_THREADS + 1) + t];
+        const double s = (double)t;
         ring_sum[(int64_t)rl_pair_lex(p, r, P) * nrings + j] += s;
     }
 }
@@ -62,13 +69,13 @@ cudaError_t launch_pair_ring(Plan& pl, const float* maps, int B, cudaStream_t st
     if (B == 0) return cudaSuccess;
     note_launch(pl);
     if (pl.P <= 4) {
-        const size_t smem = 10 * (RP_THREADS + 1) * sizeof(float);
+        const size_t smem = 10 * (RP_THREADS + 4) * sizeof(float);
         k_pair_ring<4><<<pl.nrings, RP_THREADS, smem, st>>>(pl.P, B, pl.nphi, pl.npix, pl.nrings, maps, pl.ring_sum);
     } else if (pl.P <= 8) {
-        const size_t smem = 36 * (RP_THREADS + 1) * sizeof(float);
+        const size_t smem = 36 * (RP_THREADS + 4) * sizeof(float);
         k_pair_ring<8><<<pl.nrings, RP_THREADS, smem, st>>>(pl.P, B, pl.nphi, pl.npix, pl.nrings, maps, pl.ring_sum);
     } else {
-        const size_t smem = 136 * (RP_THREADS + 1) * sizeof(float);
+        const size_t smem = 136 * (RP_THREADS + 4) * sizeof(float);
         cudaError_t e = cudaFuncSetAttribute(k_pair_ring<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_pair_ring<16><<<pl.nrings, RP_THREADS, smem, st>>>(pl.P, B, pl.nphi, pl.npix, pl.nrings, maps, pl.ring_sum);
