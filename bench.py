@@ -144,11 +144,72 @@ def legendre_flops(P, lmax, nrings):
     return 4.0 * P * n_alm * ((nrings + 1) // 2)
 
 
-# DRAM bytes per launch of the forward Legendre contraction (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu launch at this workload; see
-# profiles/legendre_tc_fp16x3_l1000_b8.md).  Keyed by (precision, lmax, nphi, P, maps per
-# launch); set to None whenever k_legendre_tc changes until it is captured again.
-LEGENDRE_TRAFFIC_GB = {("fp16x3", 2000, 4096, 16, 32): 17.04 + 16.40}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each stage's
+# kernel, from one-pass ncu captures at this workload (profiles/launches_l2000_b32_fp16x3.md
+# and profiles/legendre_tc_fp16x3_l1000_b8.md).  Keyed by (precision, lmax, nphi, P, maps
+# per launch); an entry is removed whenever its kernel changes until it is captured again.
+STAGE_TRAFFIC_GB = {
+    ("fp16x3", 2000, 4096, 16, 32): {
+        "legendre": 17.04 + 16.40, "ring_c2r": 16.53 + 16.74, "adjoint_pixel": 27.28 + 16.74,
+        "ring_r2c": 17.45 + 16.82, "legendre_adjoint_prep": 16.62 + 16.78, "legendre_adjoint": 26.19 + 0.52,
+        "legendre_prep": 0.51 + 8.39, "pair_means": 37.85 + 8.89, "cubic": 17.84 + 0.11, "linear_gemm": 32.23 + 0.07,
+    },
+}
+
+
+def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps, peaks):
+    """Roofline of every timed stage: algorithmic work per step (flops or bytes) over the
+    stage's live CUDA-event time, against its peak; sorted by time, largest first."""
+    R_half, L1, npix = (R + 1) // 2, L + 1, R * nphi
+    n_alm = (L + 1) * (L + 2) // 2
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", 1710.9)
+    fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    split = {"fp16x3": 3.0, "bf16x3": 3.0, "3xtf32": 6.0, "bf16": 1.0}
+    tensor_peak = bf16 / split[prec] if prec in split else None
+    launches = B // chunk
+    delta_bytes = chunk * P * R_half * L1 * 16.0                  # E and O rows, complex64
+    map_bytes = chunk * P * npix * 4.0
+    # stage: (bound, work per launch, launches per step, peak, unit)
+    work = {
+        "legendre": ("tensor" if tensor_peak else "alu", legendre_flops(P, L, R) * chunk, 3 * launches),
+        "legendre_adjoint": ("tensor" if tensor_peak else "alu", legendre_flops(P, L, R) * chunk, launches),
+        "ring_c2r": ("hbm", delta_bytes + map_bytes, 3 * launches),
+        "ring_r2c": ("hbm", delta_bytes + map_bytes, launches),
+        "adjoint_pixel": ("alu", 2.0 * P * n_pair * npix * chunk, launches),
+        "cubic": ("alu", 2.0 * n_max * npix * chunk, launches),
+        "linear_gemm": ("tensor" if tensor_peak else "alu", 2.0 * n_pair * P * npix * chunk, launches),
+        "pair_means": ("hbm", map_bytes + 2.0 * n_pair * npix * 8, launches),
+        "legendre_prep": ("hbm", chunk * n_alm * 8.0 + chunk * P * 2 * n_alm * 2 * 2.0, 3 * launches),
+        "legendre_adjoint_prep": ("hbm", 2.0 * delta_bytes, launches),
+    }
+    traffic = STAGE_TRAFFIC_GB.get((prec, L, nphi, P, chunk), {})
+    out = []
+    for stage, (bound, per_launch, nl) in work.items():
+        if stage not in prof or not prof[stage][1]:
+            continue
+        ms = prof[stage][0] / n_steps
+        total = per_launch * nl
+        if bound == "hbm":
+            peak, unit, achieved = hbm, "GB/s", total / (ms / 1e3) / 1e9
+            src = "measured HBM copy"
+        elif bound == "tensor":
+            tp = bf16 / 6.0 if stage == "linear_gemm" else tensor_peak     # the linear GEMM runs 3xTF32
+            peak, unit, achieved = tp, "TFLOP/s", total / (ms / 1e3) / 1e12
+            src = "measured bf16 sustained / %s" % ("2 (tf32) / 3 products" if stage == "linear_gemm"
+                                                    else "%g products per useful MAC" % split[prec])
+        else:
+            peak, unit, achieved = fp32, "TFLOP/s", total / (ms / 1e3) / 1e12
+            src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+        t = traffic.get(stage)
+        out.append({"stage": stage, "bound": bound, "achieved": round(achieved, 2), "peak": round(peak, 1),
+                    "unit": unit, "frac": round(achieved / peak, 4), "peak_source": src,
+                    "traffic": round(t, 2) if t is not None else None,
+                    "ms_per_step": round(ms, 3), "launches_per_step": nl,
+                    "per_launch": "%.4g %s" % (per_launch / (1e9 if bound == "hbm" else 1.0),
+                                               "GB" if bound == "hbm" else "flop")})
+    out.sort(key=lambda r: -r["ms_per_step"])
+    return out
 
 
 def run_gpu(args):
@@ -258,28 +319,17 @@ def run_gpu(args):
 
     value = job_throughput(B, K, world, ms)
     e2e_value = job_throughput(B, K, world, e2e_ms)
-    leg_ms, leg_n = prof["legendre"]
     n_prof_steps = max(1, K // 2)
-    flops = legendre_flops(P, L, R) * B * n_prof_steps * 3     # three syntheses per map per step
-    achieved = flops / (leg_ms / 1e3) / 1e12
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
-    if prec == "fp32":
-        # FP32 FMA pipes: 152 SMs x 128 lanes x 2 flops x 2.07 GHz (maximum SM clock)
-        roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(152 * 128 * 2 * 2.07e9 / 1e12, 1),
-                "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    else:
-        bf16 = peaks.get("bf16_tflops_sustained", 1710.9)
-        per = {"fp16x3": 3.0, "bf16x3": 3.0, "3xtf32": 6.0, "bf16": 1.0}[prec]
-        roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(bf16 / per, 1),
-                "unit": "TFLOP/s", "peak_source": "measured bf16 sustained / %g products per useful MAC" % per}
-    roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
-    traffic = LEGENDRE_TRAFFIC_GB.get((prec, L, nphi, P, min(B, args.chunk)))
-    roof["traffic"] = round(traffic, 2) if traffic is not None else None
-    if traffic is not None:
+    rooflines = stage_rooflines(prec, L, R, nphi, P, plan.n_max, plan.n_pair, min(B, args.chunk), B, prof,
+                                n_prof_steps, peaks)
+    top = rooflines[0]
+    roof = {k: top[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "peak_source")}
+    if top["traffic"] is not None:
         roof["traffic_unit"] = "GB per launch (ncu dram bytes read + written)"
-    roof["kernel"] = "legendre (forward Legendre sums), %d launches, %.3f ms per launch" % (
-        leg_n, leg_ms / max(leg_n, 1))
+    roof["kernel"] = "%s: the stage with the largest time per step (%.3f ms, %d launches), %s per launch" % (
+        top["stage"], top["ms_per_step"], top["launches_per_step"], top["per_launch"])
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "maps/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -297,6 +347,7 @@ def run_gpu(args):
         "e2e": {"value": round(e2e_value, 3), "unit": "maps/s",
                 "h2d_bytes_per_step": int(alm.numel() * 8), "d2h_bytes_per_step": int(B * 8 + 8)},
         "roofline": roof,
+        "rooflines": rooflines,
         "stage_ms_per_step": {k: round(v[0] / n_prof_steps, 3) for k, v in prof.items() if v[1]},
     }
 
@@ -500,7 +551,7 @@ def run_trispectrum(args):
             "kernel": "quartic (sum_x W M_p M_r M_s M_u, 3876 modes), %d launches, %.3f ms per launch; useful "
                       "flops 2 x n_quad x npix per map" % (q_n, q_ms / max(q_n, 1))}
     result = {
-        "metric": "maps/s, trispectrum modal coefficients at l_max=2000, 3876 modes, per-ring MC terms",
+        "metric": "maps/s, trispectrum modal coefficients at l_max=%d, %d modes, per-ring MC terms" % (L, plan.n_quad),
         "value": round(value, 3), "unit": "maps/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(ms / K, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "3xtf32": "tf32x3", "fp16x3": "f16x3", "bf16x3": "bf16x3", "bf16": "bf16"}[prec],
