@@ -319,12 +319,20 @@ cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* 
 // k = 0 .. PM/2 - 1.  It works on its pixel's map values shifted by h (v[i] = M_{i+h}),
 // so that both threads run the same code with compile-time indices: its pairs are
 // (2k, r') in the shifted frame, r' >= 2k, i.e. (2k + h, r' + h).  The maps stream
-// through a PA_STAGES-deep ring in shared memory by cp.async (each thread copies and
-// reads only its own column, so no barrier is needed); the FP64 sums are read, updated
-// and written once per launch.
+// through a PA_STAGES-deep ring in shared memory by cp.async: the two threads of a
+// pixel copy alternate rows of its column (each map value is fetched once) and read the
+// whole column after a CTA barrier; a second barrier keeps a stage from being refilled
+// while it is read.  The FP64 sums are read, updated and written once per launch.
 constexpr int PA_THREADS = 128;             // 64 pixels x 2 row parities
 constexpr int PA_PIX = PA_THREADS / 2;
-constexpr int PA_STAGES = 5;               // PM = 16: 80 floats per column >= 72 sums
+constexpr int PA_STAGES = 5;
+
+template <int PM>
+constexpr size_t pa_smem_floats() {
+    constexpr size_t ring = (size_t)PA_STAGES * PM * PA_PIX;
+    constexpr size_t sums = (size_t)((PM / 2) * (PM / 2 + 1)) * PA_THREADS;
+    return ring > sums ? ring : sums;
+}
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -335,22 +343,22 @@ template <int PM>
 __global__ void __launch_bounds__(PA_THREADS)
 k_pair_accumulate(int P, int B, int64_t npix, const float* __restrict__ maps, double* __restrict__ sums) {
     constexpr int NACC = (PM / 2) * (PM / 2 + 1);                // sum over k of (PM - 2k)
-    static_assert(NACC <= PA_STAGES * PM, "the sums must fit one ring column");
-    extern __shared__ __align__(16) float pa_ring[];            // [PA_STAGES][PM][PA_THREADS]
+    extern __shared__ __align__(16) float pa_ring[];            // [PA_STAGES][PM][PA_PIX]; then [NACC][PA_THREADS]
     const int tid = threadIdx.x;
     const int h = tid / PA_PIX, xl = tid % PA_PIX;
     const int nv = P - h;                                       // shifted values that exist
     for (int64_t x0 = (int64_t)blockIdx.x * PA_PIX; x0 < npix; x0 += (int64_t)gridDim.x * PA_PIX) {
         const int64_t x = x0 + xl;
         const bool in = x < npix;
+        __syncthreads();                                              // previous sums read out of the ring
         auto issue = [&](int b) {
             if (b < B && in) {
                 const float* src = maps + ((int64_t)b * P + h) * npix + x;
-                float* dst = pa_ring + (b % PA_STAGES) * PM * PA_THREADS + tid;
-                for (int i = 0; i < nv; ++i) {
+                float* dst = pa_ring + ((b % PA_STAGES) * PM + h) * PA_PIX + xl;
+                for (int i = h; i < P; i += 2) {                        // rows of this thread's parity
                     cp_async4(dst, src);
-                    src += npix;
-                    dst += PA_THREADS;
+                    src += 2 * npix;
+                    dst += 2 * PA_PIX;
                 }
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
@@ -362,12 +370,14 @@ k_pair_accumulate(int P, int B, int64_t npix, const float* __restrict__ maps, do
         for (int c = 0; c < NACC; ++c) acc[c] = 0.f;
 #pragma unroll 1
         for (int b = 0; b < B; ++b) {
+            __syncthreads();                                          // stage (b - 1) % PA_STAGES is free
             issue(b + PA_STAGES - 1);
-            asm volatile("cp.async.wait_group %0;" ::"n"(PA_STAGES - 1) : "memory");   // map b has landed
-            const float* col = pa_ring + (b % PA_STAGES) * PM * PA_THREADS + tid;
+            asm volatile("cp.async.wait_group %0;" ::"n"(PA_STAGES - 1) : "memory");   // this thread's rows of map b
+            __syncthreads();                                          // ... and the partner's
+            const float* col = pa_ring + ((b % PA_STAGES) * PM + h) * PA_PIX + xl;
             float v[PM];
 #pragma unroll
-            for (int i = 0; i < PM; ++i) v[i] = (i < nv && in) ? col[i * PA_THREADS] : 0.f;
+            for (int i = 0; i < PM; ++i) v[i] = (i < nv && in) ? col[i * PA_PIX] : 0.f;
             int c = 0;
 #pragma unroll
             for (int k = 0; k < PM / 2; ++k)
@@ -378,8 +388,9 @@ k_pair_accumulate(int P, int B, int64_t npix, const float* __restrict__ maps, do
                 }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
-        // the sums pass through this thread's own ring column (NACC <= PA_STAGES PM floats)
-        // so that the FP64 update below is a plain loop
+        __syncthreads();                                              // the ring is free
+        // the sums pass through shared memory ([NACC][PA_THREADS]) so that the FP64 update
+        // below is a plain loop
         float* mine = pa_ring + tid;
 #pragma unroll
         for (int c = 0; c < NACC; ++c) mine[c * PA_THREADS] = acc[c];
@@ -406,12 +417,11 @@ cudaError_t launch_pair_accumulate(Plan& pl, const float* maps, int B, cudaStrea
     const int grid = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
     note_launch(pl);
     if (pl.P <= 4)
-        k_pair_accumulate<4><<<grid, PA_THREADS, PA_STAGES * 4 * PA_THREADS * 4, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
+        k_pair_accumulate<4><<<grid, PA_THREADS, pa_smem_floats<4>() * 4, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
     else if (pl.P <= 8)
-        k_pair_accumulate<8><<<grid, PA_THREADS, PA_STAGES * 8 * PA_THREADS * 4, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
+        k_pair_accumulate<8><<<grid, PA_THREADS, pa_smem_floats<8>() * 4, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
     else
-        k_pair_accumulate<16><<<grid, PA_THREADS, PA_STAGES * 16 * PA_THREADS * 4, st>>>(pl.P, B, pl.npix, maps,
-                                                                                      pl.pair_sum);
+        k_pair_accumulate<16><<<grid, PA_THREADS, pa_smem_floats<16>() * 4, st>>>(pl.P, B, pl.npix, maps, pl.pair_sum);
     return cudaGetLastError();
 }
 
