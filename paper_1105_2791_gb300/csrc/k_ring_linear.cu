@@ -6,7 +6,8 @@
 // sums give exactly (sum_k e^{i m phi_k} = 0 for 0 < m < N_phi):
 //     G[(ab), (b, c)] = sum_j W_j <ab>_j R_{b,c}(j),   R_{b,c}(j) = N_phi Re D_{b,c,0}(theta_j),
 // north ring j: D_0 = E + O, its mirror R-1-j: D_0 = E - O.  For the adjoint the pair-mean
-// term of U_t is the per-ring V_{b,t}(j) = sum_c hk[b][t][c] <c>_j.
+// term of U_t is the per-ring V_{b,t}(j) = sum_c hk[b][t][c] <c>_j, constant on each ring,
+// so it is taken off the m = 0 analysis coefficients (k_vring_correct).
 #include "modal_internal.cuh"
 
 namespace modal {
@@ -142,6 +143,42 @@ cudaError_t launch_vring(Plan& pl, const float* hk, int B, float* vring, cudaStr
     if (B == 0) return cudaSuccess;
     dim3 grid((pl.nrings + 127) / 128, B * pl.P);
     k_vring<<<grid, 128, 0, st>>>(pl.n_pair, pl.nrings, hk, pl.ring_mean, vring);
+    note_launch(pl);
+    return cudaGetLastError();
+}
+
+// Ring mode of the adjoint: U_t = W (u_t - V_t(ring)) with V constant on a ring, so the
+// subtraction changes only the m = 0 coefficient of each ring, by nphi W_j V_t(j)
+// (sum_k e^{-i m phi_k} = 0 for 0 < m < nphi).  The analysis stores (U~_n + U~_s, U~_n - U~_s)
+// per ring pair; the equator has no south ring.  amax (split precisions) is raised to the
+// corrected values.
+__global__ void k_vring_correct(int P, int nrows, int R, int R_half, int RH, int L, int nphi,
+                                const float* __restrict__ vring, const float* __restrict__ W,
+                                float2* __restrict__ ut, unsigned* __restrict__ amax) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = blockIdx.y;
+    if (q >= R_half || row >= nrows) return;
+    const int jn = q, js = R - 1 - q;
+    const float* v = vring + (int64_t)row * R;
+    const float cn = (float)nphi * W[(int64_t)jn * nphi] * v[jn];
+    const float cs = (js != jn) ? (float)nphi * W[(int64_t)js * nphi] * v[js] : 0.f;
+    float2* e = ut + (int64_t)row * (L + 1) * 2 * RH + q;     // m = 0: E row, then O row
+    float2 ev = e[0], ov = e[RH];
+    ev.x -= cn + cs;
+    ov.x -= cn - cs;
+    e[0] = ev;
+    e[RH] = ov;
+    if (amax) {
+        const float m = fmaxf(fmaxf(fabsf(ev.x), fabsf(ev.y)), fmaxf(fabsf(ov.x), fabsf(ov.y)));
+        if (m > 0.f) atomicMax(&amax[row / P], __float_as_uint(m));
+    }
+}
+
+cudaError_t launch_vring_correct(Plan& pl, const float* vring, int nrows, float2* ut, unsigned* amax, cudaStream_t st) {
+    if (nrows == 0) return cudaSuccess;
+    dim3 grid((pl.R_half + 127) / 128, nrows);
+    k_vring_correct<<<grid, 128, 0, st>>>(pl.P, nrows, pl.nrings, pl.R_half, pl.RH, pl.lmax, pl.nphi, vring, pl.W, ut,
+                                          amax);
     note_launch(pl);
     return cudaGetLastError();
 }

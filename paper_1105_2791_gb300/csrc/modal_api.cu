@@ -830,16 +830,16 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
     cudaStream_t st = as_stream(stream);
     const float2* a = static_cast<const float2*>(alm);
     float2* out = static_cast<float2*>(grad_alm);
+    // ring mode: the pair-mean term is constant on each ring and enters only through m = 0
+    const bool ring = use_linear && h->lin_mode == MODAL_LINEAR_RING;
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
         CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "backward synthesis");
         { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_weights(*h, g + (size_t)b0 * h->n_max, nb, h->hk, st), "adjoint weights"); }
         {
             STAGE(h, ST_ADJ_PIXEL, st);
-            const bool ring = use_linear && h->lin_mode == MODAL_LINEAR_RING;
             if (ring) CK(launch_vring(*h, h->hk, nb, h->vring, st), "adjoint ring term");
-            CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear && !ring, ring ? h->vring : nullptr, h->maps, st),
-               "adjoint pixel");
+            CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear && !ring, h->maps, st), "adjoint pixel");
         }
         {
             // split precisions: the r2c kernel also records each map's max |U~| for the operand scale
@@ -847,6 +847,7 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
             unsigned* amax = (h->prec == MODAL_FP32) ? nullptr : h->tc.d_amax;
             if (amax) CK(cudaMemsetAsync(amax, 0, nb * sizeof(unsigned), st), "adjoint scale clear");
             CK(launch_ring_r2c(*h, h->maps, nb * h->P, nullptr, h->ut, amax, st), "adjoint r2c");
+            if (ring) CK(launch_vring_correct(*h, h->vring, nb * h->P, h->ut, amax, st), "adjoint ring term");
         }
         if (h->prec == MODAL_FP32) {
             STAGE(h, ST_LEGENDRE_ADJ, st);

@@ -186,12 +186,14 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
 // pair-mean term: per pixel from pl.pair_mean (use_linear, pixel mode) or per ring from
 // vring [B][P][nrings] (ring mode, use_linear = 0); neither when both are off.
 cudaError_t launch_adjoint_u(Plan& pl, const float* maps, int B, const float* hk, int use_linear,
-                             const float* vring, float* u, cudaStream_t st);
+                             float* u, cudaStream_t st);
 // k_ring_linear.cu
 cudaError_t launch_pair_ring(Plan& pl, const float* maps, int B, cudaStream_t st);
 cudaError_t launch_ring_finalize(Plan& pl, cudaStream_t st);
 cudaError_t launch_linear_ring(Plan& pl, int B, double* lin, cudaStream_t st);
 cudaError_t launch_vring(Plan& pl, const float* hk, int B, float* vring, cudaStream_t st);
+// subtract nphi W_j V(j) from the m = 0 analysis coefficients of every ring (ring mode)
+cudaError_t launch_vring_correct(Plan& pl, const float* vring, int nrows, float2* ut, unsigned* amax, cudaStream_t st);
 cudaError_t launch_ring_mean_float(Plan& pl, float* out, cudaStream_t st);
 // k_solve.cu
 cudaError_t launch_cov_accumulate(Plan& pl, const double* beta, int B, cudaStream_t st);
