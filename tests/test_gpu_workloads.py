@@ -121,3 +121,38 @@ def test_precision_sweep_gaussian_and_nongaussian_lmax2000(prec, bound):
         errs.append(_rel(beta[b], ref))
     print("precision sweep lmax=2000 %s: beta rel err G %s, T = G + 50 (G^2 - <G^2>) %s" % (prec, errs[:2], errs[2:]))
     assert max(errs) <= bound
+
+
+def test_lmax3000_tables_resident_in_hbm():
+    """l_max = 3000 on 3001 x 8192 rings, 16 modes: the lambda tables (plain and pre-split for
+    the tensor cores, about 80 GB) stay resident in HBM, so no in-kernel regeneration is
+    needed at this size on one GPU.  Maps on sampled rings and beta restricted to them
+    (ring mask) against the FP64 oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1105_2791_gb300 as M
+    L, P, R, nphi = 3000, 16, 3001, 8192
+    basis = simgen.shifted_legendre_basis(L, P)
+    cl = simgen.cl_model(L)
+    alm = simgen.gaussian_alm(cl, 2, seed=3000).astype(np.complex64)
+    rings = np.array([1, 750, 1500])
+    mask = np.zeros(R)
+    mask[rings] = 1.0
+    plan = _plan(M, L, P, basis, cl, R, nphi, "fp16x3", ring_mask=mask)
+    plan.set_chunk(2)
+    info = plan.info()
+    a = torch.from_numpy(alm).cuda()
+    maps = plan.synthesize(a)[:, :, torch.from_numpy(rings).cuda(), :].cpu().numpy()
+    beta = plan.cubic(a).cpu().numpy()
+    plan.sync()
+    print("lmax=3000 plan holds %.1f GB" % (info.device_bytes / 1e9))
+    plan.close()
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    W = om.pixel_weights(w[rings], nphi)
+    for b in range(2):
+        ref = osh.synthesize(alm[b].astype(np.complex128), L, filt, mu[rings], nphi)
+        merr = np.max(np.abs(maps[b] - ref)) / np.max(np.abs(ref))
+        berr = _rel(beta[b], om.cubic_beta(ref, W))
+        print("lmax=3000 map %d: maps max rel err %.3g, beta rel err %.3g" % (b, merr, berr))
+        assert merr <= 1e-5 and berr <= 1e-5
