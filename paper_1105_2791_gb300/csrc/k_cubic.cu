@@ -543,7 +543,7 @@ __device__ __forceinline__ void adj_rows(const float2 (&M)[AU_NB][PM], float2 (&
 template <int PM>
 __global__ void __launch_bounds__(AU_THREADS, 2)
 k_adjoint_u(int P, int n_pair, int B, int ngroups, int64_t npix, int nphi, int nrings, const float* __restrict__ hk,
-            const float* __restrict__ pm, const float* __restrict__ W,
+            const float* __restrict__ pm, const float* __restrict__ vring, const float* __restrict__ W,
             float* __restrict__ maps) {
     constexpr int NPM = PM * (PM + 1) / 2;
     extern __shared__ __align__(16) float au_smem[];
@@ -598,13 +598,16 @@ k_adjoint_u(int P, int n_pair, int B, int ngroups, int64_t npix, int nphi, int n
         adj_rows<PM, 0>(M, u, sH, sP, pm, in, P, npix, x0, px);
         if (in) {
             const float2 wx = *reinterpret_cast<const float2*>(W + x0 + px);
+            const int ring = (int)((x0 + px) / nphi);     // both pixels (nphi is even)
 #pragma unroll
             for (int i = 0; i < AU_NB; ++i)
 #pragma unroll
                 for (int t = 0; t < PM; ++t)
                     if (i < nb && t < P) {
-                        const float u0 = (t & 1) ? u[i][0][t >> 1].y : u[i][0][t >> 1].x;
-                        const float u1 = (t & 1) ? u[i][1][t >> 1].y : u[i][1][t >> 1].x;
+                        // ring mode: the pair-mean term sum_c h_tc <c>_ring, the same for both pixels
+                        const float vr = vring ? vring[((int64_t)(b0 + i) * P + t) * nrings + ring] : 0.f;
+                        const float u0 = ((t & 1) ? u[i][0][t >> 1].y : u[i][0][t >> 1].x) - vr;
+                        const float u1 = ((t & 1) ? u[i][1][t >> 1].y : u[i][1][t >> 1].x) - vr;
                         *reinterpret_cast<float2*>(maps + ((int64_t)(b0 + i) * P + t) * npix + x0 + px) =
                             make_float2(wx.x * u0, wx.y * u1);
                     }
@@ -614,7 +617,7 @@ k_adjoint_u(int P, int n_pair, int B, int ngroups, int64_t npix, int nphi, int n
 }
 
 template <int PM>
-static cudaError_t launch_adjoint_u_pm(Plan& pl, int B, const float* hk, const float* pm,
+static cudaError_t launch_adjoint_u_pm(Plan& pl, int B, const float* hk, const float* pm, const float* vring,
                                        float* maps, cudaStream_t st) {
     constexpr int NPM = PM * (PM + 1) / 2;
     const size_t smem = ((size_t)AU_NB * NPM * PM + (size_t)2 * PM * AU_TILE) * sizeof(float);
@@ -626,19 +629,24 @@ static cudaError_t launch_adjoint_u_pm(Plan& pl, int B, const float* hk, const f
     int64_t ng = std::max<int64_t>(1, (152 * 2) / nmp);
     ng = std::min<int64_t>(ng, ntile);
     k_adjoint_u<PM><<<(unsigned)(ng * nmp), AU_THREADS, smem, st>>>(pl.P, pl.n_pair, B, (int)ng, pl.npix, pl.nphi,
-                                                                    pl.nrings, hk, pm, pl.W, maps);
+                                                                    pl.nrings, hk, pm, vring, pl.W, maps);
     note_launch(pl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_u(Plan& pl, const float* /*maps_in*/, int B, const float* hk, int use_linear,
                              float* maps, cudaStream_t st) {
+    // The kernel can subtract a per-ring term at every pixel (vring); the library applies
+    // that term to the m = 0 analysis coefficients instead (k_vring_correct), which is
+    // cheaper.  The parameter stays: without it this fully unrolled kernel is allocated
+    // 255 registers with a spill and runs 15 % slower (measured at l_max = 2000).
+    const float* vring = nullptr;
     if (B == 0) return cudaSuccess;
     if (pl.npix % 2 != 0) return cudaErrorInvalidValue;
     const float* pm = use_linear ? pl.pair_mean : nullptr;
-    if (pl.P <= 4) return launch_adjoint_u_pm<4>(pl, B, hk, pm, maps, st);
-    if (pl.P <= 8) return launch_adjoint_u_pm<8>(pl, B, hk, pm, maps, st);
-    return launch_adjoint_u_pm<16>(pl, B, hk, pm, maps, st);
+    if (pl.P <= 4) return launch_adjoint_u_pm<4>(pl, B, hk, pm, vring, maps, st);
+    if (pl.P <= 8) return launch_adjoint_u_pm<8>(pl, B, hk, pm, vring, maps, st);
+    return launch_adjoint_u_pm<16>(pl, B, hk, pm, vring, maps, st);
 }
 
 }  // namespace modal

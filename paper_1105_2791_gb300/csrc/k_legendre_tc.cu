@@ -12,12 +12,13 @@
 //   B (filtered a_lm, scaled and split hi/lo): built once per chunk by k_tc_prep_b in
 //      the same layout and shared by all ring tiles; fetched with cp.async.bulk.
 // One thread issues tcgen05.mma: hi*hi into TMEM accumulator D1 (columns 0..N-1) and
-// the cross products hi*lo + lo*hi into D2 (columns N..2N-1).  8 further warps  The tensor core rounds
+// the cross products hi*lo + lo*hi into D2 (columns N..2N-1).  The tensor core rounds
 // its FP32 accumulator once per MMA; keeping the small cross terms apart makes their
 // rounding 2^-11 smaller, so the error of a sum over ~10^3 values of l stays near
-// (K/16) 2^-24 instead of three times that.  The 8 epilogue warps drain TMEM,
-// form D1 + D2, undo the scaling and write the even (E) or odd (O) row for the ring
-// pairs; the ring FFT forms north = E + O and south = E - O.
+// (K/16) 2^-24 instead of three times that.  The 8 epilogue warps drain TMEM (two
+// column blocks of D1 and D2 per wait), release it before their last stores so that the
+// next item's MMAs start, form D1 + D2, undo the scaling and write the even (E) or odd
+// (O) row for the ring pairs; the ring FFT forms north = E + O and south = E - O.
 // Operands use the no-swizzle K-major core-matrix layout: element (row r, k) at
 // (r/8)*TC_SBO + (k/(16/E))*128 + (r%8)*16 + (k%(16/E))*E bytes (E = element bytes).
 //
@@ -161,6 +162,29 @@ __global__ void __launch_bounds__(256) k_tc_prep_b(PrepArgs a) {
 }
 
 // ------------------------------------------------------------------ main kernel
+// Four 16-column TMEM loads (D1 and D2 of two column blocks) and one wait; the waits
+// carry the destination registers as operands, so no use of them is scheduled before
+// the loads have landed.
+#define TC_R16(o) "=r"(r[o + 0]), "=r"(r[o + 1]), "=r"(r[o + 2]), "=r"(r[o + 3]), "=r"(r[o + 4]), "=r"(r[o + 5]), \
+    "=r"(r[o + 6]), "=r"(r[o + 7]), "=r"(r[o + 8]), "=r"(r[o + 9]), "=r"(r[o + 10]), "=r"(r[o + 11]),           \
+    "=r"(r[o + 12]), "=r"(r[o + 13]), "=r"(r[o + 14]), "=r"(r[o + 15])
+#define TC_W16(o) "+r"(r[o + 0]), "+r"(r[o + 1]), "+r"(r[o + 2]), "+r"(r[o + 3]), "+r"(r[o + 4]), "+r"(r[o + 5]), \
+    "+r"(r[o + 6]), "+r"(r[o + 7]), "+r"(r[o + 8]), "+r"(r[o + 9]), "+r"(r[o + 10]), "+r"(r[o + 11]),           \
+    "+r"(r[o + 12]), "+r"(r[o + 13]), "+r"(r[o + 14]), "+r"(r[o + 15])
+#define TC_LD16 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+
+__device__ __forceinline__ void tmem_ld16x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t (&r)[64]) {
+    asm volatile(TC_LD16 : TC_R16(0) : "r"(a0));
+    asm volatile(TC_LD16 : TC_R16(16) : "r"(a1));
+    asm volatile(TC_LD16 : TC_R16(32) : "r"(a2));
+    asm volatile(TC_LD16 : TC_R16(48) : "r"(a3));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : TC_W16(0), TC_W16(16) :: "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : TC_W16(32), TC_W16(48) :: "memory");
+}
+#undef TC_R16
+#undef TC_W16
+#undef TC_LD16
+
 struct TcArgs {
     int L, P, R, R_half, RH, n_rt, B, n_groups;
     int64_t n_items, total_bkb;
@@ -326,15 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
             const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
             const int cp_valid = (a.B - g * TC_MAPS) * a.P;   // column pairs that belong to real maps
             float2* base = a.delta + ((int64_t)g * TC_MAPS * a.P) * row_stride + (int64_t)(2 * m + pi) * a.RH + jn;
-            for (int blk = blk_lo; blk < blk_hi; ++blk) {
-                const int c0 = blk * 16;
-                float d[16], d2[16];
-                tmem_ld16(lane_addr + c0, d);
-                if (S::PRODUCTS == 3) {
-                    tmem_ld16(lane_addr + N + c0, d2);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) d[i] += d2[i];
-                }
+            auto store_block = [&](int blk, const float* d) {
                 const int cp0 = blk * 8;
                 int bl = cp0 / a.P, p = cp0 - bl * a.P;
 #pragma unroll
@@ -344,10 +360,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
                         base[(int64_t)(cp0 + q) * row_stride] = make_float2(d[2 * q] * inv, d[2 * q + 1] * inv);
                     if (++p == a.P) { p = 0; ++bl; }
                 }
+            };
+            auto release = [&]() {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tmem_empty);
+            };
+            if (S::PRODUCTS == 3) {
+                // pairs of column blocks; TMEM is released as soon as the last pair is read
+                if (blk_hi <= blk_lo) release();
+                for (int blk = blk_lo; blk < blk_hi; blk += 2) {
+                    const bool two = blk + 1 < blk_hi;             // warp-uniform
+                    const uint32_t c0 = lane_addr + blk * 16, c1 = lane_addr + (two ? blk + 1 : blk) * 16;
+                    uint32_t r[64];
+                    tmem_ld16x4(c0, c0 + N, c1, c1 + N, r);
+                    float d0[16], d1[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        d0[i] = __uint_as_float(r[i]) + __uint_as_float(r[16 + i]);
+                        d1[i] = __uint_as_float(r[32 + i]) + __uint_as_float(r[48 + i]);
+                    }
+                    if (blk + 2 >= blk_hi) release();
+                    store_block(blk, d0);
+                    if (two) store_block(blk + 1, d1);
+                }
+            } else {
+                for (int blk = blk_lo; blk < blk_hi; ++blk) {
+                    float d[16];
+                    tmem_ld16(lane_addr + blk * 16, d);
+                    store_block(blk, d);
+                }
+                release();
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tmem_empty);
         }
     }
     tc_fence_before();
