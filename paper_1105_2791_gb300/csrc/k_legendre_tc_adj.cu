@@ -93,7 +93,8 @@ struct AdjPrepArgs {
 // B block (g, m, pi, kb): rows n = (bl, t, re/im), K = ring pairs j = kb KPS + k.
 // A thread takes one (bl, t) and one core-matrix column kc: it reads the CM values of
 // U~ there as 16-byte vectors and writes the hi and lo parts of both the Re row (n = 2q)
-// and the Im row (n = 2q + 1).
+// and the Im row (n = 2q + 1) (one 32-byte sector per part).  Consecutive threads take
+// consecutive kc of one row, so a row's KPS values are read as one contiguous run.
 template <int PREC>
 __global__ void __launch_bounds__(256) k_tc_prep_adj(AdjPrepArgs a) {
     using S = Split<PREC>;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(256) k_tc_prep_adj(AdjPrepArgs a) {
     for (int kb = blockIdx.x; kb < a.nkb; kb += gridDim.x) {
         char* bt = a.out + ((((int64_t)g * (a.L + 1) + m) * 2 + pi) * a.nkb + kb) * (int64_t)(2 * b_tile);
         for (int c = threadIdx.x; c < NKC * NQ; c += blockDim.x) {
-            const int kc = c / NQ, q = c % NQ;
+            const int kc = c % NKC, q = c / NKC;           // the NKC threads of a row read it contiguously
             const int bl = q / a.P, t = q % a.P;
             const int b = g * TC_MAPS + bl;
             const float sc = s_scale[bl];
