@@ -3,11 +3,14 @@
 //   G[(b, c), (ab)] = sum_x maps_{b,c}(x) * W_x <M_a M_b>_x        (Eq. bispectrumest linear term)
 //
 // M = 128 rows of (map, basis function), N = 144 (pairs, zero-padded), K = pixels.
-// Work item = (row tile, pixel range); a persistent CTA loops over items.  Per stage
-// (32 pixels) eight converter warps load the raw FP32 rows (maps; pair mean times W),
-// split each value into two tf32 parts rounded to nearest and store them in the
-// no-swizzle K-major core-matrix layout; one thread issues tcgen05.mma (kind::tf32,
-// hi*hi + hi*lo + lo*hi) into one of two TMEM accumulators.  Because the tensor core
+// Work item = (row tile, pixel range); a persistent CTA loops over items.  The B
+// operand, W <M_a M_b> split into tf32 hi/lo in the no-swizzle K-major core-matrix
+// layout, is the same for every map: k_lt_presplit builds it once per finalised mean,
+// one block of 32 pixels per stage, and a loader thread streams each stage's block into
+// shared memory with one cp.async.bulk.  Per stage eight converter warps load the maps'
+// FP32 rows, split each value into two tf32 parts rounded to nearest and store them in
+// the same layout; one thread issues tcgen05.mma (kind::tf32, hi*hi + hi*lo + lo*hi) into
+// one of two TMEM accumulators.  Because the tensor core
 // rounds its FP32 accumulator once per MMA, every 4 stages (16 MMA steps) the
 // accumulator is handed to eight epilogue warps that add it into FP32 register sums
 // and release it; the MMAs continue in the other buffer.  At the end of an item the
@@ -36,12 +39,35 @@ struct LinArgs {
     int nrows, ncols, n_pair;              // rows = n_pair (pairs), cols = B * P
     int64_t npix, krange;                  // pixels per item
     int n_mt, n_kr;
-    const float* panel;                    // [n_pair][npix]
-    const float* W;                        // [npix]
+    const char* bsplit;                    // [npix / 32][hi B tile, lo B tile] (k_lt_presplit)
     const float* maps;                     // [cols][npix]
     double* out;                           // [n_kr][n_pair][ncols]
     int* err;
 };
+
+// One 32-pixel stage of the B operand per CTA: W_x <pair>_x split into tf32 hi/lo, rows
+// 0..143 (pairs, zero past n_pair), stored as [hi tile][lo tile] with the converters'
+// chunk order and core-matrix offsets.
+__global__ void __launch_bounds__(256) k_lt_presplit(int n_pair, int64_t npix, const float* __restrict__ panel,
+                                                     const float* __restrict__ W, char* __restrict__ out) {
+    const int64_t xs = (int64_t)blockIdx.x * LT_KPX;
+    char* base = out + (int64_t)blockIdx.x * 2 * LT_B_TILE;
+    for (int c = threadIdx.x; c < LT_N * 8; c += blockDim.x) {
+        const int row = ((c >> 6) << 3) + (c & 7), kc = (c >> 3) & 7;
+        const int64_t x = xs + kc * 4;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (row < n_pair)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (x + i < npix) v[i] = panel[(int64_t)row * npix + x + i] * W[x + i];
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Split<MODAL_3XTF32>::split(v[i], hv[i], lv[i]);
+        const int off = (row >> 3) * 1024 + kc * 128 + (row & 7) * 16;
+        *reinterpret_cast<uint4*>(base + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(base + LT_B_TILE + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+}
 
 __device__ __forceinline__ uint64_t lt_desc(uint32_t saddr) {
     uint64_t d = 0;
@@ -77,7 +103,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
-            mbar_init(&full[s], LT_CONV_WARPS);
+            mbar_init(&full[s], LT_CONV_WARPS + 1);         // converters + the B loader's expect_tx
             mbar_init(&empty[s], 1);
             mbar_init(&acc_full[s], 1);
             mbar_init(&acc_empty[s], LT_EPI_WARPS);
@@ -96,7 +122,36 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
     const uint32_t tmem = *tmem_slot;
     const int64_t n_items = (int64_t)a.n_mt * a.n_kr;
 
-    if (warp == 1) {
+    if (warp == 0) {
+        // ---------------- B loader (one thread): the pre-split pair-mean block of each stage
+        if (lane == 0) {
+            uint32_t it = 0;
+            uint32_t last_phase[2] = {0, 0};
+            bool issued[2] = {false, false};
+            for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+                const int kr = (int)(item % a.n_kr);
+                const int64_t x0 = (int64_t)kr * a.krange, x1 = min(a.npix, x0 + a.krange);
+                const int nst = (int)(((x1 > x0 ? x1 - x0 : (int64_t)0) + LT_KPX - 1) / LT_KPX);
+                for (int st = 0; st < nst; ++st, ++it) {
+                    const int s = it & 1;
+                    const uint32_t ph = (it >> 1) & 1;
+                    if (!mbar_wait(&empty[s], ph ^ 1, abort_flag, a.err)) break;
+                    mbar_arrive_expect_tx(&full[s], 2 * LT_B_TILE);
+                    bulk_copy_g2s(stages + s * LT_STAGE + 2 * LT_A_TILE,
+                                  a.bsplit + (x0 / LT_KPX + st) * (int64_t)(2 * LT_B_TILE), 2 * LT_B_TILE, &full[s]);
+                    last_phase[s] = ph;
+                    issued[s] = true;
+                }
+            }
+            // copies still in flight complete before the CTA exits
+            for (int s = 0; s < 2; ++s) {
+                if (!issued[s]) continue;
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&full[s], last_phase[s]) && clock64() - t0 < TC_WAIT_CYCLES) {
+                }
+            }
+        }
+    } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = umma_idesc(2, LT_N);
@@ -137,7 +192,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
             }
         }
     } else if (warp >= 2 && warp < 2 + LT_CONV_WARPS) {
-        // ---------------- converters: raw FP32 rows -> tf32 hi/lo core matrices
+        // ---------------- converters: the maps' FP32 rows -> tf32 hi/lo core matrices (A)
         const int ct = threadIdx.x - 64;                    // 0 .. 255
         uint32_t it = 0;
         for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -152,25 +207,17 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
                 if (ok) {
                     char* base = stages + s * LT_STAGE;
                     const int64_t xs = x0 + (int64_t)st * LT_KPX;
-                    // A: 128 rows x 8 chunks of 4 pixels; B: 144 rows x 8 chunks.  Chunk index c runs
-                    // over blocks of 8 rows, and within a block kc-major: c = 64 (row / 8) + 8 kc +
-                    // row % 8, so that 8 consecutive threads store the 8 rows of one core matrix (128
-                    // contiguous bytes) and a warp's 16-byte stores are free of bank conflicts.  Thread
-                    // ct owns chunk column kc = (ct / 8) % 8 in every row it touches (stride 256 keeps
-                    // kc fixed), so W is read once; all loads of the stage are issued before any value
-                    // is split.
-                    constexpr int NCH = (128 + LT_N) * 8;
-                    constexpr int NU = (NCH + 32 * LT_CONV_WARPS - 1) / (32 * LT_CONV_WARPS);
+                    // A: 128 rows x 8 chunks of 4 pixels.  Chunk index c runs over blocks of 8 rows,
+                    // and within a block kc-major: c = 64 (row / 8) + 8 kc + row % 8, so that 8
+                    // consecutive threads store the 8 rows of one core matrix (128 contiguous bytes)
+                    // and a warp's 16-byte stores are free of bank conflicts.  Thread ct owns chunk
+                    // column kc = (ct / 8) % 8 in every row it touches (stride 256 keeps kc fixed);
+                    // all loads of the stage are issued before any value is split.
+                    constexpr int NCH = 128 * 8;
+                    constexpr int NU = NCH / (32 * LT_CONV_WARPS);
                     const int kc = (ct >> 3) & 7;
                     const int64_t x = xs + kc * 4;
                     const bool whole = (x + 3 < x1);            // x is a multiple of 4: 16-byte aligned
-                    float4 wv = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (whole) wv = *reinterpret_cast<const float4*>(a.W + x);
-                    else {
-                        if (x + 0 < x1) wv.x = a.W[x + 0];
-                        if (x + 1 < x1) wv.y = a.W[x + 1];
-                        if (x + 2 < x1) wv.z = a.W[x + 2];
-                    }
                     float4 vals[NU];
 #pragma unroll
                     for (int u = 0; u < NU; ++u) {
@@ -178,14 +225,8 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
                         const int row = ((c >> 6) << 3) + (c & 7);
                         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                         const float* src = nullptr;
-                        if (c < NCH) {
-                            if (row < 128) {
-                                const int gr = mt * 128 + row;
-                                if (gr < a.ncols) src = a.maps + (int64_t)gr * a.npix + x;
-                            } else if (row - 128 < a.n_pair) {
-                                src = a.panel + (int64_t)(row - 128) * a.npix + x;
-                            }
-                        }
+                        const int gr = mt * 128 + row;
+                        if (gr < a.ncols) src = a.maps + (int64_t)gr * a.npix + x;
                         if (src) {
                             if (whole) v = *reinterpret_cast<const float4*>(src);
                             else {
@@ -199,26 +240,16 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
 #pragma unroll
                     for (int u = 0; u < NU; ++u) {
                         const int c = ct + u * 32 * LT_CONV_WARPS;
-                        if (c >= NCH) continue;
                         const int row = ((c >> 6) << 3) + (c & 7);
-                        float4 v = vals[u];
-                        if (row >= 128) {
-                            v.x *= wv.x;
-                            v.y *= wv.y;
-                            v.z *= wv.z;
-                            v.w *= wv.w;
-                        }
+                        const float4 v = vals[u];
                         uint32_t hv[4], lv[4];
                         Split<MODAL_3XTF32>::split(v.x, hv[0], lv[0]);
                         Split<MODAL_3XTF32>::split(v.y, hv[1], lv[1]);
                         Split<MODAL_3XTF32>::split(v.z, hv[2], lv[2]);
                         Split<MODAL_3XTF32>::split(v.w, hv[3], lv[3]);
-                        const int r = (row < 128) ? row : row - 128;
-                        const int off = (r >> 3) * 1024 + kc * 128 + (r & 7) * 16;
-                        char* hi = base + ((row < 128) ? 0 : 2 * LT_A_TILE);
-                        const int part = (row < 128) ? LT_A_TILE : LT_B_TILE;
-                        *reinterpret_cast<uint4*>(hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                        *reinterpret_cast<uint4*>(hi + part + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                        const int off = (row >> 3) * 1024 + kc * 128 + (row & 7) * 16;
+                        *reinterpret_cast<uint4*>(base + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                        *reinterpret_cast<uint4*>(base + LT_A_TILE + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                     }
                     fence_proxy_async();
                 }
@@ -284,9 +315,21 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
     }
 }
 
+size_t linear_presplit_bytes(const Plan& pl) {
+    return (size_t)((pl.npix + LT_KPX - 1) / LT_KPX) * 2 * LT_B_TILE;
+}
+
+cudaError_t launch_linear_presplit(Plan& pl, cudaStream_t st) {
+    if (pl.n_pair > LT_N || !pl.lin_bsplit) return cudaErrorInvalidValue;
+    const int64_t nst = (pl.npix + LT_KPX - 1) / LT_KPX;
+    k_lt_presplit<<<(unsigned)nst, 256, 0, st>>>(pl.n_pair, pl.npix, pl.pair_mean, pl.W, pl.lin_bsplit);
+    note_launch(pl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
-    if (pl.n_pair > LT_N) return cudaErrorInvalidValue;
+    if (pl.n_pair > LT_N || !pl.lin_bsplit) return cudaErrorInvalidValue;
     LinArgs a;
     a.nrows = pl.n_pair;
     a.ncols = B * pl.P;
@@ -295,8 +338,7 @@ cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial
     a.n_mt = (a.ncols + 127) / 128;
     a.n_kr = pl.lin_ksplit;
     a.krange = ((pl.npix + a.n_kr - 1) / a.n_kr + LT_KPX - 1) / LT_KPX * LT_KPX;
-    a.panel = pl.pair_mean;
-    a.W = pl.W;
+    a.bsplit = pl.lin_bsplit;
     a.maps = maps;
     a.out = partial;
     a.err = pl.d_err;

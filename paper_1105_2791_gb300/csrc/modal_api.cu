@@ -225,7 +225,7 @@ static void destroy_plan(modal_plan* pl) {
     free_workspace(pl);
     dfree(pl->lam); dfree(pl->filt); dfree(pl->W); dfree(pl->wring); dfree(pl->twiddle);
     dfree(pl->modeidx); dfree(pl->tiles); dfree(pl->pair_ab);
-    dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->S1); dfree(pl->S2);
+    dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->lin_bsplit); dfree(pl->S1); dfree(pl->S2);
     dfree(pl->ring_sum); dfree(pl->ring_mean);
     dfree(pl->solve_ws); dfree(pl->d_err);
     dfree(pl->qt.tiles); dfree(pl->qt.idx); dfree(pl->qt.modes); dfree(pl->qt.pa); dfree(pl->qt.pb);
@@ -526,6 +526,15 @@ modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void*
     return MODAL_OK;
 }
 
+// The tensor-core linear term reads W <pair> pre-split into tf32 hi/lo; rebuilt whenever
+// the per-pixel mean is finalised.
+static modal_status refresh_linear_presplit(modal_plan* h, cudaStream_t st) {
+    if (h->prec == MODAL_FP32 || h->lin_mode == MODAL_LINEAR_RING) return MODAL_OK;
+    if (!h->lin_bsplit) CK(dalloc(h, &h->lin_bsplit, linear_presplit_bytes(*h)), "pre-split pair-mean panel");
+    CK(launch_linear_presplit(*h, st), "pair-mean panel split");
+    return MODAL_OK;
+}
+
 modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int finalize, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
@@ -548,6 +557,8 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
         STAGE(h, ST_PAIRS, st);
         if (ring) CK(launch_ring_finalize(*h, st), "ring pair means");
         else CK(launch_pair_finalize(*h, st), "pair finalize");
+        const modal_status ps = refresh_linear_presplit(h, st);
+        if (ps != MODAL_OK) return ps;
         h->lin_final = 1;
     }
     return MODAL_OK;
@@ -1059,6 +1070,8 @@ modal_status modal_load_state(modal_h h, const char* path) {
     if (hd.has_pairs && hd.lin_final && h->n_lin > 0) {
         if (hd.has_pairs == 2) CK(launch_ring_finalize(*h, 0), "ring pair means");
         else CK(launch_pair_finalize(*h, 0), "pair finalize");
+        const modal_status ps = refresh_linear_presplit(h, 0);
+        if (ps != MODAL_OK) return ps;
         CK(cudaDeviceSynchronize(), "load sync");
         h->lin_final = 1;
     }

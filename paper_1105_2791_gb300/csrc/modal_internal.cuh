@@ -98,6 +98,7 @@ struct Plan {
     // Monte Carlo accumulators
     double* pair_sum = nullptr;  // [n_pair][npix]
     float* pair_mean = nullptr;  // [n_pair][npix]
+    char* lin_bsplit = nullptr;  // W <pair> split into tf32 hi/lo per 32-pixel stage (tensor-core linear term)
     long long n_lin = 0;
     int lin_final = 0;
     double* S1 = nullptr;        // [n_max]
@@ -177,6 +178,8 @@ cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmaps_p, cons
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);   // k_linear_tc.cu
+size_t linear_presplit_bytes(const Plan& pl);
+cudaError_t launch_linear_presplit(Plan& pl, cudaStream_t st);   // after each finalised pixel mean
 // lin_splits: K splits summed from lin_partial ([lin_splits][n_pair][B P])
 cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* cub_partial,
                                  const double* lin_partial, int lin_splits, double* beta, cudaStream_t st);
