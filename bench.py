@@ -274,19 +274,29 @@ def run_gpu(args):
     plan.cov_accumulate(torch.randn((2 * plan.n_max, plan.n_max), generator=gen, device=dev, dtype=torch.float64))
     torch.cuda.synchronize()
 
-    def step(pl, a, e2e=False):
+    side = torch.cuda.Stream(device=dev)
+
+    def step(pl, a, e2e=False, overlap=True):
         if e2e:
             a.copy_(alm_pinned, non_blocking=True)
         pl.linear_term(a)
         pl.cubic(a, use_linear=True, out=beta)
         pl.cov_accumulate(beta)
-        fnl, sigma = pl.solve(alpha, beta)
+        if not overlap:                                  # per-stage timing: one stream, stages in order
+            fnl, sigma = pl.solve(alpha, beta)
+            pl.backward(a, g, use_linear=True, out=grad)
+            return fnl, sigma
+        # the FP64 solve (latency-bound, a few CTAs) runs on a side stream beside the adjoint
+        ready = torch.cuda.Event()
+        ready.record(torch.cuda.current_stream())
         pl.backward(a, g, use_linear=True, out=grad)
+        side.wait_event(ready)
+        fnl, sigma = M.modal_solve(pl.h, alpha, beta, beta.shape[0], stream=side)
         return fnl, sigma
 
     def timed(pl, a, steps, warmup, e2e=False, profile=False):
         for _ in range(warmup):
-            step(pl, a, e2e)
+            step(pl, a, e2e, overlap=not profile)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -297,7 +307,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         ev0.record(st)
         for _ in range(steps):
-            step(pl, a, e2e)
+            step(pl, a, e2e, overlap=not profile)
         ev1.record(st)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
