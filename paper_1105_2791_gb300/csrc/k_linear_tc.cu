@@ -3,7 +3,9 @@
 //   G[(b, c), (ab)] = sum_x maps_{b,c}(x) * W_x <M_a M_b>_x        (Eq. bispectrumest linear term)
 //
 // M = 128 rows of (map, basis function), N = 144 (pairs, zero-padded), K = pixels.
-// Work item = (row tile, pixel range); a persistent CTA loops over items.  The B
+// Work item = (row tile, pixel range), row tile fastest, so that the CTAs working on the
+// row tiles of one pixel range run side by side and read its B blocks once from HBM and
+// then from L2; a persistent CTA loops over items.  The B
 // operand, W <M_a M_b> split into tf32 hi/lo in the no-swizzle K-major core-matrix
 // layout, is the same for every map: k_lt_presplit builds it once per finalised mean,
 // one block of 32 pixels per stage, and a loader thread streams each stage's block into
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
             uint32_t last_phase[2] = {0, 0};
             bool issued[2] = {false, false};
             for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
-                const int kr = (int)(item % a.n_kr);
+                const int kr = (int)(item / a.n_mt);
                 const int64_t x0 = (int64_t)kr * a.krange, x1 = min(a.npix, x0 + a.krange);
                 const int nst = (int)(((x1 > x0 ? x1 - x0 : (int64_t)0) + LT_KPX - 1) / LT_KPX);
                 for (int st = 0; st < nst; ++st, ++it) {
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
             const uint32_t idesc = umma_idesc(2, LT_N);
             uint32_t it = 0, nflush = 0;
             for (int64_t item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
-                const int kr = (int)(item % a.n_kr);
+                const int kr = (int)(item / a.n_mt);
                 const int64_t x0 = (int64_t)kr * a.krange, x1 = min(a.npix, x0 + a.krange);
                 const int nst = (int)(((x1 > x0 ? x1 - x0 : (int64_t)0) + LT_KPX - 1) / LT_KPX);
                 const int nfl = max(1, (nst + LT_FLUSH - 1) / LT_FLUSH);    // hand-offs (one even if empty)
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
         uint32_t it = 0;
         for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
             if (*abort_flag) break;
-            const int mt = (int)(item / a.n_kr), kr = (int)(item % a.n_kr);
+            const int mt = (int)(item % a.n_mt), kr = (int)(item / a.n_mt);
             const int64_t x0 = (int64_t)kr * a.krange, x1 = min(a.npix, x0 + a.krange);
             const int nst = (int)(((x1 > x0 ? x1 - x0 : (int64_t)0) + LT_KPX - 1) / LT_KPX);
             for (int st = 0; st < nst; ++st, ++it) {
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
         const int row = quarter * 32 + lane;                // TMEM lane = row within the tile
         uint32_t nflush = 0;
         for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-            const int mt = (int)(item / a.n_kr), kr = (int)(item % a.n_kr);
+            const int mt = (int)(item % a.n_mt), kr = (int)(item / a.n_mt);
             const int64_t x0 = (int64_t)kr * a.krange, x1 = min(a.npix, x0 + a.krange);
             const int nst = (int)(((x1 > x0 ? x1 - x0 : (int64_t)0) + LT_KPX - 1) / LT_KPX);
             const int nfl = max(1, (nst + LT_FLUSH - 1) / LT_FLUSH);
@@ -315,6 +317,13 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
     }
 }
 
+// One pixel range per SM: the n_mt * nsm items of equal size spread evenly over the nsm
+// persistent CTAs, n_mt each (the partial-sum buffer holds nsm ranges).
+int linear_tc_splits(const Plan& pl, int B) {
+    (void)B;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(pl.nsm, pl.npix / LT_KPX));
+}
+
 size_t linear_presplit_bytes(const Plan& pl) {
     return (size_t)((pl.npix + LT_KPX - 1) / LT_KPX) * 2 * LT_B_TILE;
 }
@@ -336,7 +345,7 @@ cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial
     a.n_pair = pl.n_pair;
     a.npix = pl.npix;
     a.n_mt = (a.ncols + 127) / 128;
-    a.n_kr = pl.lin_ksplit;
+    a.n_kr = linear_tc_splits(pl, B);
     a.krange = ((pl.npix + a.n_kr - 1) / a.n_kr + LT_KPX - 1) / LT_KPX * LT_KPX;
     a.bsplit = pl.lin_bsplit;
     a.maps = maps;

@@ -183,7 +183,7 @@ static modal_status alloc_workspace(modal_plan* pl, int chunk) {
     CK(dalloc(pl, &pl->vring, (size_t)chunk * pl->P * pl->nrings), "workspace vring");
     // cubic partials: [chunk][cubic_ctas][n_max]; linear partials: [ksplit][n_pair][chunk*P]
     const size_t cub = (size_t)chunk * pl->cubic_ctas * pl->n_max;
-    const size_t lin = (size_t)pl->lin_ksplit * pl->n_pair * chunk * pl->P;
+    const size_t lin = (size_t)std::max(pl->lin_ksplit, pl->nsm) * pl->n_pair * chunk * pl->P;
     pl->partial_elems = cub + lin;
     CK(dalloc(pl, &pl->partial, pl->partial_elems), "workspace partial");
     {
@@ -461,6 +461,8 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
         pl->cubic_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, 512));
         int64_t ks = pl->npix / 16384;
         pl->lin_ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(ks, 128));
+        cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, pl->dev);
+        pl->nsm = std::max(pl->nsm, 1);
     }
     // tensor-core tables
     if (prec != MODAL_FP32) CKI(build_tc_tables(*pl, 0), "tensor-core tables");
@@ -588,6 +590,7 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
                 CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm");
             } else {
                 CK(launch_linear_tc(*h, h->maps, nb, lin, st), "linear gemm");
+                splits = linear_tc_splits(*h, nb);
             }
         }
         { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, splits, beta + (size_t)b0 * h->n_max, st), "beta finalize"); }

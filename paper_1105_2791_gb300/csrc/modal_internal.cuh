@@ -112,7 +112,8 @@ struct Plan {
     double* partial = nullptr;   // cubic / linear partial sums
     size_t partial_elems = 0;
     int cubic_ctas = 0;          // CTAs per map in the cubic kernel
-    int lin_ksplit = 0;          // K splits in the linear-term GEMM
+    int lin_ksplit = 0;          // K splits in the linear-term GEMM (SIMT)
+    int nsm = 0;                 // SMs of the plan's device
     float* hk = nullptr;         // [chunk][P][n_pair] adjoint weights
     // ring-only linear term (modal_set_linear_mode)
     int lin_mode = 0;            // MODAL_LINEAR_PIXEL or MODAL_LINEAR_RING
@@ -179,6 +180,7 @@ cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cu
 cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);   // k_linear_tc.cu
 size_t linear_presplit_bytes(const Plan& pl);
+int linear_tc_splits(const Plan& pl, int B);   // K splits of the tensor-core linear term for B maps
 cudaError_t launch_linear_presplit(Plan& pl, cudaStream_t st);   // after each finalised pixel mean
 // lin_splits: K splits summed from lin_partial ([lin_splits][n_pair][B P])
 cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* cub_partial,
