@@ -157,9 +157,11 @@ STAGE_TRAFFIC_GB = {
 }
 
 
-def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps, peaks):
+def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps, peaks, nsynth=3):
     """Roofline of every timed stage: algorithmic work per step (flops or bytes) over the
-    stage's live CUDA-event time, against its peak; sorted by time, largest first."""
+    stage's live CUDA-event time, against its peak; sorted by time, largest first.
+    nsynth: syntheses per chunk (linear term, cubic, and the adjoint unless it reuses the
+    cubic's maps)."""
     R_half, L1, npix = (R + 1) // 2, L + 1, R * nphi
     n_alm = (L + 1) * (L + 2) // 2
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -172,15 +174,15 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
     map_bytes = chunk * P * npix * 4.0
     # stage: (bound, work per launch, launches per step, peak, unit)
     work = {
-        "legendre": ("tensor" if tensor_peak else "alu", legendre_flops(P, L, R) * chunk, 3 * launches),
+        "legendre": ("tensor" if tensor_peak else "alu", legendre_flops(P, L, R) * chunk, nsynth * launches),
         "legendre_adjoint": ("tensor" if tensor_peak else "alu", legendre_flops(P, L, R) * chunk, launches),
-        "ring_c2r": ("hbm", delta_bytes + map_bytes, 3 * launches),
+        "ring_c2r": ("hbm", delta_bytes + map_bytes, nsynth * launches),
         "ring_r2c": ("hbm", delta_bytes + map_bytes, launches),
         "adjoint_pixel": ("alu", 2.0 * P * n_pair * npix * chunk, launches),
         "cubic": ("alu", 2.0 * n_max * npix * chunk, launches),
         "linear_gemm": ("tensor" if tensor_peak else "alu", 2.0 * n_pair * P * npix * chunk, launches),
         "pair_means": ("hbm", map_bytes + 2.0 * n_pair * npix * 8, launches),
-        "legendre_prep": ("hbm", chunk * n_alm * 8.0 + chunk * P * 2 * n_alm * 2 * 2.0, 3 * launches),
+        "legendre_prep": ("hbm", chunk * n_alm * 8.0 + chunk * P * 2 * n_alm * 2 * 2.0, nsynth * launches),
         "legendre_adjoint_prep": ("hbm", 2.0 * delta_bytes, launches),
     }
     traffic = STAGE_TRAFFIC_GB.get((prec, L, nphi, P, chunk), {})
@@ -238,6 +240,10 @@ def run_gpu(args):
     lin_sims = torch.from_numpy(simgen.gaussian_alm(cl, 2, seed=4 + 1000 * rank,
                                                     stream=simgen.STREAM_LINEAR).astype(np.complex64)).to(dev)
 
+    # the adjoint differentiates the cubic call of the same step; when the batch fits one
+    # chunk the plan keeps that call's maps for it instead of synthesising them again
+    retain = B <= args.chunk
+
     def make_plan(prec):
         try:
             plan = M.Plan(L, P, basis, cl, R, nphi, prec=prec)
@@ -246,6 +252,7 @@ def run_gpu(args):
                 return None
             raise
         plan.set_chunk(min(args.chunk, B))
+        plan.set_retain_maps(retain)
         if args.linear == "ring":
             plan.set_linear_mode("ring")
         plan.linear_term(lin_sims, finalize=True)      # a mean to subtract from the first step on
@@ -282,14 +289,15 @@ def run_gpu(args):
         pl.linear_term(a)
         pl.cubic(a, use_linear=True, out=beta)
         pl.cov_accumulate(beta)
+        backward = pl.backward_retained if retain else pl.backward
         if not overlap:                                  # per-stage timing: one stream, stages in order
             fnl, sigma = pl.solve(alpha, beta)
-            pl.backward(a, g, use_linear=True, out=grad)
+            backward(a, g, use_linear=True, out=grad)
             return fnl, sigma
         # the FP64 solve (latency-bound, a few CTAs) runs on a side stream beside the adjoint
         ready = torch.cuda.Event()
         ready.record(torch.cuda.current_stream())
-        pl.backward(a, g, use_linear=True, out=grad)
+        backward(a, g, use_linear=True, out=grad)
         side.wait_event(ready)
         fnl, sigma = M.modal_solve(pl.h, alpha, beta, beta.shape[0], stream=side)
         return fnl, sigma
@@ -333,7 +341,7 @@ def run_gpu(args):
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     rooflines = stage_rooflines(prec, L, R, nphi, P, plan.n_max, plan.n_pair, min(B, args.chunk), B, prof,
-                                n_prof_steps, peaks)
+                                n_prof_steps, peaks, nsynth=2 if retain else 3)
     top = rooflines[0]
     roof = {k: top[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "peak_source")}
     if top["traffic"] is not None:
@@ -350,6 +358,7 @@ def run_gpu(args):
                        L, R, nphi, P, plan.n_max, B, prec),
                    "lmax": L, "nrings": R, "nphi": nphi, "P": P, "n_max": plan.n_max, "batch_per_gpu": B,
                    "precision": prec, "linear_means": args.linear,
+                   "adjoint_maps": "kept from the step's cubic call" if retain else "synthesised again",
                    "l2": "inputs and intermediates > L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk,

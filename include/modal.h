@@ -188,6 +188,23 @@ modal_status modal_bivector_rotate(modal_h h, const double* zeta0, const double*
 modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, int use_linear,
                             void* grad_alm, void* stream);
 
+/* Keep the filtered maps of each modal_cubic call whose batch fits one chunk (B <= chunk;
+ * no extra memory: they stay in the plan's map workspace), so that modal_backward_retained
+ * can differentiate that call without synthesising them again.  on: 0 (default) or 1. */
+modal_status modal_set_retain_maps(modal_h h, int on);
+
+/* modal_backward at the a_lm of the plan's last modal_cubic call, from the maps that call
+ * kept: the same result as modal_backward(h, alm, B, g, use_linear, grad_alm) without the
+ * synthesis.  alm and B must be the pointer and count given to that call (checked; the
+ * caller must not have changed the a_lm since), and the call must be ordered after it on
+ * the device (same stream, or an event).  B = 0 does nothing.  MODAL_ESTATE if no maps are
+ * kept for (alm, B): retention off, B > chunk, or a later call reused the map workspace
+ * (the synthesis of modal_linear_term, modal_cubic, modal_quartic or modal_backward;
+ * modal_set_chunk).  The adjoint overwrites the kept maps: a second call returns
+ * MODAL_ESTATE. */
+modal_status modal_backward_retained(modal_h h, const void* alm, int B, const double* g, int use_linear,
+                                     void* grad_alm, void* stream);
+
 /* alpha_prs per unit fNL for the local shape b = 2 (C1 C2 + C2 C3 + C3 C1) (Eq. abispect
  * with the first-order bispectrum of T = G + f (G^2 - <G^2>)), by exact Gauss-Legendre
  * integration of Legendre series (FP64, host).  C_signal: host [lmax+1] (the signal

@@ -32,6 +32,7 @@ EXPORTS = [
     "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
     "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
     "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate", "modal_quartic",
+    "modal_set_retain_maps", "modal_backward_retained",
 ]
 MODAL_NSTAGES = 15
 
@@ -84,6 +85,8 @@ def load_library():
         "modal_bivector_rotate": [H, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p],
         "modal_quartic": [H, c_void_p, c_int, c_int, c_void_p, c_void_p],
         "modal_backward": [H, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p],
+        "modal_backward_retained": [H, c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p],
+        "modal_set_retain_maps": [H, c_int],
         "modal_alpha_local": [H, c_void_p, c_void_p],
         "modal_get_info": [H, POINTER(modal_info)],
         "modal_get_rings": [H, c_void_p, c_void_p],
@@ -265,6 +268,15 @@ def modal_bivector_rotate(h, zeta0, bt, x, B, out, stream=None):
 def modal_backward(h, alm, B, g, use_linear, grad_alm, stream=None):
     _check(load_library().modal_backward(h, _dev(alm), int(B), _dev(g), int(bool(use_linear)), _dev(grad_alm),
                                          _stream(stream)))
+
+
+def modal_set_retain_maps(h, on):
+    _check(load_library().modal_set_retain_maps(h, int(bool(on))))
+
+
+def modal_backward_retained(h, alm, B, g, use_linear, grad_alm, stream=None):
+    _check(load_library().modal_backward_retained(h, _dev(alm), int(B), _dev(g), int(bool(use_linear)),
+                                                  _dev(grad_alm), _stream(stream)))
 
 
 def modal_alpha_local(h, C_signal=None):

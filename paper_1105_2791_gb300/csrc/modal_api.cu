@@ -177,6 +177,7 @@ static modal_status alloc_workspace(modal_plan* pl, int chunk) {
     const size_t before = pl->device_bytes;
     const size_t L1 = pl->lmax + 1;
     CK(dalloc(pl, &pl->delta, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace delta");
+    pl->kept_alm = nullptr;
     CK(dalloc(pl, &pl->maps, (size_t)chunk * pl->P * pl->npix), "workspace maps");
     CK(dalloc(pl, &pl->ut, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace ut");
     CK(dalloc(pl, &pl->hk, (size_t)chunk * pl->P * pl->n_pair), "workspace hk");
@@ -298,6 +299,7 @@ static cudaError_t legendre_forward(modal_plan* pl, const float2* alm, int B, cu
 }
 
 static cudaError_t synth_chunk(modal_plan* pl, const float2* alm, int B, float* maps_out, cudaStream_t st) {
+    if (maps_out == pl->maps) pl->kept_alm = nullptr;
     {
         cudaError_t e = legendre_forward(pl, alm, B, st);
         if (e != cudaSuccess) return e;
@@ -595,6 +597,17 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
         }
         { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, splits, beta + (size_t)b0 * h->n_max, st), "beta finalize"); }
     }
+    if (h->retain_maps && B > 0 && B <= h->chunk) {      // the whole batch is in the map workspace
+        h->kept_alm = alm;
+        h->kept_B = B;
+    }
+    return MODAL_OK;
+}
+
+modal_status modal_set_retain_maps(modal_h h, int on) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    h->retain_maps = on ? 1 : 0;
+    if (!on) h->kept_alm = nullptr;
     return MODAL_OK;
 }
 
@@ -835,20 +848,17 @@ modal_status modal_bivector_rotate(modal_h h, const double* zeta0, const double*
     return s;
 }
 
-modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, int use_linear, void* grad_alm,
-                            void* stream) {
-    if (check_plan(h)) return MODAL_EINVAL;
-    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
-    if (B > 0 && (!alm || !g || !grad_alm)) return set_error(MODAL_EINVAL, "null pointer");
-    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
-    cudaStream_t st = as_stream(stream);
+// kept: the maps of a (one chunk) are already in h->maps (modal_backward_retained)
+static modal_status backward_impl(modal_h h, const void* alm, int B, const double* g, int use_linear, void* grad_alm,
+                                  cudaStream_t st, bool kept) {
     const float2* a = static_cast<const float2*>(alm);
     float2* out = static_cast<float2*>(grad_alm);
     // ring mode: the pair-mean term is constant on each ring and enters only through m = 0
     const bool ring = use_linear && h->lin_mode == MODAL_LINEAR_RING;
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
-        CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "backward synthesis");
+        if (!kept) CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "backward synthesis");
+        h->kept_alm = nullptr;                              // U overwrites the maps
         { STAGE(h, ST_ADJ_PIXEL, st); CK(launch_adjoint_weights(*h, g + (size_t)b0 * h->n_max, nb, h->hk, st), "adjoint weights"); }
         {
             STAGE(h, ST_ADJ_PIXEL, st);
@@ -872,6 +882,28 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
         }
     }
     return MODAL_OK;
+}
+
+modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, int use_linear, void* grad_alm,
+                            void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && (!alm || !g || !grad_alm)) return set_error(MODAL_EINVAL, "null pointer");
+    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+    return backward_impl(h, alm, B, g, use_linear, grad_alm, as_stream(stream), false);
+}
+
+modal_status modal_backward_retained(modal_h h, const void* alm, int B, const double* g, int use_linear,
+                                     void* grad_alm, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B == 0) return MODAL_OK;
+    if (!alm || !g || !grad_alm) return set_error(MODAL_EINVAL, "null pointer");
+    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+    if (!h->kept_alm || h->kept_alm != alm || h->kept_B != B)
+        return set_error(MODAL_ESTATE, "no maps kept for this a_lm and batch (modal_set_retain_maps, B <= chunk, "
+                                       "no synthesis or adjoint since the modal_cubic call)");
+    return backward_impl(h, alm, B, g, use_linear, grad_alm, as_stream(stream), true);
 }
 
 modal_status modal_alpha_local(modal_h h, const double* C_signal, double* alpha) {

@@ -114,6 +114,10 @@ struct Plan {
     int cubic_ctas = 0;          // CTAs per map in the cubic kernel
     int lin_ksplit = 0;          // K splits in the linear-term GEMM (SIMT)
     int nsm = 0;                 // SMs of the plan's device
+    // maps of the last modal_cubic call kept in `maps` for modal_backward_retained
+    int retain_maps = 0;
+    const void* kept_alm = nullptr;   // a_lm they were synthesised from (nullptr: none kept)
+    int kept_B = 0;
     float* hk = nullptr;         // [chunk][P][n_pair] adjoint weights
     // ring-only linear term (modal_set_linear_mode)
     int lin_mode = 0;            // MODAL_LINEAR_PIXEL or MODAL_LINEAR_RING

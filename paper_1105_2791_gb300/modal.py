@@ -107,6 +107,19 @@ class Plan:
         B.modal_backward(self.h, alm, nb, g, use_linear, out)
         return out
 
+    def set_retain_maps(self, on=True):
+        """Keep the maps of each cubic() call of at most one chunk of maps for
+        backward_retained()."""
+        B.modal_set_retain_maps(self.h, on)
+
+    def backward_retained(self, alm, g, use_linear=False, out=None):
+        """backward() of the last cubic() call (same alm tensor), from the maps it kept."""
+        nb = alm.shape[0]
+        if out is None:
+            out = torch.empty((nb, self.n_alm), dtype=torch.complex64, device=alm.device)
+        B.modal_backward_retained(self.h, alm, nb, g, use_linear, out)
+        return out
+
     # -- host-side helpers and accumulators
     def alpha_local(self, C_signal=None):
         return B.modal_alpha_local(self.h, C_signal)
