@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=32, help="maps per internal pass of the library")
     ap.add_argument("--linear", choices=["pixel", "ring"], default="pixel",
                     help="Monte Carlo pair means per pixel (default) or per ring (axisymmetric weights)")
+    ap.add_argument("--adjoint", choices=["recompute", "kept"], default="recompute",
+                    help="adjoint maps: synthesised again (default) or kept from the step's cubic call")
     ap.add_argument("--workload", choices=["l2000", "mixed", "trispectrum"], default="l2000",
                     help="l2000: the headline step; mixed: the batched Monte Carlo coefficient pass over "
                          "l_max 500 / 1000 / 2000 maps (2:1:1, 512 per step) as one captured graph; "
@@ -240,9 +242,14 @@ def run_gpu(args):
     lin_sims = torch.from_numpy(simgen.gaussian_alm(cl, 2, seed=4 + 1000 * rank,
                                                     stream=simgen.STREAM_LINEAR).astype(np.complex64)).to(dev)
 
-    # the adjoint differentiates the cubic call of the same step; when the batch fits one
-    # chunk the plan keeps that call's maps for it instead of synthesising them again
-    retain = B <= args.chunk
+    # The adjoint differentiates the cubic call of the same step and synthesises its maps
+    # again (recomputation, not storage).  --adjoint kept reuses the maps that call left in
+    # the plan's workspace instead (modal_backward_retained; the batch must fit one chunk);
+    # the default run times that variant too, in a short extra pass reported beside.
+    kept_ok = B <= args.chunk
+    if args.adjoint == "kept" and not kept_ok:
+        raise SystemExit("--adjoint kept needs --batch <= --chunk")
+    retain = args.adjoint == "kept"
 
     def make_plan(prec):
         try:
@@ -252,7 +259,7 @@ def run_gpu(args):
                 return None
             raise
         plan.set_chunk(min(args.chunk, B))
-        plan.set_retain_maps(retain)
+        plan.set_retain_maps(kept_ok)
         if args.linear == "ring":
             plan.set_linear_mode("ring")
         plan.linear_term(lin_sims, finalize=True)      # a mean to subtract from the first step on
@@ -283,13 +290,13 @@ def run_gpu(args):
 
     side = torch.cuda.Stream(device=dev)
 
-    def step(pl, a, e2e=False, overlap=True):
+    def step(pl, a, e2e=False, overlap=True, kept=None):
         if e2e:
             a.copy_(alm_pinned, non_blocking=True)
         pl.linear_term(a)
         pl.cubic(a, use_linear=True, out=beta)
         pl.cov_accumulate(beta)
-        backward = pl.backward_retained if retain else pl.backward
+        backward = pl.backward_retained if (retain if kept is None else kept) else pl.backward
         if not overlap:                                  # per-stage timing: one stream, stages in order
             fnl, sigma = pl.solve(alpha, beta)
             backward(a, g, use_linear=True, out=grad)
@@ -302,9 +309,9 @@ def run_gpu(args):
         fnl, sigma = M.modal_solve(pl.h, alpha, beta, beta.shape[0], stream=side)
         return fnl, sigma
 
-    def timed(pl, a, steps, warmup, e2e=False, profile=False):
+    def timed(pl, a, steps, warmup, e2e=False, profile=False, kept=None):
         for _ in range(warmup):
-            step(pl, a, e2e, overlap=not profile)
+            step(pl, a, e2e, overlap=not profile, kept=kept)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -315,7 +322,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         ev0.record(st)
         for _ in range(steps):
-            step(pl, a, e2e, overlap=not profile)
+            step(pl, a, e2e, overlap=not profile, kept=kept)
         ev1.record(st)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
@@ -334,6 +341,13 @@ def run_gpu(args):
     # end to end through the public API from pinned host memory
     a_e2e = torch.empty_like(alm)
     e2e_ms, _ = timed(plan, a_e2e, K, 1, e2e=True)
+    # the same step with the adjoint on the cubic call's kept maps (or, under --adjoint kept,
+    # with the maps synthesised again), device-timed
+    other = None
+    if kept_ok:
+        oms, _ = timed(plan, alm, K, 1, kept=not retain)
+        other = {"adjoint_maps": "synthesised again" if retain else "kept from the step's cubic call",
+                 "value": round(job_throughput(B, K, world, oms), 3), "ms_per_step": round(oms / K, 3)}
 
     value = job_throughput(B, K, world, ms)
     e2e_value = job_throughput(B, K, world, e2e_ms)
@@ -367,6 +381,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(alm.numel() * 8), "d2h_bytes_per_step": int(B * 8 + 8)},
         "roofline": roof,
         "rooflines": rooflines,
+        "other_adjoint": other,
         "stage_ms_per_step": {k: round(v[0] / n_prof_steps, 3) for k, v in prof.items() if v[1]},
     }
 
