@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(256) k_tc_prep_b(PrepArgs a) {
     __shared__ float2 s_a[TC_MAPS * 64];
     __shared__ float s_f[64 * 16];
     __shared__ float s_scale[TC_MAPS];
+    __shared__ int s_dec[16 * 16];                              // per column n: (map row of s_a, p, Re/Im)
     const int N = 16 * a.P;
     const int b_tile = N * TC_KB;
     const int m = blockIdx.y >> 1, pi = blockIdx.y & 1, g = blockIdx.z;
@@ -123,6 +124,12 @@ __global__ void __launch_bounds__(256) k_tc_prep_b(PrepArgs a) {
         const int b = g * TC_MAPS + threadIdx.x;
         s_scale[threadIdx.x] = (b < a.B) ? exp2f((float)tc_scale_exp(a.amax[b])) : 0.f;
     }
+    // column n = (map bl, p, Re/Im) = 2 (bl P + p) + comp, decoded once per CTA
+    for (int n = threadIdx.x; n < N; n += blockDim.x)
+        s_dec[n] = ((n / (2 * a.P)) * KPS) << 16 | ((n / 2) % a.P) << 1 | (n & 1);
+    // this thread's first (chunk column, n) and its stride over c = kc N + n, divided once
+    const int kc0 = threadIdx.x / N, n0 = threadIdx.x % N;
+    const int dkc = blockDim.x / N, dn = blockDim.x % N;
     for (int kb = blockIdx.x; kb < nkb; kb += gridDim.x) {
         const int l0 = m + pi + 2 * kb * KPS;                   // l of K index k: l0 + 2 k
         __syncthreads();
@@ -143,20 +150,26 @@ __global__ void __launch_bounds__(256) k_tc_prep_b(PrepArgs a) {
         }
         __syncthreads();
         char* bt = a.out + ((int64_t)g * a.total_bkb + a.bblk_base[2 * m + pi] + kb) * (int64_t)(2 * b_tile);
-        for (int c = threadIdx.x; c < NKC * N; c += blockDim.x) {
-            const int kc = c / N, n = c % N;
-            const int bl = n / (2 * a.P), p = (n / 2) % a.P, comp = n % 2;
+        for (int kc = kc0, n = n0; kc < NKC;) {
+            const int dec = s_dec[n];
+            const int arow = dec >> 16, p = (dec >> 1) & 0x7fff, comp = dec & 1;
             T hv[CM], lv[CM];
 #pragma unroll
             for (int i = 0; i < CM; ++i) {
                 const int k = kc * CM + i;
-                const float2 av = s_a[bl * KPS + k];
+                const float2 av = s_a[arow + k];
                 const float x = s_f[k * 16 + p] * (comp ? av.y : av.x);
                 S::split(x, hv[i], lv[i]);
             }
-            const int off = (n / 8) * TC_SBO + kc * 128 + (n % 8) * 16;
+            const int off = (n >> 3) * TC_SBO + kc * 128 + (n & 7) * 16;
             *reinterpret_cast<uint4*>(bt + off) = *reinterpret_cast<const uint4*>(hv);
             *reinterpret_cast<uint4*>(bt + b_tile + off) = *reinterpret_cast<const uint4*>(lv);
+            kc += dkc;
+            n += dn;
+            if (n >= N) {
+                n -= N;
+                ++kc;
+            }
         }
     }
 }
