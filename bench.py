@@ -11,8 +11,9 @@ shifted-Legendre modes (n_max = 816), C_l = 1/(l(l+1)), synthetic Gaussian a_lm
 (seeded Philox).  All buffers are far larger than L2 (129 MB), so no flush is needed.
 
 `value` is device-timed maps/s with inputs resident; `e2e` times the same step through
-the public API with a_lm copied from pinned host memory every step and the fNL values
-returned to the host.  `--impl reference` times the FP64 CPU oracle on a bounded
+the public API with a_lm copied from pinned host memory every step (on a copy stream,
+double-buffered, so that the next step's copy overlaps this step's kernels) and the fNL
+values returned to the host.  `--impl reference` times the FP64 CPU oracle on a bounded
 sample of the same workload.
 """
 from __future__ import annotations
@@ -290,9 +291,7 @@ def run_gpu(args):
 
     side = torch.cuda.Stream(device=dev)
 
-    def step(pl, a, e2e=False, overlap=True, kept=None):
-        if e2e:
-            a.copy_(alm_pinned, non_blocking=True)
+    def step(pl, a, overlap=True, kept=None):
         pl.linear_term(a)
         pl.cubic(a, use_linear=True, out=beta)
         pl.cov_accumulate(beta)
@@ -309,9 +308,41 @@ def run_gpu(args):
         fnl, sigma = M.modal_solve(pl.h, alpha, beta, beta.shape[0], stream=side)
         return fnl, sigma
 
+    copy_stream = torch.cuda.Stream(device=dev)
+
+    def run_steps(pl, a, n, e2e, profile, kept):
+        """n steps on the current stream.  e2e: every step's a_lm is copied in from pinned
+        host memory on a copy stream into one of two device buffers, so that the copy for
+        step i + 1 runs beside the kernels of step i; the kernels of a step wait for its copy,
+        and a copy waits until the step that last used its buffer is done."""
+        cur = torch.cuda.current_stream()
+        if not e2e:
+            for _ in range(n):
+                step(pl, a, overlap=not profile, kept=kept)
+            return
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        free = [torch.cuda.Event(), torch.cuda.Event()]
+        for ev in free:
+            ev.record(cur)
+
+        def issue_copy(i):
+            j = i % 2
+            copy_stream.wait_event(free[j])
+            with torch.cuda.stream(copy_stream):
+                a[j].copy_(alm_pinned, non_blocking=True)
+            copied[j].record(copy_stream)
+
+        if n > 0:
+            issue_copy(0)
+        for i in range(n):
+            if i + 1 < n:
+                issue_copy(i + 1)
+            cur.wait_event(copied[i % 2])
+            step(pl, a[i % 2], overlap=not profile, kept=kept)
+            free[i % 2].record(cur)
+
     def timed(pl, a, steps, warmup, e2e=False, profile=False, kept=None):
-        for _ in range(warmup):
-            step(pl, a, e2e, overlap=not profile, kept=kept)
+        run_steps(pl, a, warmup, e2e, profile, kept)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -321,8 +352,7 @@ def run_gpu(args):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         ev0.record(st)
-        for _ in range(steps):
-            step(pl, a, e2e, overlap=not profile, kept=kept)
+        run_steps(pl, a, steps, e2e, profile, kept)
         ev1.record(st)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
@@ -339,7 +369,7 @@ def run_gpu(args):
     _, prof = timed(plan, alm, max(1, K // 2), 1, profile=True)
     launches = sum(n for (_, n) in prof_plain_timing.values())
     # end to end through the public API from pinned host memory
-    a_e2e = torch.empty_like(alm)
+    a_e2e = [torch.empty_like(alm), torch.empty_like(alm)]
     e2e_ms, _ = timed(plan, a_e2e, K, 1, e2e=True)
     # the same step with the adjoint on the cubic call's kept maps (or, under --adjoint kept,
     # with the maps synthesised again), device-timed
