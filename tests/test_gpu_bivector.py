@@ -107,7 +107,7 @@ def test_bivector_from_few_sims_recovers_most_of_the_direct_weighting():
     """Sec. III.B's claim on a 500-ring masked sky with sigma^2(theta) noise (P = 6, 56 modes):
     with zeta0 = f_sky x the full-sky closed form, the whitened covariance has one dominant
     direction, and a bivector fitted on 500 sims weights f_NL nearly as well as the direct
-    zeta from 4000 sims, far better than zeta0 alone.  Judged by the empirical scatter of
+    zeta from 4000 sims, far better than zeta0 alone.  Measured by the empirical scatter of
     f_NL over 1000 independent Gaussian maps (seeded CUDA normals)."""
     import math
     from oracle import sht as osh
