@@ -122,8 +122,6 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
 modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, double* beta,
                          void* stream);
 
-/* Covariance sums over simulations (Eq. linearterm): S1 += sum_b beta_b,
- * S2 += sum_b beta_b beta_b^T (FP64).  dev beta [B][n_max]. */
 /* Trispectrum modal coefficients (Sec. IV: the B term of the quartic estimator with the
  * four-harmonic Gaunt integral, separable modes q_p q_r q_s q_u, v_l = 1), on the plan's
  * grid:  tau_prsu = sum_x W_x [M_p M_r M_s M_u - sum over the 6 single pairs <ab> M_c M_d
@@ -136,6 +134,8 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
  * call allocates the quartic tables and buffers (about chunk x 0.5 MB x cubic CTAs). */
 modal_status modal_quartic(modal_h h, const void* alm, int B, int use_linear, double* tau, void* stream);
 
+/* Covariance sums over simulations (Eq. linearterm): S1 += sum_b beta_b,
+ * S2 += sum_b beta_b beta_b^T (FP64).  dev beta [B][n_max]. */
 modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* stream);
 
 /* Estimator (Eq. modalest, Eq. modalvariance, Eq. Cholrot): zeta = sample covariance
