@@ -13,8 +13,9 @@ shifted-Legendre modes (n_max = 816), C_l = 1/(l(l+1)), synthetic Gaussian a_lm
 `value` is device-timed maps/s with inputs resident; `e2e` times the same step through
 the public API with a_lm copied from pinned host memory every step (on a copy stream,
 double-buffered, so that the next step's copy overlaps this step's kernels) and the fNL
-values returned to the host.  `--impl reference` times the FP64 CPU oracle on a bounded
-sample of the same workload.
+values returned to the host.  `cpu_baseline` times the FP64 CPU oracle on a bounded sample of
+the workload, and `parity` compares the GPU's beta on that sample with the oracle's.
+`--impl reference` times the oracle alone.
 """
 from __future__ import annotations
 
@@ -425,7 +426,7 @@ def run_gpu(args):
         result["speedup_vs_plain_fp32"] = round(value / world / result["plain_fp32_value"], 3)
         plain.close()
     if rank == 0 and not args.no_baseline:
-        result["cpu_baseline"] = cpu_baseline(args.cpu_rings)
+        result["cpu_baseline"], result["parity"] = cpu_baseline(args.cpu_rings, prec)
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
@@ -437,7 +438,8 @@ def run_gpu(args):
 def oracle_step_sample(nring_sample, seed=3):
     """One map of the workload through the oracle's per-map step (synthesis, pair means,
     cubic with the linear term, adjoint) on `nring_sample` rings spread pole to equator;
-    returns (seconds, extrapolated seconds per map)."""
+    returns (seconds, extrapolated seconds per map, rings, sample) where sample holds the
+    map's a_lm (complex64 values), the rings and the oracle's maps on them."""
     import simgen
     from oracle import modal as om, sht as osh
 
@@ -445,7 +447,8 @@ def oracle_step_sample(nring_sample, seed=3):
     basis = simgen.shifted_legendre_basis(L, P)
     cl = simgen.cl_model(L)
     filt = osh.filter_table(basis, cl)
-    a = simgen.gaussian_alm(cl, 1, seed=seed)[0]
+    a32 = simgen.gaussian_alm(cl, 1, seed=seed).astype(np.complex64)
+    a = a32[0].astype(np.complex128)
     mu, w = osh.gl_nodes(R)
     rings = np.unique(np.linspace(0, R // 2, nring_sample).astype(int))
     t0 = time.perf_counter()
@@ -455,14 +458,56 @@ def oracle_step_sample(nring_sample, seed=3):
     g = np.ones(beta.size) / beta.size
     om.adjoint_grad(a, g, L, filt, mu[rings], w[rings], nphi, None, pm)
     dt = time.perf_counter() - t0
-    return dt, dt * R / len(rings), len(rings)
+    return dt, dt * R / len(rings), len(rings), {"alm": a32, "rings": rings, "maps": maps, "basis": basis, "cl": cl,
+                                                 "filt": filt, "mu": mu, "w": w}
 
 
-def cpu_baseline(nring_sample):
-    dt, per_map, k = oracle_step_sample(nring_sample)
-    return {"value": round(1.0 / per_map, 8), "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
+def gpu_beta_error(prec, sample, seed=4):
+    """beta with the linear term of the oracle sample's map on the GPU, restricted by a ring
+    mask to the sampled rings, against the oracle's on the same rings; the pair means come
+    from one independent simulation, synthesised by each side.  Returns
+    ||beta_gpu - beta_oracle||_2 / ||beta_oracle||_2."""
+    import torch
+    import simgen
+    import paper_1105_2791_gb300 as M
+    from oracle import modal as om, sht as osh
+
+    L, R, nphi, P = WORKLOAD["lmax"], WORKLOAD["nrings"], WORKLOAD["nphi"], WORKLOAD["P"]
+    rings = sample["rings"]
+    sim = simgen.gaussian_alm(sample["cl"], 1, seed=seed, stream=simgen.STREAM_LINEAR).astype(np.complex64)
+    sim_maps = osh.synthesize(sim[0].astype(np.complex128), L, sample["filt"], sample["mu"][rings], nphi)
+    ref = om.cubic_beta(sample["maps"], om.pixel_weights(sample["w"][rings], nphi), om.pair_means([sim_maps]))
+    mask = np.zeros(R)
+    mask[rings] = 1.0
+    plan = M.Plan(L, P, sample["basis"], sample["cl"], R, nphi, prec=prec, ring_mask=mask)
+    try:
+        plan.set_chunk(1)
+        plan.linear_term(torch.from_numpy(sim).cuda(), finalize=True)
+        beta = plan.cubic(torch.from_numpy(sample["alm"]).cuda(), use_linear=True).cpu().numpy()[0]
+        plan.sync()
+    finally:
+        plan.close()
+    return float(np.linalg.norm(beta - ref) / np.linalg.norm(ref))
+
+
+def cpu_baseline(nring_sample, prec=None):
+    """The oracle timed on a bounded sample; with prec, also the GPU's beta on that sample
+    against the oracle's (the accepted error metric, tolerance 1e-5)."""
+    dt, per_map, k, sample = oracle_step_sample(nring_sample)
+    base = {"value": round(1.0 / per_map, 8), "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": "1 map at lmax=2000 (P=16, 4096 longitudes) on %d of 2001 rings: synthesis, pair means, "
                       "cubic with linear term, adjoint; %.1f s, extrapolated by ring count" % (k, dt)}
+    if prec is None:
+        return base, None
+    parity = {"metric": "||beta_gpu - beta_oracle||_2 / ||beta_oracle||_2", "tol": 1e-5, "precision": prec,
+              "sample": "the oracle sample's map on its %d rings (ring-masked plan), linear term from one "
+                        "independent simulation" % k}
+    try:
+        err = gpu_beta_error(prec, sample)
+        parity.update(beta_rel_err=float("%.3g" % err), ok=bool(err <= 1e-5))
+    except Exception as e:          # the measurement line is printed whatever happens here
+        parity.update(error=str(e)[:200])
+    return base, parity
 
 
 def run_mixed(args):
@@ -671,7 +716,7 @@ def run_reference(args):
         oracle_step_sample(2)
     total, per_maps = 0.0, []
     for _ in range(args.steps):
-        dt, per_map, k = oracle_step_sample(args.cpu_rings)
+        dt, per_map, k, _ = oracle_step_sample(args.cpu_rings)
         total += dt
         per_maps.append(per_map)
     per_map = float(np.mean(per_maps))
