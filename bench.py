@@ -424,6 +424,15 @@ def run_gpu(args):
         pms, _ = timed(plain, alm, max(1, K // 2), 1)
         result["plain_fp32_value"] = round(B * max(1, K // 2) / (pms / 1e3), 3)
         result["speedup_vs_plain_fp32"] = round(value / world / result["plain_fp32_value"], 3)
+        # the metric's comparator proper: the plain FP32 path one map per launch (the adjoint
+        # synthesising its maps again, as in the default step)
+        try:
+            plain.set_chunk(1)
+            oms, _ = timed(plain, alm, max(1, K // 2), 1, kept=False)
+            result["plain_one_map_value"] = round(B * max(1, K // 2) / (oms / 1e3), 3)
+            result["speedup_vs_plain_one_map"] = round(value / world / result["plain_one_map_value"], 3)
+        except Exception as e:       # the measurement line is printed whatever happens here
+            result["plain_one_map_error"] = str(e)[:200]
         plain.close()
     if rank == 0 and not args.no_baseline:
         result["cpu_baseline"], result["parity"] = cpu_baseline(args.cpu_rings, prec)
