@@ -235,7 +235,11 @@ modal_status modal_set_linear_mode(modal_h h, int mode);
 modal_status modal_get_zeta(modal_h h, double* zeta);
 /* Clear accumulators: what & 1 -> linear-term sums, what & 2 -> covariance sums. */
 modal_status modal_reset(modal_h h, int what);
-/* Maps per internal pass (workspace is sized by it); reallocates.  Synchronises. */
+/* Maps per internal pass (workspace is sized by it); reallocates.  Synchronises.
+ * chunk in [1, 4096], else MODAL_EINVAL.  If the new workspace cannot be allocated the
+ * call returns MODAL_ENOMEM with the previous chunk restored; if even that fails, the
+ * plan has no workspace and the calls that run maps through it return MODAL_ESTATE
+ * until a modal_set_chunk succeeds. */
 modal_status modal_set_chunk(modal_h h, int chunk);
 /* Synchronise `stream`, then report asynchronous faults (MODAL_ECUDA) or a device
  * wait that gave up (MODAL_ETIMEOUT, with the flag cleared). */

@@ -171,13 +171,9 @@ static void free_workspace(modal_plan* pl) {
     pl->workspace_bytes = 0;
 }
 
-static modal_status alloc_workspace(modal_plan* pl, int chunk) {
-    free_workspace(pl);
-    pl->chunk = chunk;
-    const size_t before = pl->device_bytes;
+static modal_status alloc_workspace_buffers(modal_plan* pl, int chunk) {
     const size_t L1 = pl->lmax + 1;
     CK(dalloc(pl, &pl->delta, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace delta");
-    pl->kept_alm = nullptr;
     CK(dalloc(pl, &pl->maps, (size_t)chunk * pl->P * pl->npix), "workspace maps");
     CK(dalloc(pl, &pl->ut, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace ut");
     CK(dalloc(pl, &pl->hk, (size_t)chunk * pl->P * pl->n_pair), "workspace hk");
@@ -196,8 +192,26 @@ static modal_status alloc_workspace(modal_plan* pl, int chunk) {
         CK(dalloc(pl, &q, tc_adj_workspace_bytes(*pl, chunk)), "workspace tensor-core adjoint operands");
         pl->tca.bops = q;
     }
-    pl->workspace_bytes = pl->device_bytes - before;
     return MODAL_OK;
+}
+
+// The per-pass buffers for `chunk` maps.  On failure the buffers allocated so far stay
+// attached (and counted) until the next free_workspace.
+static modal_status alloc_workspace(modal_plan* pl, int chunk) {
+    free_workspace(pl);
+    pl->chunk = chunk;
+    pl->kept_alm = nullptr;
+    const size_t before = pl->device_bytes;
+    const modal_status s = alloc_workspace_buffers(pl, chunk);
+    pl->workspace_bytes = pl->device_bytes - before;
+    return s;
+}
+
+// Calls that run maps through the plan need its workspace; a failed modal_set_chunk that
+// could not restore the previous one leaves none (chunk 0).
+static modal_status check_workspace(modal_h h) {
+    if (h->chunk >= 1) return MODAL_OK;
+    return set_error(MODAL_ESTATE, "the plan has no workspace (a modal_set_chunk failed); call modal_set_chunk");
 }
 
 static modal_status ensure_pair_buffers(modal_plan* pl) {
@@ -499,11 +513,19 @@ modal_status modal_set_chunk(modal_h h, int chunk) {
     if (check_plan(h)) return MODAL_EINVAL;
     if (chunk < 1 || chunk > 4096) return set_error(MODAL_EINVAL, "chunk must be in [1, 4096]");
     CK(cudaDeviceSynchronize(), "set_chunk sync");
-    return alloc_workspace(h, chunk);
+    const int old = h->chunk;
+    const modal_status s = alloc_workspace(h, chunk);
+    if (s == MODAL_OK) return MODAL_OK;
+    const std::string why = modal_last_error();
+    if (old >= 1 && alloc_workspace(h, old) == MODAL_OK) return set_error(s, why + " (the previous chunk is kept)");
+    free_workspace(h);
+    h->chunk = 0;
+    return set_error(s, why + " (the plan has no workspace until modal_set_chunk succeeds)");
 }
 
 modal_status modal_synthesize(modal_h h, const void* alm, int B, float* maps, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B > 0 && (!alm || !maps)) return set_error(MODAL_EINVAL, "null pointer");
     cudaStream_t st = as_stream(stream);
@@ -517,6 +539,7 @@ modal_status modal_synthesize(modal_h h, const void* alm, int B, float* maps, vo
 
 modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B > 0 && (!alm || !maps)) return set_error(MODAL_EINVAL, "null pointer");
     cudaStream_t st = as_stream(stream);
@@ -541,6 +564,7 @@ static modal_status refresh_linear_presplit(modal_plan* h, cudaStream_t st) {
 
 modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int finalize, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B > 0 && !alm_sims) return set_error(MODAL_EINVAL, "null pointer");
     const bool ring = h->lin_mode == MODAL_LINEAR_RING;
@@ -570,6 +594,7 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
 
 modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, double* beta, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B > 0 && (!alm || !beta)) return set_error(MODAL_EINVAL, "null pointer");
     if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
@@ -634,6 +659,7 @@ static modal_status ensure_quartic(modal_plan* h) {
 
 modal_status modal_quartic(modal_h h, const void* alm, int B, int use_linear, double* tau, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B > 0 && (!alm || !tau)) return set_error(MODAL_EINVAL, "null pointer");
     if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "Monte Carlo terms requested before modal_linear_term(finalize)");
@@ -887,6 +913,7 @@ static modal_status backward_impl(modal_h h, const void* alm, int B, const doubl
 modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, int use_linear, void* grad_alm,
                             void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B > 0 && (!alm || !g || !grad_alm)) return set_error(MODAL_EINVAL, "null pointer");
     if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
@@ -896,6 +923,7 @@ modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, 
 modal_status modal_backward_retained(modal_h h, const void* alm, int B, const double* g, int use_linear,
                                      void* grad_alm, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
     if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
     if (B == 0) return MODAL_OK;
     if (!alm || !g || !grad_alm) return set_error(MODAL_EINVAL, "null pointer");
