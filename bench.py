@@ -416,7 +416,9 @@ def run_gpu(args):
         "stage_ms_per_step": {k: round(v[0] / n_prof_steps, 3) for k, v in prof.items() if v[1]},
     }
 
-    if rank == 0 and not args.no_baseline and prec != "fp32":
+    # the plain comparators time through the same barrier / max-over-ranks path, so they run
+    # only in single-process runs (under torchrun rank 0 would wait on ranks that have left)
+    if rank == 0 and world == 1 and not args.no_baseline and prec != "fp32":
         plan.close()
         plain = make_plan("fp32")
         plain.cov_accumulate(torch.randn((2 * plain.n_max, plain.n_max), generator=gen, device=dev,
@@ -434,7 +436,7 @@ def run_gpu(args):
         except Exception as e:       # the measurement line is printed whatever happens here
             result["plain_one_map_error"] = str(e)[:200]
         plain.close()
-    if rank == 0 and not args.no_baseline:
+    if rank == 0 and world == 1 and not args.no_baseline:
         result["cpu_baseline"], result["parity"] = cpu_baseline(args.cpu_rings, prec)
     if rank == 0:
         print(json.dumps(result))
@@ -686,7 +688,7 @@ def run_trispectrum(args):
         "roofline": roof,
         "stage_ms_per_step": {k: round(v[0] / n_prof, 3) for k, v in prof.items() if v[1]},
     }
-    if rank == 0 and not args.no_baseline:
+    if rank == 0 and world == 1 and not args.no_baseline:
         result["cpu_baseline"] = cpu_baseline_trispectrum(args.cpu_rings)
     if rank == 0:
         print(json.dumps(result))
