@@ -292,10 +292,14 @@ const char* modal_stage_name(int stage);
  *     beta[i] = dev double [B[i]][n_max_i] exactly as modal_cubic; alm, B and beta are
  *     host arrays of nplans entries.  With use_graph != 0 the launches are captured into
  *     one CUDA graph on the first call and the graph is replayed by later calls with the
- *     same pointers, counts and use_linear (new contents of the same buffers are read);
- *     any change re-captures it.  Kernels replayed from a graph are not counted by
+ *     same pointers, counts and use_linear (new contents of the same buffers are read)
+ *     while no member plan has changed state since the capture; a different argument, or
+ *     a plan changed by modal_set_chunk, modal_set_linear_mode, modal_set_retain_maps,
+ *     modal_reset, modal_load_state or the first allocation of its linear-term buffers,
+ *     re-captures it.  Kernels replayed from a graph are not counted by
  *     modal_get_profile, and plan profiling is suspended while a graph is captured.
- *     Errors: as modal_cubic for each plan; MODAL_ECUDA if capture or replay fails. */
+ *     Errors: as modal_cubic for each plan (MODAL_ESTATE for a plan without workspace);
+ *     MODAL_ECUDA if capture or replay fails. */
 typedef struct modal_batch* modal_batch_h;
 modal_status modal_batch_create(const modal_h* plans, int nplans, modal_batch_h* out);
 modal_status modal_batch_cubic(modal_batch_h bh, const void* const* alm, const int* B, int use_linear,

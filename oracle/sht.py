@@ -222,3 +222,43 @@ def analyze(maps: np.ndarray, lmax: int, mu, w, nphi: int) -> np.ndarray:
     """
     Tm = (2.0 * np.pi / nphi) * fourier_analysis(maps, lmax, nphi)
     return legendre_analysis(Tm, lmax, mu, w)
+
+
+def legendre_sums_many(alms: np.ndarray, lmax: int, filt: np.ndarray, mu) -> np.ndarray:
+    """legendre_sums for several maps, the lambda table of each ring block formed once:
+    complex [nmaps][P][lmax+1][len(mu)]."""
+    mu = np.atleast_1d(np.asarray(mu, dtype=float))
+    filt = np.atleast_2d(filt)
+    alms = np.atleast_2d(alms)
+    D = np.zeros((alms.shape[0], filt.shape[0], lmax + 1, mu.size), dtype=np.complex128)
+    for blk in ring_blocks(mu.size):
+        lam = legendre_table(lmax, mu[blk])
+        for m in range(lmax + 1):
+            start = m * (2 * lmax + 3 - m) // 2
+            lam_m = lam[start: start + lmax - m + 1]
+            for i in range(alms.shape[0]):
+                coef = filt[:, m:] * _alm_m(alms[i], lmax, m)[None, :]
+                D[i, :, m, blk] = coef @ lam_m
+    return D
+
+
+def synthesize_many(alms: np.ndarray, lmax: int, filt: np.ndarray, mu, nphi: int) -> np.ndarray:
+    """synthesize for several maps: [nmaps][P][len(mu)][nphi]."""
+    D = legendre_sums_many(alms, lmax, filt, mu)
+    return np.stack([fourier_synthesis(D[i], nphi) for i in range(D.shape[0])])
+
+
+def analyze_many(maps: np.ndarray, lmax: int, mu, w, nphi: int) -> np.ndarray:
+    """analyze for several maps [nmaps][nrings][nphi], the lambda table of each ring block
+    formed once: complex [nmaps][n_alm]."""
+    maps = np.asarray(maps)
+    mu = np.atleast_1d(np.asarray(mu, dtype=float))
+    Tm = (2.0 * np.pi / nphi) * fourier_analysis(maps, lmax, nphi)       # [map][ring][m]
+    out = np.zeros((maps.shape[0], (lmax + 1) * (lmax + 2) // 2), dtype=np.complex128)
+    for blk in ring_blocks(mu.size):
+        lam = legendre_table(lmax, mu[blk])
+        wt = (np.asarray(w)[blk])[None, :, None] * Tm[:, blk]         # [map][ring][m]
+        for m in range(lmax + 1):
+            start = m * (2 * lmax + 3 - m) // 2
+            out[:, start: start + lmax - m + 1] += (lam[start: start + lmax - m + 1] @ wt[:, :, m].T).T
+    return out

@@ -353,9 +353,26 @@ def modal_stage_name(stage):
 
 
 def modal_cubic_static(maps, W, npix, P, B, beta, stream=None):
-    """Allocation-free cubic coefficients of caller-held maps (see include/modal.h)."""
-    _check(load_library().modal_cubic_static(_dev(maps), _dev(W), int(npix), int(P), int(B), _dev(beta),
-                                             _stream(stream)))
+    """Allocation-free cubic coefficients of caller-held maps (see include/modal.h).
+
+    Tensors are checked before the call (the library sees raw pointers only): maps float32
+    with at least B * P * npix elements, W float32 with at least npix, beta float64 with at
+    least B * n_max, all contiguous on the current CUDA device."""
+    import torch
+    npix, P, B = int(npix), int(P), int(B)
+    n_max = P * (P + 1) * (P + 2) // 6
+    dev = torch.cuda.current_device()
+    for name, t, dtype, need in (("maps", maps, torch.float32, B * P * npix), ("W", W, torch.float32, npix),
+                                 ("beta", beta, torch.float64, B * n_max)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError("%s must be on the current CUDA device (cuda:%d)" % (name, dev))
+        if t.dtype != dtype:
+            raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+        if t.numel() < need:
+            raise ValueError("%s holds %d elements, the call reads or writes %d" % (name, t.numel(), need))
+    _check(load_library().modal_cubic_static(_dev(maps), _dev(W), npix, P, B, _dev(beta), _stream(stream)))
 
 
 def modal_destroy(h):

@@ -157,8 +157,7 @@ static size_t per_map_workspace(const modal_plan* pl) {
 }
 
 static void free_workspace(modal_plan* pl) {
-    size_t freed = 0;
-    (void)freed;
+    ++pl->generation;
     dfree(pl->delta); pl->delta = nullptr;
     dfree(pl->maps); pl->maps = nullptr;
     dfree(pl->ut); pl->ut = nullptr;
@@ -216,6 +215,7 @@ static modal_status check_workspace(modal_h h) {
 
 static modal_status ensure_pair_buffers(modal_plan* pl) {
     if (pl->pair_sum) return MODAL_OK;
+    ++pl->generation;
     const size_t n = (size_t)pl->n_pair * pl->npix;
     CK(dalloc(pl, &pl->pair_sum, n), "pair sums");
     CK(dalloc(pl, &pl->pair_mean, n), "pair mean");
@@ -226,6 +226,7 @@ static modal_status ensure_pair_buffers(modal_plan* pl) {
 
 static modal_status ensure_ring_buffers(modal_plan* pl) {
     if (pl->ring_sum) return MODAL_OK;
+    ++pl->generation;
     const size_t n = (size_t)pl->n_pair * pl->nrings;
     CK(dalloc(pl, &pl->ring_sum, n), "ring pair sums");
     CK(dalloc(pl, &pl->ring_mean, n), "ring pair means");
@@ -506,6 +507,7 @@ modal_status modal_set_linear_mode(modal_h h, int mode) {
     const modal_status r = modal_reset(h, 1);
     if (r != MODAL_OK) return r;
     h->lin_mode = mode;
+    ++h->generation;
     return MODAL_OK;
 }
 
@@ -557,7 +559,10 @@ modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void*
 // the per-pixel mean is finalised.
 static modal_status refresh_linear_presplit(modal_plan* h, cudaStream_t st) {
     if (h->prec == MODAL_FP32 || h->lin_mode == MODAL_LINEAR_RING) return MODAL_OK;
-    if (!h->lin_bsplit) CK(dalloc(h, &h->lin_bsplit, linear_presplit_bytes(*h)), "pre-split pair-mean panel");
+    if (!h->lin_bsplit) {
+        ++h->generation;
+        CK(dalloc(h, &h->lin_bsplit, linear_presplit_bytes(*h)), "pre-split pair-mean panel");
+    }
     CK(launch_linear_presplit(*h, st), "pair-mean panel split");
     return MODAL_OK;
 }
@@ -633,6 +638,7 @@ modal_status modal_set_retain_maps(modal_h h, int on) {
     if (check_plan(h)) return MODAL_EINVAL;
     h->retain_maps = on ? 1 : 0;
     if (!on) h->kept_alm = nullptr;
+    ++h->generation;
     return MODAL_OK;
 }
 
@@ -1026,6 +1032,7 @@ modal_status modal_get_zeta(modal_h h, double* zeta) {
 modal_status modal_reset(modal_h h, int what) {
     if (check_plan(h)) return MODAL_EINVAL;
     CK(cudaDeviceSynchronize(), "reset sync");
+    ++h->generation;
     if (what & 1) {
         if (h->pair_sum) CK(cudaMemset(h->pair_sum, 0, (size_t)h->n_pair * h->npix * sizeof(double)), "reset pair sums");
         if (h->ring_sum) CK(cudaMemset(h->ring_sum, 0, (size_t)h->n_pair * h->nrings * sizeof(double)), "reset ring sums");
@@ -1105,6 +1112,7 @@ modal_status modal_load_state(modal_h h, const char* path) {
         return set_error(MODAL_EINVAL, "state file does not match this plan");
     }
     CK(cudaDeviceSynchronize(), "load sync");
+    ++h->generation;
     if (hd.has_pairs && (hd.has_pairs == 2) != (h->lin_mode == MODAL_LINEAR_RING)) {
         std::fclose(f);
         return set_error(MODAL_EINVAL, "state file holds the other linear-term mode");
@@ -1193,6 +1201,7 @@ struct modal_batch {
     std::vector<const void*> key_alm;
     std::vector<int> key_B;
     std::vector<double*> key_beta;
+    std::vector<unsigned long long> key_gen;      // the plans' generations at capture
     int key_linear = -1;
 };
 
@@ -1261,6 +1270,7 @@ modal_status modal_batch_cubic(modal_batch_h bh, const void* const* alm, const i
         if (B[i] > 0 && (!alm[i] || !beta[i])) return set_error(MODAL_EINVAL, "null pointer");
         if (use_linear && !bh->plans[i]->lin_final)
             return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+        if (check_workspace(bh->plans[i])) return MODAL_ESTATE;
     }
     CK(cudaSetDevice(bh->plans[0]->dev), "set device");
     const cudaStream_t st = as_stream(stream);
@@ -1270,7 +1280,9 @@ modal_status modal_batch_cubic(modal_batch_h bh, const void* const* alm, const i
         const modal_status r = batch_run(bh, alm, B, use_linear, beta);
         if (r != MODAL_OK) return r;
     } else {
-        const bool same = bh->exec && bh->key_linear == (use_linear ? 1 : 0) &&
+        std::vector<unsigned long long> gen(n);
+        for (size_t i = 0; i < n; ++i) gen[i] = bh->plans[i]->generation;
+        const bool same = bh->exec && bh->key_linear == (use_linear ? 1 : 0) && bh->key_gen == gen &&
                           std::equal(bh->key_alm.begin(), bh->key_alm.end(), alm) &&
                           std::equal(bh->key_B.begin(), bh->key_B.end(), B) &&
                           std::equal(bh->key_beta.begin(), bh->key_beta.end(), beta);
@@ -1303,6 +1315,7 @@ modal_status modal_batch_cubic(modal_batch_h bh, const void* const* alm, const i
             bh->key_alm.assign(alm, alm + n);
             bh->key_B.assign(B, B + n);
             bh->key_beta.assign(beta, beta + n);
+            bh->key_gen = gen;
             bh->key_linear = use_linear ? 1 : 0;
         }
         CK(cudaGraphLaunch(bh->exec, bh->main), "graph launch");

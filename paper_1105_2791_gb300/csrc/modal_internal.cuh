@@ -138,6 +138,11 @@ struct Plan {
     double stage_ms[MODAL_NSTAGES] = {};
     long long stage_launches[MODAL_NSTAGES] = {};
     mutable long long launch_count = 0;   // kernels launched by this plan (note_launch)
+    // Bumped by every change that alters what a modal_cubic call launches or which buffers it
+    // touches (workspace reallocation, linear-term mode, map retention, reset, state load,
+    // first allocation of the linear-term buffers): a captured batch graph is replayed only
+    // while the generations of its plans are unchanged.
+    unsigned long long generation = 0;
     QuarticState qt;
 };
 

@@ -154,3 +154,34 @@ def config(name: str) -> dict:
         "l1000": dict(lmax=1000, nrings=1001, nphi=2048, P=12, seed=4, mask=True, noise=True),
     }
     return dict(presets[name])
+
+
+def ring_weights(nrings: int) -> np.ndarray:
+    """Gauss-Legendre weights, north first, from numpy's routine (float64 [nrings]).
+
+    Used only to scale the pixel noise draws (noise_maps)."""
+    _, w = np.polynomial.legendre.leggauss(nrings)
+    return w[::-1].copy()
+
+
+def noise_maps(nrings: int, nphi: int, nmaps: int, seed: int, sigma0_sq: float,
+               stream: int = STREAM_NOISE, first_map: int = 0) -> np.ndarray:
+    """White pixel noise n(x) = sigma(theta_j) xi_x / sqrt(Omega_j), Omega_j = w_j 2 pi / nphi,
+    sigma^2 = sigma0^2 (1 + 3 cos^2 theta), xi ~ N(0, 1); rounded to float32
+    [nmaps][nrings][nphi] so that every consumer reads the same values."""
+    sig = noise_sigma_rings(nrings, sigma0_sq)
+    omega = ring_weights(nrings) * 2.0 * math.pi / nphi
+    xi = pixel_normals(nrings, nphi, nmaps, seed, stream, first_map)
+    return ((sig / np.sqrt(omega))[None, :, None] * xi).astype(np.float32)
+
+
+def standard_normals(shape, seed: int, stream: int = STREAM_MISC) -> np.ndarray:
+    """Standard normal draws of the given shape, float64."""
+    return _rng(seed, stream).standard_normal(shape)
+
+
+def field_variance(cl: np.ndarray) -> float:
+    """<G^2> = sum_l (2l+1) C_l / (4 pi) of a Gaussian field with power C_l (the constant
+    subtracted in the non-Gaussian maps T = G + f (G^2 - <G^2>))."""
+    l = np.arange(np.asarray(cl).size)
+    return float(np.sum((2 * l + 1) * np.asarray(cl)) / (4.0 * math.pi))

@@ -69,3 +69,39 @@ def test_mixed_lmax_batch_matches_single_plans(prec):
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_graph_is_recaptured_after_a_plan_changes():
+    """A captured batch graph holds the workspace pointers and chunk loop of its plans at
+    capture time: after modal_set_chunk (which frees and reallocates the workspace),
+    modal_set_retain_maps or modal_reset the next graph call must capture again, never
+    replay launches on freed or stale buffers."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1105_2791_gb300 as M
+    plans, alms, sims = _setup(M, "fp32")
+    batch = M.Batch(plans)
+
+    def check():
+        out = [o.clone() for o in batch.cubic(alms, use_linear=True, graph=True)]
+        for plan, a, o in zip(plans, alms, out):
+            assert torch.equal(o, plan.cubic(a, use_linear=True)), plan.lmax
+
+    check()                                             # capture
+    check()                                             # replay
+    plans[2].set_chunk(1)                               # new workspace, four chunk passes
+    check()
+    plans[1].set_chunk(2)
+    plans[0].set_retain_maps(True)
+    check()
+    # reset then a new finalised mean (same buffers, new contents)
+    plans[2].reset(1)
+    with pytest.raises(M.ModalError):
+        batch.cubic(alms, use_linear=True, graph=True)  # no finalised mean: refused, not replayed
+    plans[2].linear_term(torch.from_numpy(sims[2][:3]).cuda(), finalize=True)
+    check()
+    for p in plans:
+        p.sync()
+    batch.close()
+    for p in plans:
+        p.close()
