@@ -182,7 +182,7 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
         "legendre_adjoint": ("tensor" if tensor_peak else "alu", legendre_flops(P, L, R) * chunk, launches),
         "ring_c2r": ("hbm", delta_bytes + map_bytes, nsynth * launches),
         "ring_r2c": ("hbm", delta_bytes + map_bytes, launches),
-        "adjoint_pixel": ("alu", 2.0 * P * n_pair * npix * chunk, launches),
+        "adjoint_pixel": ("tensor" if tensor_peak else "alu", 2.0 * P * n_pair * npix * chunk, launches),
         "cubic": ("alu", 2.0 * n_max * npix * chunk, launches),
         "linear_gemm": ("tensor" if tensor_peak else "alu", 2.0 * n_pair * P * npix * chunk, launches),
         "pair_means": ("hbm", map_bytes + 2.0 * n_pair * npix * 8, launches),
@@ -200,9 +200,10 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
             peak, unit, achieved = hbm, "GB/s", total / (ms / 1e3) / 1e9
             src = "measured HBM copy"
         elif bound == "tensor":
-            tp = bf16 / 6.0 if stage == "linear_gemm" else tensor_peak     # the linear GEMM runs 3xTF32
+            tf32x3 = stage in ("linear_gemm", "adjoint_pixel")               # these run 3xTF32
+            tp = bf16 / 6.0 if tf32x3 else tensor_peak
             peak, unit, achieved = tp, "TFLOP/s", total / (ms / 1e3) / 1e12
-            src = "measured bf16 sustained / %s" % ("2 (tf32) / 3 products" if stage == "linear_gemm"
+            src = "measured bf16 sustained / %s" % ("2 (tf32) / 3 products" if tf32x3
                                                     else "%g products per useful MAC" % split[prec])
         else:
             peak, unit, achieved = fp32, "TFLOP/s", total / (ms / 1e3) / 1e12

@@ -153,7 +153,8 @@ static size_t per_map_workspace(const modal_plan* pl) {
     const size_t delta = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
     const size_t maps = (size_t)pl->P * pl->npix * sizeof(float);
     const size_t ut = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
-    return delta + maps + ut + tc_b_workspace_bytes(*pl, 8) / 8 + tc_adj_workspace_bytes(*pl, 8) / 8;
+    return delta + maps + ut + tc_b_workspace_bytes(*pl, 8) / 8 + tc_adj_workspace_bytes(*pl, 8) / 8 +
+           adjoint_tc_workspace_bytes(*pl, 1);
 }
 
 static void free_workspace(modal_plan* pl) {
@@ -163,6 +164,7 @@ static void free_workspace(modal_plan* pl) {
     dfree(pl->ut); pl->ut = nullptr;
     dfree(pl->partial); pl->partial = nullptr;
     dfree(pl->hk); pl->hk = nullptr;
+    dfree(pl->adj_hops); pl->adj_hops = nullptr;
     dfree(pl->vring); pl->vring = nullptr;
     dfree(pl->tc.bops); pl->tc.bops = nullptr;
     dfree(pl->tca.bops); pl->tca.bops = nullptr;
@@ -176,6 +178,7 @@ static modal_status alloc_workspace_buffers(modal_plan* pl, int chunk) {
     CK(dalloc(pl, &pl->maps, (size_t)chunk * pl->P * pl->npix), "workspace maps");
     CK(dalloc(pl, &pl->ut, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace ut");
     CK(dalloc(pl, &pl->hk, (size_t)chunk * pl->P * pl->n_pair), "workspace hk");
+    CK(dalloc(pl, &pl->adj_hops, adjoint_tc_workspace_bytes(*pl, chunk)), "workspace adjoint operands");
     CK(dalloc(pl, &pl->vring, (size_t)chunk * pl->P * pl->nrings), "workspace vring");
     // cubic partials: [chunk][cubic_ctas][n_max]; linear partials: [ksplit][n_pair][chunk*P]
     const size_t cub = (size_t)chunk * pl->cubic_ctas * pl->n_max;
@@ -895,7 +898,10 @@ static modal_status backward_impl(modal_h h, const void* alm, int B, const doubl
         {
             STAGE(h, ST_ADJ_PIXEL, st);
             if (ring) CK(launch_vring(*h, h->hk, nb, h->vring, st), "adjoint ring term");
-            CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear && !ring, h->maps, st), "adjoint pixel");
+            if (h->prec == MODAL_FP32)
+                CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear && !ring, h->maps, st), "adjoint pixel");
+            else
+                CK(launch_adjoint_tc(*h, nb, h->hk, use_linear && !ring, h->maps, st), "adjoint pixel");
         }
         {
             // split precisions: the r2c kernel also records each map's max |U~| for the operand scale

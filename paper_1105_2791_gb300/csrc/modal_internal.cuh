@@ -119,6 +119,7 @@ struct Plan {
     const void* kept_alm = nullptr;   // a_lm they were synthesised from (nullptr: none kept)
     int kept_B = 0;
     float* hk = nullptr;         // [chunk][P][n_pair] adjoint weights
+    char* adj_hops = nullptr;    // [chunk] tf32 hi/lo B operands of the tensor-core adjoint pixel weights
     // ring-only linear term (modal_set_linear_mode)
     int lin_mode = 0;            // MODAL_LINEAR_PIXEL or MODAL_LINEAR_RING
     int has_pix_mask = 0;        // W varies along rings: ring mode refused
@@ -201,6 +202,9 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
 // vring [B][P][nrings] (ring mode, use_linear = 0); neither when both are off.
 cudaError_t launch_adjoint_u(Plan& pl, const float* maps, int B, const float* hk, int use_linear,
                              float* u, cudaStream_t st);
+// k_adjoint_tc.cu: the same pixel weights as a tcgen05 product (split plans); in place on maps
+size_t adjoint_tc_workspace_bytes(const Plan& pl, int chunk);
+cudaError_t launch_adjoint_tc(Plan& pl, int B, const float* hk, int use_linear, float* maps, cudaStream_t st);
 // k_ring_linear.cu
 cudaError_t launch_pair_ring(Plan& pl, const float* maps, int B, cudaStream_t st);
 cudaError_t launch_ring_finalize(Plan& pl, cudaStream_t st);
