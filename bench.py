@@ -5,7 +5,7 @@ One step = one batch of B maps through every stage of the per-map path:
   linear-term pass   synthesis (filter + Legendre sums + ring FFT) and the pair sums
   coefficient pass   synthesis, cubic term with the linear term, covariance sums
   solve              FP64 Cholesky of zeta and the fNL estimate of every map
-  adjoint            d(sum_n g_n beta_n)/d a_lm with maps recomputed
+  adjoint            d fNL / d a_lm (the adjoint with g = d fNL / d beta) with maps recomputed
 The workload is l_max = 2000 on 2001 Gauss-Legendre rings x 4096 longitudes, 16
 shifted-Legendre modes (n_max = 816), C_l = 1/(l(l+1)), synthetic Gaussian a_lm
 (seeded Philox).  All buffers are far larger than L2 (129 MB), so no flush is needed.
@@ -286,13 +286,15 @@ def run_gpu(args):
             raise SystemExit("precision %s not available" % prec)
 
     alpha = plan.alpha_local()
-    g = torch.from_numpy(np.tile(alpha / (alpha @ alpha), (B, 1))).to(dev)
     beta = torch.empty((B, plan.n_max), dtype=torch.float64, device=dev)
     grad = torch.empty((B, plan.n_alm), dtype=torch.complex64, device=dev)
     # Seed the covariance sums with 2 n_max random vectors so that zeta is positive definite
     # from the first step on (a real run accumulates N_cov >> n_max simulations first).
     gen = torch.Generator(device=dev).manual_seed(5)
     plan.cov_accumulate(torch.randn((2 * plan.n_max, plan.n_max), generator=gen, device=dev, dtype=torch.float64))
+    # the adjoint differentiates fNL: g = d fNL / d beta = zeta^-1 alpha / alpha^T zeta^-1 alpha
+    w_fnl, _ = plan.fnl_weights(alpha)
+    g = w_fnl[None, :].repeat(B, 1).contiguous()
     torch.cuda.synchronize()
 
     side = torch.cuda.Stream(device=dev)

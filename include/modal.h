@@ -148,6 +148,16 @@ modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* st
 modal_status modal_solve(modal_h h, const double* alpha, const double* beta, int B,
                          double* fnl, double* sigma, void* stream);
 
+/* Derivative of the estimate with respect to the modal coefficients (Eq. modalest):
+ * fNL = alpha^T zeta^-1 beta / alpha^T zeta^-1 alpha is linear in beta, so
+ *   d fNL / d beta = w = zeta^-1 alpha / (alpha^T zeta^-1 alpha),
+ * formed on the GPU from the accumulated covariance (FP64 Cholesky zeta = L L^T, forward
+ * and back substitution).  w passed as g to modal_backward gives d fNL / d a_lm.
+ * alpha: host [n_max]; w: dev out [n_max] float64; sigma: host out (may be NULL).
+ * MODAL_ESTATE with fewer than 2 covariance sims; MODAL_ENOTPD if zeta is not positive
+ * definite.  Synchronises. */
+modal_status modal_fnl_weights(modal_h h, const double* alpha, double* w, double* sigma, void* stream);
+
 /* Bivector form of the covariance (Sec. III.B, Eqs. ic_bivector, ic_bivectorinv,
  * bivecvariance).  Given an ideal covariance zeta0 = L0 L0^T (e.g. full sky with
  * homogeneous noise, where it is cheap to know), the Monte Carlo zeta is modelled as

@@ -26,6 +26,8 @@ What each function follows:
                    read as the unbiased sample covariance divided by 6.
   solve_fnl        Eq. modalest and Eq. modalvariance via the Cholesky rotation
                    (Eq. Cholrot): E = alpha'.beta' / |alpha'|^2, sigma^2 = 6 / |alpha'|^2.
+  fnl_weights      d fNL / d beta of Eq. modalest (fNL is linear in beta):
+                   zeta^-1 alpha / (alpha^T zeta^-1 alpha).
   alpha_local      Eq. abispect for b = 2 f (C1 C2 + C2 C3 + C3 C1), the first-order
                    bispectrum of T = G + f (G^2 - <G^2>), evaluated through the identity
                    sum h^2 F G H = 8 pi^2 int f g h dmu (h from Sec. III.A).
@@ -191,6 +193,15 @@ def solve_fnl(zeta: np.ndarray, alpha: np.ndarray, betas: np.ndarray):
     bp = solve_triangular(Lc, np.atleast_2d(betas).T, lower=True)
     norm = float(ap @ ap)
     return (ap @ bp) / norm, math.sqrt(6.0 / norm)
+
+
+def fnl_weights(zeta: np.ndarray, alpha: np.ndarray) -> np.ndarray:
+    """d fNL / d beta of Eq. modalest: fNL = alpha^T zeta^-1 beta / alpha^T zeta^-1 alpha is
+    linear in beta, w = zeta^-1 alpha / (alpha^T zeta^-1 alpha), by the Cholesky factor
+    zeta = L L^T: alpha' = L^-1 alpha, w = L^-T alpha' / |alpha'|^2."""
+    Lc = np.linalg.cholesky(zeta)
+    ap = solve_triangular(Lc, alpha, lower=True)
+    return solve_triangular(Lc.T, ap, lower=False) / float(ap @ ap)
 
 
 def _legendre_table(lmax: int, x: np.ndarray) -> np.ndarray:

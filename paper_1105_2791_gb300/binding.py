@@ -32,7 +32,7 @@ EXPORTS = [
     "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
     "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
     "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate", "modal_quartic",
-    "modal_set_retain_maps", "modal_backward_retained",
+    "modal_set_retain_maps", "modal_backward_retained", "modal_fnl_weights",
 ]
 MODAL_NSTAGES = 15
 
@@ -80,6 +80,7 @@ def load_library():
         "modal_cubic": [H, c_void_p, c_int, c_int, c_void_p, c_void_p],
         "modal_cov_accumulate": [H, c_void_p, c_int, c_void_p],
         "modal_solve": [H, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
+        "modal_fnl_weights": [H, c_void_p, c_void_p, c_void_p, c_void_p],
         "modal_bivector_fit": [H, c_void_p, c_void_p, c_void_p, c_void_p],
         "modal_solve_bivector": [H, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
         "modal_bivector_rotate": [H, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p],
@@ -235,6 +236,15 @@ def modal_solve(h, alpha, beta, B, stream=None):
     _check(load_library().modal_solve(h, a_ptr, _dev(beta), int(B), fnl.ctypes.data_as(c_void_p), byref(sigma),
                                       _stream(stream)))
     return fnl[: int(B)], sigma.value
+
+
+def modal_fnl_weights(h, alpha, w, stream=None):
+    """w = d fNL / d beta = zeta^-1 alpha / (alpha^T zeta^-1 alpha) into dev w [n_max] float64;
+    returns sigma."""
+    a_arr, a_ptr = _host(alpha, np.float64)
+    sigma = c_double(0.0)
+    _check(load_library().modal_fnl_weights(h, a_ptr, _dev(w), byref(sigma), _stream(stream)))
+    return sigma.value
 
 
 def modal_bivector_fit(h, zeta0, stream=None):

@@ -171,6 +171,37 @@ cudaError_t launch_solve_rhs(Plan& pl, const double* Lc, int n, double* rhs, int
     return cudaGetLastError();
 }
 
+// Back substitution L^T x = y in place (one CTA): after x_i is known every thread updates
+// its y_k, k < i, with L_ik (row i of the lower factor).
+__global__ void __launch_bounds__(256) k_solve_rhs_t(int n, const double* __restrict__ Lc, double* __restrict__ v) {
+    __shared__ double xi;
+    for (int i = n - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) {
+            xi = v[i] / Lc[(int64_t)i * n + i];
+            v[i] = xi;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < i; k += blockDim.x) v[k] -= Lc[(int64_t)i * n + k] * xi;
+        __syncthreads();
+    }
+}
+
+// w = x / norm[0] (one CTA).
+__global__ void __launch_bounds__(256) k_scale_by(int n, const double* __restrict__ x, const double* __restrict__ norm,
+                                                  double* __restrict__ w) {
+    const double inv = 1.0 / norm[0];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = x[i] * inv;
+}
+
+cudaError_t launch_fnl_weights(Plan& pl, const double* Lc, int n, double* v, const double* norm, double* w,
+                               cudaStream_t st) {
+    k_solve_rhs_t<<<1, 256, 0, st>>>(n, Lc, v);
+    note_launch(pl);
+    k_scale_by<<<1, 256, 0, st>>>(n, v, norm, w);
+    note_launch(pl);
+    return cudaGetLastError();
+}
+
 // out[0] = |alpha'|^2, out[1 + b] = alpha'.beta'_b / |alpha'|^2; rhs = [alpha'; beta'_0; ...].
 __global__ void __launch_bounds__(256) k_estimates(int n, int B, const double* __restrict__ rhs, double* __restrict__ out) {
     __shared__ double red[256];

@@ -710,6 +710,39 @@ static modal_status read_device_error(modal_h h, cudaStream_t st) {
     return MODAL_OK;
 }
 
+modal_status modal_fnl_weights(modal_h h, const double* alpha, double* w, double* sigma, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!alpha || !w) return set_error(MODAL_EINVAL, "alpha and w are required");
+    if (h->n_cov < 2) return set_error(MODAL_ESTATE, "need at least 2 covariance simulations");
+    cudaStream_t st = as_stream(stream);
+    const int n = h->n_max;
+    double* ws = nullptr;
+    CK(cudaMallocAsync(&ws, ((size_t)n * n + n + 1) * sizeof(double), st), "weights workspace");
+    double* A = ws;
+    double* v = ws + (size_t)n * n;
+    double* norm = v + n;
+    auto run = [&]() -> modal_status {
+        { STAGE(h, ST_SOLVE, st); CK(launch_zeta(*h, A, st), "zeta"); }
+        { STAGE(h, ST_SOLVE, st); CK(launch_cholesky(*h, A, n, st), "cholesky"); }
+        CK(cudaMemcpyAsync(v, alpha, n * sizeof(double), cudaMemcpyHostToDevice, st), "alpha copy");
+        modal_status es = read_device_error(h, st);
+        if (es != MODAL_OK) return es;
+        { STAGE(h, ST_SOLVE, st); CK(launch_solve_rhs(*h, A, n, v, 1, st), "triangular solve"); }
+        { STAGE(h, ST_SOLVE, st); CK(launch_estimates(*h, v, n, 0, norm, st), "alpha norm"); }
+        { STAGE(h, ST_SOLVE, st); CK(launch_fnl_weights(*h, A, n, v, norm, w, st), "back substitution"); }
+        double nrm = 0.0;
+        CK(cudaMemcpyAsync(&nrm, norm, sizeof(double), cudaMemcpyDeviceToHost, st), "norm copy");
+        CK(cudaStreamSynchronize(st), "weights sync");
+        if (!(nrm > 0.0)) return set_error(MODAL_ENOTPD, "alpha^T zeta^-1 alpha is not positive");
+        if (sigma) *sigma = std::sqrt(6.0 / nrm);
+        return MODAL_OK;
+    };
+    const modal_status s = run();
+    cudaFreeAsync(ws, st);
+    cudaStreamSynchronize(st);
+    return s;
+}
+
 modal_status modal_solve(modal_h h, const double* alpha, const double* beta, int B, double* fnl, double* sigma,
                          void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;

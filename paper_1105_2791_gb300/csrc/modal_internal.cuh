@@ -219,6 +219,9 @@ cudaError_t launch_zeta(Plan& pl, double* zeta, cudaStream_t st);
 cudaError_t launch_cholesky(Plan& pl, double* A, int n, cudaStream_t st);
 cudaError_t launch_solve_rhs(Plan& pl, const double* Lc, int n, double* rhs, int nrhs, cudaStream_t st);
 cudaError_t launch_estimates(Plan& pl, const double* rhs, int n, int B, double* out, cudaStream_t st);
+// v = alpha' (forward-solved) -> w = L^-T alpha' / norm[0] (dev norm = |alpha'|^2)
+cudaError_t launch_fnl_weights(Plan& pl, const double* Lc, int n, double* v, const double* norm, double* w,
+                               cudaStream_t st);
 cudaError_t launch_wait_selftest(int* d_err, int spin_limit, cudaStream_t st);
 // trispectrum modes (k_quartic.cu)
 cudaError_t quartic_tables(Plan& pl);

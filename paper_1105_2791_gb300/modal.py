@@ -85,6 +85,13 @@ class Plan:
         nb = 0 if beta is None else beta.shape[0]
         return B.modal_solve(self.h, alpha, beta, nb)
 
+    def fnl_weights(self, alpha):
+        """(w, sigma): w = d fNL / d beta = zeta^-1 alpha / (alpha^T zeta^-1 alpha), dev [n_max]
+        float64, from the accumulated covariance (modal_fnl_weights)."""
+        w = torch.empty(self.n_max, dtype=torch.float64, device="cuda")
+        sigma = B.modal_fnl_weights(self.h, alpha, w)
+        return w, sigma
+
     def bivector_fit(self, zeta0):
         """(bt, l1): the Monte Carlo zeta fitted as L0 (I + bt bt^T) L0^T, zeta0 = L0 L0^T."""
         return B.modal_bivector_fit(self.h, zeta0)
@@ -174,6 +181,33 @@ class ModalBeta(torch.autograd.Function):
 
 def modal_beta(alm, plan, use_linear=False):
     return ModalBeta.apply(alm, plan, use_linear)
+
+
+class ModalFnl(torch.autograd.Function):
+    """fNL of each map (Eq. modalest with the plan's accumulated covariance and a shape
+    alpha) as a function of its a_lm (complex64 [B][n_alm]).  fNL is linear in beta with
+    d fNL / d beta = w = zeta^-1 alpha / (alpha^T zeta^-1 alpha) (modal_fnl_weights), so the
+    backward is the library's adjoint with g_b = (d L / d fNL_b) w; zeta is held fixed."""
+
+    @staticmethod
+    def forward(ctx, alm, plan, alpha, use_linear):
+        a = alm.detach().contiguous()
+        beta = plan.cubic(a, use_linear)
+        fnl, _ = plan.solve(alpha, beta)
+        w, _ = plan.fnl_weights(alpha)
+        ctx.plan, ctx.use_linear = plan, bool(use_linear)
+        ctx.save_for_backward(alm, w)
+        return torch.from_numpy(np.ascontiguousarray(fnl)).to(alm.device)
+
+    @staticmethod
+    def backward(ctx, gfnl):
+        alm, w = ctx.saved_tensors
+        g = (gfnl.detach().to(torch.float64)[:, None] * w[None, :]).contiguous()
+        return ctx.plan.backward(alm.detach().contiguous(), g, ctx.use_linear), None, None, None
+
+
+def modal_fnl(alm, plan, alpha, use_linear=True):
+    return ModalFnl.apply(alm, plan, alpha, use_linear)
 
 
 class Batch:

@@ -1,0 +1,231 @@
+"""GPU parity at the sizes the metric and the workloads are quoted on, against FP64 oracle
+results stored by tests/golden/make_fullsize.py (oracle/ and simgen/ only; minutes to tens
+of minutes of host time each, too slow to recompute here).
+
+  l_max = 2000 workload, full 2001 x 4096 grid (every pixel in every sum), 16 modes:
+      beta of a Gaussian map G and of T = G + 50 (G^2 - <G^2>), with and without the
+      linear term (pair means over 2 simulations)            ||d beta|| / ||beta|| <= 1e-5
+  adjoint workload, l_max = 1000 on the full 1001 x 2048 grid, 12 modes, noise and band mask:
+      the gradient of sum_n g_n beta_n on 4096 sampled coefficients  ||d grad|| / ||grad|| <= 1e-5,
+      its norm (<= 1e-5) and four projections on seeded random directions
+      (|d (r . grad)| <= 3e-5 ||grad||: three standard deviations of r . d grad when
+      ||d grad|| = 1e-5 ||grad||), and beta with the linear term
+  WMAP-resolution chain (l_max = 500, 220 modes, N_lin = 256, N_cov = 1024, noise, mask) and
+  the 816-mode chain at l_max = 2000 (N_cov = 1024): zeta (diagonal and 256 sampled
+      entries, <= 1e-5), alpha (<= 1e-10), beta of the data maps (<= 1e-5), sigma (<= 1e-5) and
+      fNL (|d fNL| <= 1e-4 sigma); the sums run over 8 rings selected by a ring mask, which the
+      oracle sums over directly.
+
+Inputs come only from simgen; each side runs its own transforms (the non-Gaussian maps are
+built on an exact-cubic grid by each side, and the stored a_lm samples of T check the GPU's
+input before its beta is compared).
+"""
+import importlib.util
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import simgen
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+PRECS = [p for p in os.environ.get("MODAL_TEST_PRECS", "fp32,fp16x3,3xtf32").split(",") if p]
+
+
+def _maker():
+    spec = importlib.util.spec_from_file_location("make_fullsize", os.path.join(HERE, "golden", "make_fullsize.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+MK = _maker()
+
+
+def _golden(target):
+    path = MK.path(target)
+    if not os.path.exists(path):
+        pytest.skip("%s not written (python tests/golden/make_fullsize.py %s)" % (os.path.basename(path), target))
+    return MK.load(target)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1105_2791_gb300 as M
+    return M
+
+
+def _plan(M, L, P, basis, cl, R, nphi, prec, **kw):
+    try:
+        return M.Plan(L, P, basis, cl, R, nphi, prec=prec, **kw)
+    except M.ModalError as e:
+        if prec != "fp32" and "not supported" in str(e):
+            pytest.skip("precision %s not built" % prec)
+        raise
+
+
+def _c64(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).cuda()
+
+
+def _nongaussian(M, aS, cl, f):
+    """a_lm of T = S + f (S^2 - <S^2>): S synthesised and T analysed by the library on an
+    exact-cubic grid (float32 maps, T formed in float64)."""
+    L = cl.size - 1
+    R, nphi = MK.exact_cubic_grid(L)
+    raw = M.Plan(L, 1, np.sqrt(cl)[None, :], cl, R, nphi, prec="fp32")
+    S = raw.synthesize(aS)[:, 0].double()
+    T = S + f * (S * S - simgen.field_variance(cl))
+    aT = raw.analyze(T.float().contiguous())
+    raw.sync()
+    raw.close()
+    return aT
+
+
+def _noisy(plan, cl, n, seed, stream, s0, batch=64):
+    """Signal a_lm plus the library's quadrature analysis of the seeded pixel noise."""
+    out = []
+    for b0 in range(0, n, batch):
+        nb = min(batch, n - b0)
+        sig = _c64(simgen.gaussian_alm(cl, nb, seed=seed, stream=stream, first_map=b0))
+        if s0 > 0:
+            nm = simgen.noise_maps(plan.nrings, plan.nphi, nb, seed=seed, sigma0_sq=s0, first_map=b0)
+            sig = sig + plan.analyze(torch.from_numpy(nm).cuda())
+        out.append(sig)
+    return torch.cat(out).contiguous()
+
+
+# ------------------------------------------------------------------ l_max = 2000, full grid
+@pytest.fixture(scope="module")
+def l2000_inputs():
+    M = _lib()
+    gd = _golden("beta_l2000")
+    L = gd["lmax"]
+    cl = simgen.cl_model(L)
+    aG = _c64(simgen.gaussian_alm(cl, 1, seed=3))
+    aT = _nongaussian(M, aG, cl, gd["f_ng"])
+    idx = np.array(gd["aT_index"])
+    ref = np.array(gd["aT_sample"][0]) + 1j * np.array(gd["aT_sample"][1])
+    got = aT[0].cpu().numpy()[idx]
+    err = _rel(got, ref)
+    print("T = G + %g (G^2 - <G^2>) at l_max=%d: sampled a_lm rel err %.3g" % (gd["f_ng"], L, err))
+    assert err <= 1e-5
+    sims = _c64(simgen.gaussian_alm(cl, 2, seed=4, stream=simgen.STREAM_LINEAR))
+    return gd, torch.cat([aG, aT]).contiguous(), sims
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_grid_beta_l2000(prec, l2000_inputs):
+    M = _lib()
+    gd, alm, sims = l2000_inputs
+    L, P, R, nphi = gd["lmax"], gd["P"], gd["nrings"], gd["nphi"]
+    cl = simgen.cl_model(L)
+    plan = _plan(M, L, P, simgen.shifted_legendre_basis(L, P), cl, R, nphi, prec)
+    plan.set_chunk(2)
+    plan.linear_term(sims, finalize=True)
+    beta = plan.cubic(alm).cpu().numpy()
+    beta_lin = plan.cubic(alm, use_linear=True).cpu().numpy()
+    plan.sync()
+    plan.close()
+    for i, name in enumerate(("G", "T")):
+        e0 = _rel(beta[i], gd["beta_%s" % name])
+        e1 = _rel(beta_lin[i], gd["beta_lin_%s" % name])
+        print("full grid l_max=%d %s %s: beta rel err %.3g, with linear term %.3g" % (L, prec, name, e0, e1))
+        assert e0 <= 1e-5 and e1 <= 1e-5
+
+
+# ------------------------------------------------------------------ adjoint, l_max = 1000, full grid
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_grid_gradient_l1000(prec):
+    M = _lib()
+    gd = _golden("grad_l1000")
+    L, P, R, nphi, s0 = gd["lmax"], gd["P"], gd["nrings"], gd["nphi"], gd["sigma0_sq"]
+    cl = simgen.cl_model(L)
+    cl_tot = cl + np.where(np.arange(L + 1) >= 2, 2.0 * s0, 0.0)
+    plan = _plan(M, L, P, simgen.shifted_legendre_basis(L, P), cl_tot, R, nphi, prec,
+                 ring_mask=simgen.band_mask(R, gd["mask_deg"]))
+    plan.set_chunk(2)
+    plan.linear_term(_noisy(plan, cl, 2, 101, simgen.STREAM_LINEAR, s0), finalize=True)
+    a = _noisy(plan, cl, 1, 102, simgen.STREAM_DATA, s0)
+    g = torch.from_numpy(simgen.standard_normals(gd["n_max"], seed=103)[None, :]).cuda()
+    beta = plan.cubic(a, use_linear=True).cpu().numpy()[0]
+    grad = plan.backward(a, g, use_linear=True).cpu().numpy()[0].astype(np.complex128)
+    plan.sync()
+    plan.close()
+    idx = np.array(gd["grad_index"])
+    ref = np.array(gd["grad_sample"][0]) + 1j * np.array(gd["grad_sample"][1])
+    gnorm = gd["grad_norm"]
+    e_beta = _rel(beta, gd["beta_lin"])
+    e_smp = _rel(grad[idx], ref)
+    e_norm = abs(np.linalg.norm(grad) - gnorm) / gnorm
+    r = simgen.standard_normals((4, grad.size, 2), seed=gd["proj_seed"])
+    proj = np.array([np.sum(grad.real * r[k, :, 0] + grad.imag * r[k, :, 1]) for k in range(4)])
+    e_proj = np.max(np.abs(proj - np.array(gd["grad_proj"]))) / gnorm
+    print("full grid l_max=%d %s: beta %.3g, gradient samples %.3g, norm %.3g, projections %.3g (of ||grad||)"
+          % (L, prec, e_beta, e_smp, e_norm, e_proj))
+    assert e_beta <= 1e-5 and e_smp <= 1e-5 and e_norm <= 1e-5 and e_proj <= 3e-5
+
+
+# ------------------------------------------------------------------ Monte Carlo chains at size
+def _chain(M, gd, prec):
+    L, P, R, nphi, s0 = gd["lmax"], gd["P"], gd["nrings"], gd["nphi"], gd["sigma0_sq"]
+    cl = simgen.cl_model(L)
+    cl_tot = cl + (np.where(np.arange(L + 1) >= 2, 2.0 * s0, 0.0) if s0 > 0 else 0.0)
+    sel = np.zeros(R)
+    sel[np.array(gd["rings"])] = 1.0
+    plan = _plan(M, L, P, simgen.shifted_legendre_basis(L, P), cl_tot, R, nphi, prec, ring_mask=sel)
+    plan.set_chunk(32)
+    s_lin, s_cov, s_dat = gd["seeds"]
+    plan.linear_term(_noisy(plan, cl, gd["n_lin"], s_lin, simgen.STREAM_LINEAR, s0), finalize=True)
+    for b0 in range(0, gd["n_cov"], 256):
+        nb = min(256, gd["n_cov"] - b0)
+        sig = _c64(simgen.gaussian_alm(cl, nb, seed=s_cov, stream=simgen.STREAM_COV, first_map=b0))
+        if s0 > 0:
+            nm = simgen.noise_maps(R, nphi, nb, seed=s_cov, sigma0_sq=s0, first_map=b0)
+            sig = sig + plan.analyze(torch.from_numpy(nm).cuda())
+        plan.cov_accumulate(plan.cubic(sig.contiguous(), use_linear=True))
+    data = _noisy(plan, cl, 4, s_dat, simgen.STREAM_DATA, s0)
+    if gd["f_ng"]:
+        aS = _c64(simgen.gaussian_alm(cl, 4, seed=s_dat, stream=simgen.STREAM_DATA)[2:])
+        data[2:] += _nongaussian(M, aS, cl, gd["f_ng"]) - aS
+    bd = plan.cubic(data.contiguous(), use_linear=True)
+    alpha = plan.alpha_local(C_signal=cl)
+    fnl, sigma = plan.solve(alpha, bd)          # sums over the selected rings only: a parity check, not an estimate
+    zeta = plan.zeta()
+    plan.sync()
+    plan.close()
+    zi = np.array(gd["zeta_index"])
+    e_diag = _rel(np.diag(zeta), gd["zeta_diag"])
+    e_zs = _rel(zeta.ravel()[zi], gd["zeta_sample"])
+    e_alpha = _rel(alpha, gd["alpha"])
+    e_beta = max(_rel(b, r) for b, r in zip(bd.cpu().numpy(), gd["beta_data"]))
+    e_sigma = abs(sigma - gd["sigma"]) / gd["sigma"]
+    e_fnl = np.max(np.abs(np.asarray(fnl) - np.array(gd["fnl"]))) / gd["sigma"]
+    print("chain l_max=%d (%d modes) %s: zeta diag %.3g, sampled %.3g; alpha %.3g; data beta %.3g; sigma %.3g; "
+          "fNL %.3g sigma (fNL %s, sigma %.4g)" % (L, gd["n_max"], prec, e_diag, e_zs, e_alpha, e_beta, e_sigma,
+                                                  e_fnl, np.round(fnl, 6), sigma))
+    assert e_diag <= 1e-5 and e_zs <= 1e-5 and e_alpha <= 1e-10 and e_beta <= 1e-5
+    assert e_sigma <= 1e-5 and e_fnl <= 1e-4
+    return fnl, sigma
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
+def test_wmap_resolution_chain_at_size(prec):
+    M = _lib()
+    _chain(M, _golden("wmap_chain"), prec)
+
+
+@pytest.mark.parametrize("prec", ["fp16x3"])
+def test_816_mode_chain_l2000_at_size(prec):
+    M = _lib()
+    _chain(M, _golden("chain_l2000"), prec)

@@ -523,3 +523,22 @@ def test_planted_quartic_mistakes_are_caught():
         return fn
     for kind in ("three_splits", "one_matching", "matching_sign"):
         assert _hermite_check(variant(kind)) > 1e-3, kind
+
+
+def test_fnl_weights_are_the_derivative_of_the_estimate():
+    """w = d fNL / d beta: fNL(beta) = w . beta for random beta (fNL is linear in beta), the
+    identity covariance gives alpha / |alpha|^2, and under a mode transform T (beta -> T beta,
+    alpha -> T alpha, zeta -> T zeta T^T) the weights become T^-T w."""
+    rng = np.random.default_rng(7)
+    n = 20
+    X = rng.standard_normal((3 * n, n))
+    zeta = X.T @ X / (3 * n) + 0.1 * np.eye(n)
+    alpha = rng.standard_normal(n)
+    betas = rng.standard_normal((5, n))
+    w = modal.fnl_weights(zeta, alpha)
+    fnl, _ = modal.solve_fnl(zeta, alpha, betas)
+    assert np.allclose(betas @ w, fnl, rtol=1e-12, atol=1e-12)
+    assert np.allclose(modal.fnl_weights(np.eye(n), alpha), alpha / (alpha @ alpha), rtol=1e-13)
+    T = simgen.random_modes_matrix(n, seed=8)
+    wT = modal.fnl_weights(T @ zeta @ T.T, T @ alpha)
+    assert np.allclose(wT, np.linalg.solve(T.T, w), rtol=1e-9, atol=1e-12)

@@ -154,3 +154,21 @@ def test_analysis_inverts_synthesis(L, nrings, nphi):
     a = simgen.white_alm(L, 1, seed=7)[0]
     maps = sht.synthesize(a, L, np.ones((1, L + 1)), mu, nphi)[0]
     np.testing.assert_allclose(sht.analyze(maps, L, mu, w, nphi), a, atol=1e-12)
+
+
+def test_batched_transforms_equal_the_per_map_transforms():
+    """synthesize_many / analyze_many (the lambda table of a ring block formed once for
+    several maps, used by the full-size fixture script) give the per-map results exactly."""
+    L, P, R, nphi = 24, 3, 27, 64
+    cl = simgen.cl_model(L)
+    filt = sht.filter_table(simgen.shifted_legendre_basis(L, P), cl)
+    a = simgen.gaussian_alm(cl, 3, seed=51)
+    mu, w = sht.gl_nodes(R)
+    many = sht.synthesize_many(a, L, filt, mu, nphi)
+    for i in range(3):
+        assert np.array_equal(many[i], sht.synthesize(a[i], L, filt, mu, nphi))
+    x = simgen.noise_maps(R, nphi, 3, seed=52, sigma0_sq=0.1).astype(np.float64)
+    am = sht.analyze_many(x, L, mu, w, nphi)
+    for i in range(3):
+        ref = sht.analyze(x[i], L, mu, w, nphi)
+        assert np.max(np.abs(am[i] - ref)) <= 1e-13 * np.max(np.abs(ref))
