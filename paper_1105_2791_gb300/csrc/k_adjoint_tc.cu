@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(AT_THREADS, 1) k_adjoint_tc(const __grid_const
         mbar_init(&hbar, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&pm_full[i], 1);
-            mbar_init(&pm_empty[i], 4 * nbq);             // every converter warp of every map of the tile
+            mbar_init(&pm_empty[i], 4 * AT_GROUPS);       // every converter warp, once per tile
         }
         abort_word = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -284,7 +284,11 @@ __global__ void __launch_bounds__(AT_THREADS, 1) k_adjoint_tc(const __grid_const
                     if (t < a.P) out[(int64_t)t * a.npix] = v[t] * w;
             }
         };
-        // the map values of the group's next tile-map are loaded one tile-map ahead
+        // Every group walks every tile of the CTA in order: it waits for the tile's pair means,
+        // converts its own tile-maps of that tile (n = ti nbq + j with n = g mod AT_GROUPS, none
+        // for some tiles when nbq < AT_GROUPS) and releases the buffer, so each buffer's fills
+        // are observed one phase at a time and no tile can overtake another on a buffer.
+        // The map values of the group's next tile-map are loaded one tile-map ahead.
         float Mn[AT_PM];
         auto load_maps = [&](int64_t n) {
             const int64_t x = (tile0 + (n / nbq) * a.G) * 128 + xl;
@@ -293,68 +297,73 @@ __global__ void __launch_bounds__(AT_THREADS, 1) k_adjoint_tc(const __grid_const
 #pragma unroll
             for (int p = 0; p < AT_PM; ++p) Mn[p] = (in && p < a.P) ? mb[(int64_t)p * a.npix] : 0.f;
         };
-        load_maps(g);
-        for (int64_t n = g; n < n_tm; n += AT_GROUPS) {
-            const int64_t ti = n / nbq;                   // tile index in this CTA's sequence
-            const int64_t tile = tile0 + ti * a.G;
-            const int b = b0 + (int)(n % nbq);
-            const int64_t x = tile * 128 + xl;
-            const bool in = x < a.npix;
-            float M[AT_PM];
-#pragma unroll
-            for (int p = 0; p < AT_PM; ++p) M[p] = Mn[p];
-            load_maps(n + AT_GROUPS);
-            const float* spm = nullptr;
+        int64_t next_n = g;
+        load_maps(next_n);
+        for (int64_t ti = 0; ok && ti < ntile_cta; ++ti) {
+            const float* spm_tile = nullptr;
             if (use_pm) {
-                ok = ok && !*abort_flag && mbar_wait(&pm_full[ti & 1], (uint32_t)((ti >> 1) & 1), abort_flag, a.err);
+                ok = !*abort_flag && mbar_wait(&pm_full[ti & 1], (uint32_t)((ti >> 1) & 1), abort_flag, a.err);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
-                if (in) spm = sPM + (int64_t)(ti & 1) * a.n_pair * 128 + xl;
+                spm_tile = sPM + (int64_t)(ti & 1) * a.n_pair * 128 + xl;
             }
+            for (; next_n < n_tm && next_n / nbq == ti; ) {
+                const int64_t n = next_n;
+                next_n += AT_GROUPS;
+                const int64_t tile = tile0 + ti * a.G;
+                const int b = b0 + (int)(n % nbq);
+                const int64_t x = tile * 128 + xl;
+                const bool in = x < a.npix;
+                float M[AT_PM];
 #pragma unroll
-            for (int S = 0; S < AT_NST; ++S) {
-                if (u > 0) {                              // the group's previous stage is consumed
-                    ok = ok && !*abort_flag && mbar_wait(&mma_done[g], (u - 1) & 1, abort_flag, a.err);
-                    ok = __all_sync(0xffffffffu, ok);
-                    if (!ok) break;
-                    tc_fence_after();
-                    if (S == 0 && have_prev) epilogue();
-                }
-                if (S == 0) at_stage<0, 0, FULL>(M, spm, rows, lane_base + colA);
-                else if (S == 1) at_stage<1, 0, FULL>(M, spm, rows, lane_base + colA);
-                else at_stage<2, 0, FULL>(M, spm, rows, lane_base + colA);
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&a_full[g]);
-                    if (S == AT_NST - 1 && use_pm) mbar_arrive(&pm_empty[ti & 1]);   // this warp is done with the tile's means
-                }
-                if (leader) {
-                    bool go = mbar_wait(&a_full[g], u & 1, abort_flag, a.err);
-                    if (go && u == 0) go = mbar_wait(&hbar, 0, abort_flag, a.err);
-                    if (go) {
+                for (int p = 0; p < AT_PM; ++p) M[p] = Mn[p];
+                load_maps(next_n);
+                const float* spm = in ? spm_tile : nullptr;
+#pragma unroll
+                for (int S = 0; S < AT_NST; ++S) {
+                    if (u > 0) {                          // the group's previous stage is consumed
+                        ok = ok && !*abort_flag && mbar_wait(&mma_done[g], (u - 1) & 1, abort_flag, a.err);
+                        ok = __all_sync(0xffffffffu, ok);
+                        if (!ok) break;
                         tc_fence_after();
-                        const uint32_t bh0 = smem_u32(sB + (int64_t)(b - b0) * AT_BMAP + S * 2 * AT_BT);
-                        const uint32_t dcol = tmem + colD;
-#pragma unroll
-                        for (int i = 0; i < AT_SK / 8; ++i) {
-                            const uint32_t ah = tmem + colA + i * 8, al = ah + AT_SK;
-                            const uint64_t bh = at_bdesc(bh0 + i * 256), bl = at_bdesc(bh0 + AT_BT + i * 256);
-                            at_mma(dcol, ah, bh, idesc, (S == 0 && i == 0) ? 0u : 1u);
-                            at_mma(dcol, ah, bl, idesc, 1u);
-                            at_mma(dcol, al, bh, idesc, 1u);
-                        }
+                        if (S == 0 && have_prev) epilogue();
                     }
-                    umma_commit(&mma_done[g]);            // also on abort: keeps the phases in step
+                    if (S == 0) at_stage<0, 0, FULL>(M, spm, rows, lane_base + colA);
+                    else if (S == 1) at_stage<1, 0, FULL>(M, spm, rows, lane_base + colA);
+                    else at_stage<2, 0, FULL>(M, spm, rows, lane_base + colA);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&a_full[g]);
+                    if (leader) {
+                        bool go = mbar_wait(&a_full[g], u & 1, abort_flag, a.err);
+                        if (go && u == 0) go = mbar_wait(&hbar, 0, abort_flag, a.err);
+                        if (go) {
+                            tc_fence_after();
+                            const uint32_t bh0 = smem_u32(sB + (int64_t)(b - b0) * AT_BMAP + S * 2 * AT_BT);
+                            const uint32_t dcol = tmem + colD;
+#pragma unroll
+                            for (int i = 0; i < AT_SK / 8; ++i) {
+                                const uint32_t ah = tmem + colA + i * 8, al = ah + AT_SK;
+                                const uint64_t bh = at_bdesc(bh0 + i * 256), bl = at_bdesc(bh0 + AT_BT + i * 256);
+                                at_mma(dcol, ah, bh, idesc, (S == 0 && i == 0) ? 0u : 1u);
+                                at_mma(dcol, ah, bl, idesc, 1u);
+                                at_mma(dcol, al, bh, idesc, 1u);
+                            }
+                        }
+                        umma_commit(&mma_done[g]);        // also on abort: keeps the phases in step
+                    }
+                    __syncwarp();
+                    ++u;
                 }
-                __syncwarp();
-                ++u;
+                if (!ok) break;
+                have_prev = true;
+                prev_x = x;
+                prev_b = b;
             }
             if (!ok) break;
-            have_prev = true;
-            prev_x = x;
-            prev_b = b;
+            // this warp's last read of the tile's pair means is done (its stores to TMEM waited)
+            if (use_pm && lane == 0) mbar_arrive(&pm_empty[ti & 1]);
         }
         if (ok && have_prev) {
             ok = mbar_wait(&mma_done[g], (u - 1) & 1, abort_flag, a.err);

@@ -480,3 +480,30 @@ def test_wmap_resolution_workload():
     err = _rel(beta, ref)
     print("WMAP-resolution workload (lmax=500, P=10) fp16x3: beta rel err %.3g" % err)
     assert err <= 1e-5
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nb", [1, 3, 5])
+def test_backward_few_maps_with_pixel_means(prec, nb):
+    """The adjoint with per-pixel pair means for 1, 3 and 5 maps, 12 modes: the tensor-core
+    pixel-weight kernel gives each CTA a quad of maps, so with fewer maps than converter
+    groups several pixel tiles are in flight at once on its two pair-mean buffers."""
+    M = _cuda_or_skip()
+    L, P, R, nphi = 60, 12, 61, 128
+    basis, cl, alm = _case(L, P, nb, seed=81 + nb)
+    mask = simgen.band_mask(R, 20.0)
+    plan = _plan(M, L, P, basis, cl, R, nphi, prec, ring_mask=mask)
+    sims = simgen.gaussian_alm(cl, 4, seed=82, stream=simgen.STREAM_LINEAR).astype(np.complex64)
+    plan.linear_term(torch.from_numpy(sims).cuda(), finalize=True)
+    g = np.random.default_rng(83).standard_normal((nb, plan.n_max))
+    grad = plan.backward(torch.from_numpy(alm).cuda(), torch.from_numpy(g).cuda(), True).cpu().numpy()
+    plan.sync()
+    plan.close()
+    mu, w = osh.gl_nodes(R)
+    filt = osh.filter_table(basis, cl)
+    pm = om.pair_means(list(osh.synthesize_many(sims.astype(np.complex128), L, filt, mu, nphi)))
+    for b in range(nb):
+        ref = om.adjoint_grad(alm[b].astype(np.complex128), g[b], L, filt, mu, w, nphi, mask, pm)
+        err = _rel(grad[b], ref)
+        print("adjoint lmax=%d P=%d %s %d maps, map %d: grad rel err %.3g" % (L, P, prec, nb, b, err))
+        assert err <= 1e-5
