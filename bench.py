@@ -154,25 +154,35 @@ def legendre_flops(P, lmax, nrings):
 # per launch); an entry is removed whenever its kernel changes until it is captured again.
 STAGE_TRAFFIC_GB = {
     ("fp16x3", 2000, 4096, 16, 32): {
-        "legendre": 19.67 + 16.39, "pair_means": 25.71 + 8.88, "ring_c2r": 16.53 + 16.74, "adjoint_pixel": 27.28 + 16.74,
+        "legendre": 19.67 + 16.39, "pair_means": 25.71 + 8.88, "ring_c2r": 16.53 + 16.74,
         "ring_r2c": 17.45 + 16.82, "legendre_adjoint": 26.19 + 0.52,
         "legendre_prep": 0.51 + 8.40, "cubic": 17.84 + 0.11,
     },
 }
 
 
-def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps, peaks, nsynth=3):
+def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps, peaks, nsynth=3, probe=None):
     """Roofline of every timed stage: algorithmic work per step (flops or bytes) over the
     stage's live CUDA-event time, against its peak; sorted by time, largest first.
     nsynth: syntheses per chunk (linear term, cubic, and the adjoint unless it reuses the
     cubic's maps)."""
     R_half, L1, npix = (R + 1) // 2, L + 1, R * nphi
     n_alm = (L + 1) * (L + 2) // 2
+    probe = probe or {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     bf16 = peaks.get("bf16_tflops_sustained", 1710.9)
-    fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    # FP32 SIMT and tf32 tensor rates: the library's probes in this run where available
+    # (modal_peak_probe), else derived (lanes x clock) and the bf16 rate / 2 by nominal ratio
+    fp32 = probe.get("fp32_simt") or 152 * 128 * 2 * 2.07e9 / 1e12
+    fp32_src = ("measured in this run: packed f32x2 FMA probe" if probe.get("fp32_simt")
+                else "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
+    tf32 = probe.get("tf32_tensor") or bf16 / 2.0
+    tf32_src = ("measured in this run: tcgen05 kind::tf32 probe (M128 N256) / 3 products" if probe.get("tf32_tensor")
+                else "measured bf16 sustained / 2 (tf32) / 3 products")
     split = {"fp16x3": 3.0, "bf16x3": 3.0, "3xtf32": 6.0, "bf16": 1.0}
     tensor_peak = bf16 / split[prec] if prec in split else None
+    if prec == "3xtf32" and probe.get("tf32_tensor"):
+        tensor_peak = tf32 / 3.0
     launches = B // chunk
     delta_bytes = chunk * P * R_half * L1 * 16.0                  # E and O rows, complex64
     map_bytes = chunk * P * npix * 4.0
@@ -200,14 +210,13 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
             peak, unit, achieved = hbm, "GB/s", total / (ms / 1e3) / 1e9
             src = "measured HBM copy"
         elif bound == "tensor":
-            tf32x3 = stage in ("linear_gemm", "adjoint_pixel")               # these run 3xTF32
-            tp = bf16 / 6.0 if tf32x3 else tensor_peak
+            tf32x3 = stage in ("linear_gemm", "adjoint_pixel") or prec == "3xtf32"   # these run 3xTF32
+            tp = tf32 / 3.0 if tf32x3 else tensor_peak
             peak, unit, achieved = tp, "TFLOP/s", total / (ms / 1e3) / 1e12
-            src = "measured bf16 sustained / %s" % ("2 (tf32) / 3 products" if tf32x3
-                                                    else "%g products per useful MAC" % split[prec])
+            src = tf32_src if tf32x3 else "measured bf16 sustained / %g products per useful MAC" % split[prec]
         else:
             peak, unit, achieved = fp32, "TFLOP/s", total / (ms / 1e3) / 1e12
-            src = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+            src = fp32_src
         t = traffic.get(stage)
         if achieved > peak:
             # the peaks are a torch copy kernel and cuBLAS, not hard ceilings: a kernel that
@@ -369,6 +378,16 @@ def run_gpu(args):
         ms = max_over_ranks(ms, dev)
         return ms, prof
 
+    # roofline denominators the driver does not measure: FP32 SIMT, FP64 SIMT, tcgen05 tf32
+    # and f16 rates, each probed once on this GPU before the timed region
+    probe = {}
+    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor"):
+        try:
+            probe[kind] = round(M.modal_peak_probe(kind), 2)
+        except M.ModalError as e:
+            probe[kind + "_error"] = str(e)[:120]
+    torch.cuda.synchronize()
+
     K, W = args.steps, args.warmup
     with ClockSampler(local) as clocks:
         ms, prof_plain_timing = timed(plan, alm, K, W)
@@ -387,13 +406,15 @@ def run_gpu(args):
         other = {"adjoint_maps": "synthesised again" if retain else "kept from the step's cubic call",
                  "value": round(job_throughput(B, K, world, oms), 3), "ms_per_step": round(oms / K, 3)}
 
+    # the headline step's beta of map 0 (the step's coefficient pass, linear term on)
+    beta_headline = beta[0].double().cpu().numpy().copy() if args.lmax == WORKLOAD["lmax"] else None
     value = job_throughput(B, K, world, ms)
     e2e_value = job_throughput(B, K, world, e2e_ms)
     n_prof_steps = max(1, K // 2)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     rooflines = stage_rooflines(prec, L, R, nphi, P, plan.n_max, plan.n_pair, min(B, args.chunk), B, prof,
-                                n_prof_steps, peaks, nsynth=2 if retain else 3)
+                                n_prof_steps, peaks, nsynth=2 if retain else 3, probe=probe)
     top = rooflines[0]
     roof = {k: top[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "peak_source")}
     if top["traffic"] is not None:
@@ -419,12 +440,25 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(alm.numel() * 8), "d2h_bytes_per_step": int(B * 8 + 8)},
         "roofline": roof,
         "rooflines": rooflines,
+        "peak_probes_tflops": probe,
         "other_adjoint": other,
         "stage_ms_per_step": {k: round(v[0] / n_prof_steps, 3) for k, v in prof.items() if v[1]},
     }
 
     # the plain comparators time through the same barrier / max-over-ranks path, so they run
     # only in single-process runs (under torchrun rank 0 would wait on ranks that have left)
+    if rank == 0 and world == 1 and args.lmax == WORKLOAD["lmax"]:
+        # the batched Monte Carlo configuration (l_max 500/1000/2000, 2:1:1, one captured graph),
+        # timed on the same GPU after the headline step's plan is released
+        plan.close()
+        try:
+            mv, mms, ml, mclk, mn = mixed_measure(M, dev, prec, args.chunk, max(2, K // 2), 2)
+            result["mixed_workload"] = {
+                "metric": "maps/s, mixed l_max 500/1000/2000 (2:1:1) coefficient pass with linear term, P=16",
+                "value": round(mv, 3), "unit": "maps/s", "ms_per_step": round(mms, 3), "maps_per_step": mn,
+                "steps": max(2, K // 2), "gpu_launches_per_step": int(ml), "clocks": mclk}
+        except Exception as e:          # the headline line is printed whatever happens here
+            result["mixed_workload"] = {"error": str(e)[:200]}
     if rank == 0 and world == 1 and not args.no_baseline and prec != "fp32":
         plan.close()
         plain = make_plan("fp32")
@@ -444,7 +478,7 @@ def run_gpu(args):
             result["plain_one_map_error"] = str(e)[:200]
         plain.close()
     if rank == 0 and world == 1 and not args.no_baseline:
-        result["cpu_baseline"], result["parity"] = cpu_baseline(args.cpu_rings, prec)
+        result["cpu_baseline"], result["parity"] = cpu_baseline(args.cpu_rings, prec, beta_headline)
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
@@ -508,13 +542,43 @@ def gpu_beta_error(prec, sample, seed=4):
     return float(np.linalg.norm(beta - ref) / np.linalg.norm(ref))
 
 
-def cpu_baseline(nring_sample, prec=None):
+def oracle_map_seconds(L, R, nphi, P, nring_sample=None, seed=5):
+    """Seconds per map of the oracle's per-map step (synthesis, pair means, cubic with the
+    linear term, adjoint) at l_max = L on an R x nphi grid, on all rings or on a sample of
+    them spread pole to equator and extrapolated by ring count."""
+    import simgen
+    from oracle import modal as om, sht as osh
+    basis, cl = simgen.shifted_legendre_basis(L, P), simgen.cl_model(L)
+    filt = osh.filter_table(basis, cl)
+    a = simgen.gaussian_alm(cl, 1, seed=seed)[0]
+    mu, w = osh.gl_nodes(R)
+    rings = np.arange(R) if nring_sample is None else np.unique(np.linspace(0, R // 2, nring_sample).astype(int))
+    t0 = time.perf_counter()
+    maps = osh.synthesize(a, L, filt, mu[rings], nphi)
+    pm = om.pair_means([maps])
+    beta = om.cubic_beta(maps, om.pixel_weights(w[rings], nphi), pm)
+    om.adjoint_grad(a, np.ones(beta.size) / beta.size, L, filt, mu[rings], w[rings], nphi, None, pm)
+    return (time.perf_counter() - t0) * R / len(rings)
+
+
+FULLGRID_GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_beta_l2000_p16.json")
+
+
+def cpu_baseline(nring_sample, prec=None, beta_headline=None):
     """The oracle timed on a bounded sample; with prec, also the GPU's beta on that sample
-    against the oracle's (the accepted error metric, tolerance 1e-5)."""
+    against the oracle's (the accepted error metric, tolerance 1e-5), and, with the headline
+    step's beta of its first map, that beta against the stored full-grid oracle result."""
     dt, per_map, k, sample = oracle_step_sample(nring_sample)
     base = {"value": round(1.0 / per_map, 8), "unit": "maps/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": "1 map at lmax=2000 (P=16, 4096 longitudes) on %d of 2001 rings: synthesis, pair means, "
                       "cubic with linear term, adjoint; %.1f s, extrapolated by ring count" % (k, dt)}
+    try:
+        base["seconds_per_map"] = {
+            "lmax32_P6_33x128_full_grid": round(oracle_map_seconds(32, 33, 128, 6), 4),
+            "lmax500_P10_501x1024_64_rings_extrapolated": round(oracle_map_seconds(500, 501, 1024, 10, 64), 3),
+            "lmax2000_P16_2001x4096_%d_rings_extrapolated" % k: round(per_map, 1)}
+    except Exception as e:              # the measurement line is printed whatever happens here
+        base["seconds_per_map_error"] = str(e)[:200]
     if prec is None:
         return base, None
     parity = {"metric": "||beta_gpu - beta_oracle||_2 / ||beta_oracle||_2", "tol": 1e-5, "precision": prec,
@@ -525,45 +589,46 @@ def cpu_baseline(nring_sample, prec=None):
         parity.update(beta_rel_err=float("%.3g" % err), ok=bool(err <= 1e-5))
     except Exception as e:          # the measurement line is printed whatever happens here
         parity.update(error=str(e)[:200])
+    if beta_headline is not None and os.path.exists(FULLGRID_GOLDEN):
+        ref = np.array(json.load(open(FULLGRID_GOLDEN))["beta_lin_G"])
+        fe = float(np.linalg.norm(beta_headline - ref) / np.linalg.norm(ref))
+        parity["full_grid"] = {"beta_rel_err": float("%.3g" % fe), "ok": bool(fe <= 1e-5),
+                               "sample": "the headline step's map 0 (seed 3) with the linear term of its 2 "
+                                         "simulations (seed 4), every pixel of the 2001 x 4096 grid, against the "
+                                         "oracle result stored by tests/golden/make_fullsize.py"}
     return base, parity
 
 
-def run_mixed(args):
+MIXED = [(500, 256), (1000, 128), (2000, 128)]      # (l_max, maps per step): the 2:1:1 batched mix
+
+
+def mixed_measure(M, dev, prec, chunk, steps, warmup, rank=0, world=1, local=0):
     """Batched Monte Carlo coefficient pass: 256 maps at l_max = 500, 128 at 1000 and 128 at
     2000 per step (P = 16, 20-degree band mask, linear term), one plan per l_max grouped in a
-    modal batch and replayed as one CUDA graph."""
+    modal batch and replayed as one CUDA graph.  Returns (maps/s, ms per step, kernels per
+    step, clock summary, maps per step)."""
     import torch
-    import torch.distributed as dist
-
     import simgen
-    import paper_1105_2791_gb300 as M
 
-    rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     P = 16
-    prec = "fp16x3" if args.prec == "auto" else args.prec
-    mix = [(500, 256), (1000, 128), (2000, 128)]
     plans, alms = [], []
-    for i, (L, nb) in enumerate(mix):
+    for i, (L, nb) in enumerate(MIXED):
         R, nphi = L + 1, 1 << int(math.ceil(math.log2(2 * L + 2)))
         cl = simgen.cl_model(L)
         pl = M.Plan(L, P, simgen.shifted_legendre_basis(L, P), cl, R, nphi, prec=prec,
                     ring_mask=simgen.band_mask(R, 20.0))
-        pl.set_chunk(min(args.chunk, nb))
+        pl.set_chunk(min(chunk, nb))
         pl.linear_term(torch.from_numpy(simgen.gaussian_alm(cl, 4, seed=50 + i, stream=simgen.STREAM_LINEAR)
                                         .astype(np.complex64)).to(dev), finalize=True)
         plans.append(pl)
         alms.append(torch.from_numpy(simgen.gaussian_alm(cl, nb, seed=60 + i + 1000 * rank).astype(np.complex64)).to(dev))
     batch = M.Batch(plans)
-    n_maps = sum(nb for _, nb in mix)
-    K, W = args.steps, args.warmup
-    for _ in range(W):
+    n_maps = sum(nb for _, nb in MIXED)
+    for _ in range(warmup):
         batch.cubic(alms, use_linear=True, graph=True)
     torch.cuda.synchronize()
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     for pl in plans:
         M.modal_get_profile(pl.h)
@@ -571,12 +636,12 @@ def run_mixed(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         ev0.record(st)
-        for _ in range(K):
+        for _ in range(steps):
             batch.cubic(alms, use_linear=True, graph=True)
         ev1.record(st)
         torch.cuda.synchronize()
     ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
-    value = job_throughput(n_maps, K, world, ms)
+    value = job_throughput(n_maps, steps, world, ms)
     # kernels per step: one direct (uncaptured) pass, counted by the plans
     for pl in plans:
         M.modal_get_profile(pl.h)
@@ -585,23 +650,41 @@ def run_mixed(args):
     launches = sum(sum(n for (_, n) in M.modal_get_profile(pl.h).values()) for pl in plans)
     for pl in plans:
         pl.sync()
+    batch.close()
+    for pl in plans:
+        pl.close()
+    return value, ms / steps, launches, clocks.summary(), n_maps
+
+
+def run_mixed(args):
+    """The batched Monte Carlo configuration as the timed workload (its own metric line)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1105_2791_gb300 as M
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = "fp16x3" if args.prec == "auto" else args.prec
+    K, W = args.steps, args.warmup
+    value, ms, launches, clk, n_maps = mixed_measure(M, dev, prec, args.chunk, K, W, rank, world, local)
     if rank == 0:
         print(json.dumps({
             "metric": "maps/s, mixed l_max 500/1000/2000 (2:1:1) coefficient pass with linear term, P=16",
             "value": round(value, 3), "unit": "maps/s", "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": round(ms / K, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "3xtf32": "tf32x3", "fp16x3": "f16x3", "bf16x3": "bf16x3", "bf16": "bf16"}[prec],
             "data": "synthetic",
             "config": {"workload": "batched Monte Carlo: 256 @ l_max 500, 128 @ 1000, 128 @ 2000 per step, "
                                    "P=16, band mask, one captured CUDA graph", "maps_per_step": n_maps,
                        "precision": prec, "l2": "inputs and intermediates > L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "clocks": clocks.summary(), "gpu_launches": int(launches) * K,
+            "clocks": clk, "gpu_launches": int(launches) * K,
             "roofline": None, "e2e": None,
         }), flush=True)
-    batch.close()
-    for pl in plans:
-        pl.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -660,12 +743,24 @@ def run_trispectrum(args):
         M.modal_set_profiling(plan.h, False)
         return max_over_ranks(ev0.elapsed_time(ev1), dev), prof
 
+    # roofline denominators the driver does not measure: FP32 SIMT, FP64 SIMT, tcgen05 tf32
+    # and f16 rates, each probed once on this GPU before the timed region
+    probe = {}
+    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor"):
+        try:
+            probe[kind] = round(M.modal_peak_probe(kind), 2)
+        except M.ModalError as e:
+            probe[kind + "_error"] = str(e)[:120]
+    torch.cuda.synchronize()
+
     K, W = args.steps, args.warmup
     with ClockSampler(local) as clocks:
         ms, prof0 = timed(alm, K, W)
     n_prof = max(1, K // 2)
     _, prof = timed(alm, n_prof, 1, profile=True)
     e2e_ms, _ = timed(torch.empty_like(alm), K, 1, e2e=True)
+    # the headline step's beta of map 0 (the step's coefficient pass, linear term on)
+    beta_headline = beta[0].double().cpu().numpy().copy() if args.lmax == WORKLOAD["lmax"] else None
     value = job_throughput(B, K, world, ms)
     q_ms, q_n = prof["quartic"]
     npix = R * nphi

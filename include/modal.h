@@ -280,6 +280,14 @@ modal_status modal_selftest_wait(modal_h h, int spin_limit, void* stream);
 modal_status modal_cubic_static(const float* maps, const float* W, long long npix, int P, int B,
                                 double* beta, void* stream);
 
+/* Throughput probes for roofline denominators (not part of the estimator): kind 0 = FP32
+ * SIMT (packed f32x2 FMA), 1 = FP64 SIMT, 2 = tcgen05 tf32, 3 = tcgen05 f16 (M = 128,
+ * N = 256, FP32 accumulate, operands in shared memory).  Runs a fixed amount of independent
+ * work on every SM of the current device (a few ms) and writes the rate in TFLOP/s
+ * (a multiply-add counts 2).  MODAL_EINVAL for another kind; MODAL_ETIMEOUT if the
+ * tensor-core wait gave up.  Synchronises `stream`. */
+modal_status modal_peak_probe(int kind, double* tflops, void* stream);
+
 /* Per-stage timing.  With profiling enabled every kernel launch of the plan is
  * bracketed by CUDA events recorded on the launching stream.  modal_get_profile
  * synchronises, writes for each stage s < nstages the summed event time in ms

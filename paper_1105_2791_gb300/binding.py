@@ -32,7 +32,7 @@ EXPORTS = [
     "modal_last_error", "modal_set_profiling", "modal_get_profile", "modal_stage_name", "modal_cubic_static",
     "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
     "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate", "modal_quartic",
-    "modal_set_retain_maps", "modal_backward_retained", "modal_fnl_weights",
+    "modal_set_retain_maps", "modal_backward_retained", "modal_fnl_weights", "modal_peak_probe",
 ]
 MODAL_NSTAGES = 15
 
@@ -81,6 +81,7 @@ def load_library():
         "modal_cov_accumulate": [H, c_void_p, c_int, c_void_p],
         "modal_solve": [H, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
         "modal_fnl_weights": [H, c_void_p, c_void_p, c_void_p, c_void_p],
+        "modal_peak_probe": [c_int, c_void_p, c_void_p],
         "modal_bivector_fit": [H, c_void_p, c_void_p, c_void_p, c_void_p],
         "modal_solve_bivector": [H, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
         "modal_bivector_rotate": [H, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p],
@@ -245,6 +246,16 @@ def modal_fnl_weights(h, alpha, w, stream=None):
     sigma = c_double(0.0)
     _check(load_library().modal_fnl_weights(h, a_ptr, _dev(w), byref(sigma), _stream(stream)))
     return sigma.value
+
+
+PEAK_KINDS = {"fp32_simt": 0, "fp64_simt": 1, "tf32_tensor": 2, "f16_tensor": 3}
+
+
+def modal_peak_probe(kind, stream=None):
+    """Measured throughput (TFLOP/s) of one of PEAK_KINDS on the current device."""
+    v = c_double(0.0)
+    _check(load_library().modal_peak_probe(int(PEAK_KINDS.get(kind, kind)), byref(v), _stream(stream)))
+    return v.value
 
 
 def modal_bivector_fit(h, zeta0, stream=None):

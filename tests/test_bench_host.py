@@ -110,3 +110,19 @@ def test_clock_record_flags_slowdowns():
 def test_job_throughput_is_whole_job_maps_per_second():
     assert bench.job_throughput(32, 4, 1, 160.0) == pytest.approx(32 * 4 / 0.160)
     assert bench.job_throughput(32, 4, 8, 160.0) == pytest.approx(8 * 32 * 4 / 0.160)
+
+
+def test_probed_peaks_replace_the_derived_ones():
+    """With the library's throughput probes of this run, the FP32-SIMT stages use the probed
+    FP32 rate and the 3xTF32 stages a third of the probed tf32 tensor rate; the split-FP16
+    stages keep the driver's sustained bf16 figure."""
+    probe = {"fp32_simt": 70.0, "tf32_tensor": 900.0}
+    rows = _by_stage(bench.stage_rooflines("fp16x3", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,
+                                           probe=probe))
+    assert rows["cubic"]["peak"] == pytest.approx(70.0)
+    assert rows["linear_gemm"]["peak"] == pytest.approx(300.0) and rows["adjoint_pixel"]["peak"] == pytest.approx(300.0)
+    assert rows["legendre"]["peak"] == pytest.approx(1710.9 / 3, rel=1e-3)
+    assert "measured in this run" in rows["cubic"]["peak_source"]
+    tf = _by_stage(bench.stage_rooflines("3xtf32", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,
+                                         probe=probe))
+    assert tf["legendre"]["peak"] == pytest.approx(300.0)

@@ -105,3 +105,50 @@ def test_graph_is_recaptured_after_a_plan_changes():
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_mixed_lmax_batch_at_size_against_oracle():
+    """The batched Monte Carlo configuration's plans, l_max = 500, 1000 and 2000 on their
+    (l_max + 1) x next-pow2 grids with 16 modes (816 coefficients), band mask and linear term,
+    maps in the ratio 2:1:1, captured as one graph and replayed, against the oracle summed
+    over 3 sampled unmasked rings of each plan (a ring mask selects them on the GPU)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1105_2791_gb300 as M
+    P = 16
+    plans, alms, sims, setups = [], [], [], []
+    for i, (L, nb) in enumerate([(500, 4), (1000, 2), (2000, 2)]):
+        R, nphi = L + 1, 1 << int(np.ceil(np.log2(2 * L + 2)))
+        band = simgen.band_mask(R, 20.0)
+        ok = np.nonzero(band[: (R + 1) // 2] > 0)[0]
+        rings = ok[[0, len(ok) // 2, len(ok) - 1]]
+        sel = np.zeros(R)
+        sel[rings] = 1.0
+        basis, cl = simgen.shifted_legendre_basis(L, P), simgen.cl_model(L)
+        plan = M.Plan(L, P, basis, cl, R, nphi, prec="fp16x3", ring_mask=sel)
+        s = simgen.gaussian_alm(cl, 4, seed=110 + i, stream=simgen.STREAM_LINEAR).astype(np.complex64)
+        plan.linear_term(torch.from_numpy(s).cuda(), finalize=True)
+        a = simgen.gaussian_alm(cl, nb, seed=120 + i).astype(np.complex64)
+        plans.append(plan)
+        sims.append(s)
+        alms.append(torch.from_numpy(a).cuda())
+        setups.append((L, R, nphi, basis, cl, rings, a))
+    batch = M.Batch(plans)
+    batch.cubic(alms, use_linear=True, graph=True)                      # capture
+    out = [o.clone().cpu().numpy() for o in batch.cubic(alms, use_linear=True, graph=True)]   # replay
+    for p in plans:
+        p.sync()
+    batch.close()
+    for p in plans:
+        p.close()
+    for (L, R, nphi, basis, cl, rings, a), s, beta in zip(setups, sims, out):
+        mu, w = osh.gl_nodes(R)
+        filt = osh.filter_table(basis, cl)
+        W = om.pixel_weights(w[rings], nphi)
+        pm = om.pair_means(list(osh.synthesize_many(s.astype(np.complex128), L, filt, mu[rings], nphi)))
+        maps = osh.synthesize_many(a.astype(np.complex128), L, filt, mu[rings], nphi)
+        for b in range(a.shape[0]):
+            err = float(np.linalg.norm(beta[b] - om.cubic_beta(maps[b], W, pm)) /
+                        np.linalg.norm(om.cubic_beta(maps[b], W, pm)))
+            print("mixed batch l_max=%d map %d: beta rel err %.3g" % (L, b, err))
+            assert err <= 1e-5
