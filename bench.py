@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--batch", type=int, default=32, help="maps per step per GPU")
     ap.add_argument("--prec", default="auto", help="fp32 | 3xtf32 | fp16x3 | bf16x3 | bf16 | auto")
-    ap.add_argument("--no-baseline", action="store_true", help="skip the plain FP32 comparison and CPU baseline")
+    ap.add_argument("--no-baseline", action="store_true",
+                    help="skip the plain FP32 comparison, the CPU baseline and the mixed-workload key")
     ap.add_argument("--cpu-rings", type=int, default=8, help="rings in the CPU-baseline sample")
     ap.add_argument("--lmax", type=int, default=2000, help="smaller l_max for profiler captures only")
     ap.add_argument("--chunk", type=int, default=32, help="maps per internal pass of the library")
@@ -447,7 +448,7 @@ def run_gpu(args):
 
     # the plain comparators time through the same barrier / max-over-ranks path, so they run
     # only in single-process runs (under torchrun rank 0 would wait on ranks that have left)
-    if rank == 0 and world == 1 and args.lmax == WORKLOAD["lmax"]:
+    if rank == 0 and world == 1 and args.lmax == WORKLOAD["lmax"] and not args.no_baseline:
         # the batched Monte Carlo configuration (l_max 500/1000/2000, 2:1:1, one captured graph),
         # timed on the same GPU after the headline step's plan is released
         plan.close()
@@ -460,7 +461,7 @@ def run_gpu(args):
         except Exception as e:          # the headline line is printed whatever happens here
             result["mixed_workload"] = {"error": str(e)[:200]}
     if rank == 0 and world == 1 and not args.no_baseline and prec != "fp32":
-        plan.close()
+        plan.close()                    # (a no-op when the mixed workload already released it)
         plain = make_plan("fp32")
         plain.cov_accumulate(torch.randn((2 * plain.n_max, plain.n_max), generator=gen, device=dev,
                                          dtype=torch.float64))
