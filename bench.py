@@ -219,6 +219,13 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
             peak, unit, achieved = fp32, "TFLOP/s", total / (ms / 1e3) / 1e12
             src = fp32_src
         t = traffic.get(stage)
+        extra = {}
+        if stage == "adjoint_pixel" and bound == "tensor" and probe.get("tf32_tensor_n16"):
+            # the same product against the tensor pipe's measured rate at its own instruction
+            # shape (M = 128, N = 16): the ceiling of a kernel that issues N = 16 MMAs
+            sp = probe["tf32_tensor_n16"] / 3.0
+            extra = {"shape_peak": round(sp, 1), "shape_frac": round(achieved / sp, 4),
+                     "shape_peak_source": "measured in this run: tcgen05 kind::tf32 probe (M128 N16) / 3 products"}
         if achieved > peak:
             # the peaks are a torch copy kernel and cuBLAS, not hard ceilings: a kernel that
             # streams well can exceed them slightly; flagged, not capped
@@ -228,7 +235,7 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
                     "traffic": round(t, 2) if t is not None else None,
                     "ms_per_step": round(ms, 3), "launches_per_step": nl,
                     "per_launch": "%.4g %s" % (per_launch / (1e9 if bound == "hbm" else 1.0),
-                                               "GB" if bound == "hbm" else "flop")})
+                                               "GB" if bound == "hbm" else "flop"), **extra})
     out.sort(key=lambda r: -r["ms_per_step"])
     return out
 
@@ -380,9 +387,10 @@ def run_gpu(args):
         return ms, prof
 
     # roofline denominators the driver does not measure: FP32 SIMT, FP64 SIMT, tcgen05 tf32
-    # and f16 rates, each probed once on this GPU before the timed region
+    # and f16 rates (and tf32 at the adjoint's N = 16), each probed once on this GPU before
+    # the timed region
     probe = {}
-    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor"):
+    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor", "tf32_tensor_n16"):
         try:
             probe[kind] = round(M.modal_peak_probe(kind), 2)
         except M.ModalError as e:
@@ -745,9 +753,10 @@ def run_trispectrum(args):
         return max_over_ranks(ev0.elapsed_time(ev1), dev), prof
 
     # roofline denominators the driver does not measure: FP32 SIMT, FP64 SIMT, tcgen05 tf32
-    # and f16 rates, each probed once on this GPU before the timed region
+    # and f16 rates (and tf32 at the adjoint's N = 16), each probed once on this GPU before
+    # the timed region
     probe = {}
-    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor"):
+    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor", "tf32_tensor_n16"):
         try:
             probe[kind] = round(M.modal_peak_probe(kind), 2)
         except M.ModalError as e:

@@ -33,7 +33,15 @@
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *    asynchronous on that stream except modal_init, modal_solve, modal_sync,
  *    the getters and state I/O, which synchronise.
- *  - A plan is not thread-safe; concurrent calls on one plan race.
+ *  - A plan is not thread-safe; calls on one plan whose work overlaps on the
+ *    GPU (different streams) race, with one exception: the FP64 solve family
+ *    (modal_solve, modal_fnl_weights) reads only the covariance sums and its
+ *    arguments and writes only its own stream-ordered workspace and its own
+ *    device error word, so it may run on a second stream beside modal_backward
+ *    or modal_backward_retained of the same plan, issued from the same host
+ *    thread, once the covariance sums it reads are complete on its stream (an
+ *    event).  With profiling on, the stage times of such overlapping calls
+ *    include each other's work.
  *  - Errors are returned as status codes and never abort; modal_last_error()
  *    gives a message for the calling thread's last failure.  Kernel faults
  *    surface as MODAL_ECUDA at the next synchronising call; a bounded device
@@ -98,7 +106,10 @@ typedef struct {
  * tables for the tensor-core precisions), the filter q_p(l)/sqrt(C_l) (zero where
  * C_l <= 0) and the pixel weights.  Sec. III.A (basis), Eq. legoestimator (filter).
  *   basis: host [P][lmax+1];  C_l: host [lmax+1];  1 <= P <= 16;  2 <= lmax <= 4000.
- * Synchronises.  On failure *out is NULL. */
+ * The tables stay resident (they grow as lmax^3: about 25 GB at lmax = 2000 for the
+ * tensor-core precisions); when they and the workspace of one map exceed the device's
+ * free memory, returns MODAL_ENOMEM before allocating anything, with the sizes in
+ * modal_last_error().  Synchronises.  On failure *out is NULL. */
 modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
                         const modal_grid* grid, int prec, modal_h* out);
 
@@ -282,7 +293,8 @@ modal_status modal_cubic_static(const float* maps, const float* W, long long npi
 
 /* Throughput probes for roofline denominators (not part of the estimator): kind 0 = FP32
  * SIMT (packed f32x2 FMA), 1 = FP64 SIMT, 2 = tcgen05 tf32, 3 = tcgen05 f16 (M = 128,
- * N = 256, FP32 accumulate, operands in shared memory).  Runs a fixed amount of independent
+ * N = 256, FP32 accumulate, operands in shared memory), 4 = tcgen05 tf32 at N = 16 (the
+ * shape of the adjoint's pixel-weight product).  Runs a fixed amount of independent
  * work on every SM of the current device (a few ms) and writes the rate in TFLOP/s
  * (a multiply-add counts 2).  MODAL_EINVAL for another kind; MODAL_ETIMEOUT if the
  * tensor-core wait gave up.  Synchronises `stream`. */

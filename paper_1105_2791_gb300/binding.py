@@ -248,7 +248,7 @@ def modal_fnl_weights(h, alpha, w, stream=None):
     return sigma.value
 
 
-PEAK_KINDS = {"fp32_simt": 0, "fp64_simt": 1, "tf32_tensor": 2, "f16_tensor": 3}
+PEAK_KINDS = {"fp32_simt": 0, "fp64_simt": 1, "tf32_tensor": 2, "f16_tensor": 3, "tf32_tensor_n16": 4}
 
 
 def modal_peak_probe(kind, stream=None):

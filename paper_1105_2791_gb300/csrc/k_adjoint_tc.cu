@@ -14,14 +14,16 @@
 // into tf32 hi + lo (both rounded to nearest) and stores them along the lane's columns with
 // tcgen05.st, so the operand never passes through shared memory.  B (H_b, split the same
 // way, core-matrix K-major layout) stays in shared memory for the CTA's 4 maps.
-// K runs in two stages of 72 pairs.  Three groups of four converter warps (one per TMEM
-// lane quarter) each own an A region of one stage (72 hi + 72 lo columns) and a 16-column
-// accumulator; a group converts a stage, its leader thread issues the 9 K-steps x 3
+// K runs in three stages of 48 pairs.  Four groups of four converter warps (one per TMEM
+// lane quarter) each own an A region of one stage (48 hi + 48 lo columns) and a 16-column
+// accumulator; a group converts a stage, its leader thread issues the 6 K-steps x 3
 // products (hi*hi, hi*lo, lo*hi, kind::tf32, A from TMEM) and commits to the group's
-// mbarrier; after the second stage the group reads its accumulator, scales by W_x and
+// mbarrier; after the third stage the group reads its accumulator, scales by W_x and
 // writes U in place over the maps (tile by tile; a tile's maps are read before its U is
-// written).  Groups work on different maps of a pixel tile at the same time, so the pair
-// means of the tile are fetched once from L2 and then hit in L1.
+// written).  The CTA's tile-maps (pixel tile, map of the quad) are dealt to the groups
+// round-robin, so with a full quad group g takes map g of every tile; a loader warp brings
+// each tile's pair means into shared memory by TMA (double-buffered), and every group walks
+// every tile of the CTA, so the pair-mean buffers' phases stay in step.
 //
 // Work: the CTA keeps one quad of maps (its B operands) and walks pixel tiles c / n_quads,
 // + G, ...; CTAs next to each other take the same tile for different quads.  Every wait is

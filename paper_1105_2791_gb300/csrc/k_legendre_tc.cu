@@ -433,6 +433,16 @@ size_t tc_b_workspace_bytes(const Plan& pl, int chunk) {
     return (size_t)groups * total * 2 * (16 * pl.P) * TC_KB;
 }
 
+size_t tc_table_bytes(const Plan& pl) {
+    if (pl.prec == MODAL_FP32) return 0;
+    const int KPS = kps_for(pl.prec);
+    const int64_t n_rt = (pl.R_half + 127) / 128;
+    int64_t total = 0;
+    for (int m = 0; m <= pl.lmax; ++m)
+        for (int pi = 0; pi < 2; ++pi) total += n_rt * tc_nkb(pl.lmax, m, pi, KPS);
+    return (size_t)total * TC_A_STAGE;
+}
+
 cudaError_t build_tc_tables(Plan& pl, cudaStream_t st) {
     const int L = pl.lmax;
     const int KPS = kps_for(pl.prec);

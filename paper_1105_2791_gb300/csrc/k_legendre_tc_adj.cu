@@ -374,6 +374,16 @@ size_t tc_adj_workspace_bytes(const Plan& pl, int chunk) {
     return (size_t)groups * (pl.lmax + 1) * 2 * nkb * 2 * (16 * pl.P) * TC_KB;
 }
 
+size_t tc_adj_table_bytes(const Plan& pl) {
+    if (pl.prec == MODAL_FP32) return 0;
+    const int L = pl.lmax;
+    const int64_t nkb = (pl.R_half + ta_kps(pl.prec) - 1) / ta_kps(pl.prec);
+    int64_t total = 0;
+    for (int m = 0; m <= L; ++m)
+        for (int pi = 0; pi < 2; ++pi) total += (int64_t)ta_nlt(L, m, pi) * nkb;
+    return (size_t)total * TC_A_STAGE;
+}
+
 cudaError_t build_tc_adj_tables(Plan& pl, cudaStream_t st) {
     const int L = pl.lmax;
     const int KPS = ta_kps(pl.prec);

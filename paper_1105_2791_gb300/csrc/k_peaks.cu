@@ -1,6 +1,7 @@
 // Throughput probes for the roofline denominators that no library kernel can supply:
 // the FP32 SIMT rate (packed f32x2 FMA), the FP64 SIMT rate, and the tcgen05 tensor rate
-// for tf32 and f16 inputs (M = 128, N = 256, FP32 accumulate, operands in shared memory).
+// for tf32 and f16 inputs (M = 128, N = 256, FP32 accumulate, operands in shared memory),
+// plus the tf32 rate at N = 16, the narrow shape of the adjoint's pixel-weight product.
 // Each probe runs a fixed amount of independent work on every SM and is timed with CUDA
 // events on the caller's stream; the result is the work over the elapsed time.
 #include "modal_internal.cuh"
@@ -48,16 +49,16 @@ __global__ void __launch_bounds__(PK_THREADS) k_peak_dfma(int iters, double* sin
     if (s == 1234.5) sink[threadIdx.x] = s;
 }
 
-// One CTA per SM: a single thread issues `iters` MMAs (M = 128, N = 256, K = 8 tf32 or 16
-// f16 per instruction) on zeroed shared-memory operands into one TMEM accumulator, then one
-// commit, and waits (bounded) for it before TMEM is freed.
-template <bool TF32>
+// One CTA per SM: a single thread issues `iters` MMAs (M = 128, N = 256 or 16, K = 8 tf32
+// or 16 f16 per instruction) on zeroed shared-memory operands into one TMEM accumulator,
+// then one commit, and waits (bounded) for it before TMEM is freed.
+template <bool TF32, int N>
 __global__ void __launch_bounds__(128, 1) k_peak_mma(int iters, int* err) {
     extern __shared__ __align__(1024) char pk_smem[];
     char* ops = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(pk_smem) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t done;
     __shared__ uint32_t tmem_slot;
-    constexpr int A_BYTES = 128 * 32, B_BYTES = 256 * 32;    // one K step (32 bytes of K per row)
+    constexpr int A_BYTES = 128 * 32, B_BYTES = N * 32;      // one K step (32 bytes of K per row)
     for (int i = threadIdx.x; i < (A_BYTES + B_BYTES) / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(ops)[i] = make_uint4(0, 0, 0, 0);
     if (threadIdx.x == 0) {
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(128, 1) k_peak_mma(int iters, int* err) {
             return d;
         };
         const uint64_t ad = desc(smem_u32(ops)), bd = desc(smem_u32(ops + A_BYTES));
-        const uint32_t idesc = umma_idesc(TF32 ? 2 : 0, 256);
+        const uint32_t idesc = umma_idesc(TF32 ? 2 : 0, N);
         for (int it = 0; it < iters; ++it) umma<TF32>(tmem, ad, bd, idesc, it == 0 ? 0u : 1u);
         umma_commit(&done);                              // one commit tracks every MMA issued above
         const long long t0 = clock64();
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(128, 1) k_peak_mma(int iters, int* err) {
 using namespace modal;
 
 extern "C" modal_status modal_peak_probe(int kind, double* tflops, void* stream) {
-    if (!tflops || kind < 0 || kind > 3) return set_error(MODAL_EINVAL, "kind in [0, 3] and tflops required");
+    if (!tflops || kind < 0 || kind > 4) return set_error(MODAL_EINVAL, "kind in [0, 4] and tflops required");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int dev = 0, nsm = 0;
     modal_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -132,16 +133,24 @@ extern "C" modal_status modal_peak_probe(int kind, double* tflops, void* stream)
             const int iters = 256;
             k_peak_dfma<<<nsm * 8, PK_THREADS, 0, st>>>(iters, static_cast<double*>(buf));
             flop = (double)nsm * 8 * PK_THREADS * iters * 16 * 8 * 2;
-        } else {                                         // tcgen05, tf32 (2) or f16 (3)
+        } else {                                         // tcgen05: tf32 (2), f16 (3), tf32 at N = 16 (4)
             const int iters = 65536;
-            const size_t smem = 1024 + 128 * 32 + 256 * 32;
-            const bool tf32 = kind == 2;
-            cudaError_t e = tf32 ? cudaFuncSetAttribute(k_peak_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                                 : cudaFuncSetAttribute(k_peak_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const int n = kind == 4 ? 16 : 256;
+            const size_t smem = 1024 + 128 * 32 + (size_t)n * 32;
+            const bool tf32 = kind != 3;
+            cudaError_t e;
+            if (kind == 2) {
+                e = cudaFuncSetAttribute(k_peak_mma<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e == cudaSuccess) k_peak_mma<true, 256><<<nsm, 128, smem, st>>>(iters, static_cast<int*>(buf));
+            } else if (kind == 3) {
+                e = cudaFuncSetAttribute(k_peak_mma<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e == cudaSuccess) k_peak_mma<false, 256><<<nsm, 128, smem, st>>>(iters, static_cast<int*>(buf));
+            } else {
+                e = cudaFuncSetAttribute(k_peak_mma<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e == cudaSuccess) k_peak_mma<true, 16><<<nsm, 128, smem, st>>>(iters, static_cast<int*>(buf));
+            }
             if (e != cudaSuccess) return e;
-            if (tf32) k_peak_mma<true><<<nsm, 128, smem, st>>>(iters, static_cast<int*>(buf));
-            else k_peak_mma<false><<<nsm, 128, smem, st>>>(iters, static_cast<int*>(buf));
-            flop = (double)nsm * iters * 2.0 * 128 * 256 * (tf32 ? 8 : 16);
+            flop = (double)nsm * iters * 2.0 * 128 * n * (tf32 ? 8 : 16);
         }
         if (timed) cudaEventRecord(e1, st);
         return cudaGetLastError();

@@ -134,14 +134,14 @@ __global__ void __launch_bounds__(256) k_chol_update(int n, int k0, double* __re
 
 cudaError_t launch_cholesky(Plan& pl, double* A, int n, cudaStream_t st) {
     for (int k0 = 0; k0 < n; k0 += CH_NB) {
-        k_chol_diag<<<1, CH_NB * CH_NB, 0, st>>>(n, k0, A, pl.d_err);
+        k_chol_diag<<<1, CH_NB * CH_NB, 0, st>>>(n, k0, A, pl.d_err + 1);
         note_launch(pl);
         const int below = n - k0 - CH_NB;
         if (below > 0) {
-            k_chol_panel<<<(below + 7) / 8, 256, 0, st>>>(n, k0, A, pl.d_err);
+            k_chol_panel<<<(below + 7) / 8, 256, 0, st>>>(n, k0, A, pl.d_err + 1);
             note_launch(pl);
             const int nt = (below + CH_NB - 1) / CH_NB;
-            k_chol_update<<<nt * (nt + 1) / 2, 256, 0, st>>>(n, k0, A, pl.d_err);
+            k_chol_update<<<nt * (nt + 1) / 2, 256, 0, st>>>(n, k0, A, pl.d_err + 1);
             note_launch(pl);
         }
     }

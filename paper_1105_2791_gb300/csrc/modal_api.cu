@@ -362,7 +362,39 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
     pl->cl.assign(C_l, C_l + lmax + 1);
     gauss_legendre(grid->nrings, pl->mu, pl->w);
 
+    // kernel geometry
+    {
+        int64_t ctas = pl->npix / 8192;
+        pl->cubic_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, 512));
+        int64_t ks = pl->npix / 16384;
+        pl->lin_ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(ks, 128));
+        cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, pl->dev);
+        pl->nsm = std::max(pl->nsm, 1);
+    }
+
     auto fail = [&](modal_status s) { destroy_plan(pl); return s; };
+    // Refuse a plan whose resident tables and a one-map workspace exceed the device's free
+    // memory before allocating any of it (the tables grow as lmax^3: about 25 GB at lmax =
+    // 2000 for the tensor-core precisions, near 200 GB at 4000).
+    {
+        const size_t tables = (size_t)pl->n_alm * pl->RH * sizeof(float) + tc_table_bytes(*pl) +
+                              tc_adj_table_bytes(*pl) + (size_t)pl->npix * sizeof(float);
+        const size_t one_map = per_map_workspace(pl) +
+                               ((size_t)pl->cubic_ctas * pl->n_max +
+                                (size_t)std::max(pl->lin_ksplit, pl->nsm) * pl->n_pair * pl->P) * sizeof(double);
+        const size_t margin = (size_t)256 << 20;          // small tables, the context's own use
+        size_t free_b = 0, total_b = 0;
+        const cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+        if (e != cudaSuccess) return fail(cuda_check(e, "cudaMemGetInfo"));
+        if (tables + one_map + margin > free_b) {
+            char msg[256];
+            std::snprintf(msg, sizeof msg,
+                          "plan needs %.2f GB of device memory (tables %.2f GB, workspace for one map %.2f GB); "
+                          "%.2f GB free",
+                          (tables + one_map + margin) / 1e9, tables / 1e9, one_map / 1e9, free_b / 1e9);
+            return fail(set_error(MODAL_ENOMEM, msg));
+        }
+    }
 #define CKI(expr, what)                                        \
     do {                                                       \
         modal_status _s = cuda_check((expr), (what));          \
@@ -473,17 +505,8 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
     CKI(dalloc(pl, &pl->S2, (size_t)pl->n_max * pl->n_max), "S2");
     CKI(cudaMemset(pl->S1, 0, pl->n_max * sizeof(double)), "S1 clear");
     CKI(cudaMemset(pl->S2, 0, (size_t)pl->n_max * pl->n_max * sizeof(double)), "S2 clear");
-    CKI(dalloc(pl, &pl->d_err, 1), "error word");
-    CKI(cudaMemset(pl->d_err, 0, sizeof(int)), "error word clear");
-    // kernel geometry
-    {
-        int64_t ctas = pl->npix / 8192;
-        pl->cubic_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, 512));
-        int64_t ks = pl->npix / 16384;
-        pl->lin_ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(ks, 128));
-        cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, pl->dev);
-        pl->nsm = std::max(pl->nsm, 1);
-    }
+    CKI(dalloc(pl, &pl->d_err, 2), "error words");
+    CKI(cudaMemset(pl->d_err, 0, 2 * sizeof(int)), "error words clear");
     // tensor-core tables
     if (prec != MODAL_FP32) CKI(build_tc_tables(*pl, 0), "tensor-core tables");
     if (prec != MODAL_FP32) CKI(build_tc_adj_tables(*pl, 0), "tensor-core adjoint tables");
@@ -697,12 +720,14 @@ modal_status modal_cov_accumulate(modal_h h, const double* beta, int B, void* st
     return MODAL_OK;
 }
 
-static modal_status read_device_error(modal_h h, cudaStream_t st) {
+// word: the data path's error word (h->d_err) or the FP64 solve's (h->d_err + 1), so that a
+// solve running on another stream beside the data path never reads the other's errors.
+static modal_status read_device_error(modal_h h, cudaStream_t st, int* word) {
     int e = 0;
-    CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word read");
+    CK(cudaMemcpyAsync(&e, word, sizeof(int), cudaMemcpyDeviceToHost, st), "error word read");
     CK(cudaStreamSynchronize(st), "sync");
     if (e) {
-        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), st), "error word clear");
+        CK(cudaMemsetAsync(word, 0, sizeof(int), st), "error word clear");
         CK(cudaStreamSynchronize(st), "sync");
         if (e & MODAL_DEVERR_NOTPD) return set_error(MODAL_ENOTPD, "zeta is not positive definite");
         if (e & MODAL_DEVERR_TIMEOUT) return set_error(MODAL_ETIMEOUT, "a device-side wait hit its spin limit");
@@ -725,7 +750,7 @@ modal_status modal_fnl_weights(modal_h h, const double* alpha, double* w, double
         { STAGE(h, ST_SOLVE, st); CK(launch_zeta(*h, A, st), "zeta"); }
         { STAGE(h, ST_SOLVE, st); CK(launch_cholesky(*h, A, n, st), "cholesky"); }
         CK(cudaMemcpyAsync(v, alpha, n * sizeof(double), cudaMemcpyHostToDevice, st), "alpha copy");
-        modal_status es = read_device_error(h, st);
+        modal_status es = read_device_error(h, st, h->d_err + 1);
         if (es != MODAL_OK) return es;
         { STAGE(h, ST_SOLVE, st); CK(launch_solve_rhs(*h, A, n, v, 1, st), "triangular solve"); }
         { STAGE(h, ST_SOLVE, st); CK(launch_estimates(*h, v, n, 0, norm, st), "alpha norm"); }
@@ -761,7 +786,7 @@ modal_status modal_solve(modal_h h, const double* alpha, const double* beta, int
         { STAGE(h, ST_SOLVE, st); CK(launch_cholesky(*h, A, n, st), "cholesky"); }
         CK(cudaMemcpyAsync(rhs, alpha, n * sizeof(double), cudaMemcpyHostToDevice, st), "alpha copy");
         if (B > 0) CK(cudaMemcpyAsync(rhs + n, beta, (size_t)B * n * sizeof(double), cudaMemcpyDeviceToDevice, st), "beta copy");
-        modal_status es = read_device_error(h, st);
+        modal_status es = read_device_error(h, st, h->d_err + 1);
         if (es != MODAL_OK) return es;
         { STAGE(h, ST_SOLVE, st); CK(launch_solve_rhs(*h, A, n, rhs, B + 1, st), "triangular solve"); }
         { STAGE(h, ST_SOLVE, st); CK(launch_estimates(*h, rhs, n, B, est, st), "estimates"); }
@@ -789,7 +814,7 @@ static modal_status factor_zeta0(modal_h h, const double* zeta0, double* A, cuda
     const int n = h->n_max;
     CK(cudaMemcpyAsync(A, zeta0, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, st), "zeta0 copy");
     { STAGE(h, ST_SOLVE, st); CK(launch_cholesky(*h, A, n, st), "cholesky of zeta0"); }
-    modal_status es = read_device_error(h, st);
+    modal_status es = read_device_error(h, st, h->d_err + 1);
     if (es == MODAL_ENOTPD) return set_error(MODAL_ENOTPD, "zeta0 is not positive definite");
     return es;
 }
@@ -1091,7 +1116,7 @@ modal_status modal_sync(modal_h h, void* stream) {
     cudaStream_t st = as_stream(stream);
     CK(cudaStreamSynchronize(st), "sync");
     CK(cudaGetLastError(), "sync");
-    return read_device_error(h, st);
+    return read_device_error(h, st, h->d_err);
 }
 
 modal_status modal_selftest_wait(modal_h h, int spin_limit, void* stream) {

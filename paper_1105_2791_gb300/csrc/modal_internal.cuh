@@ -127,7 +127,7 @@ struct Plan {
     double* ring_mean = nullptr; // [n_pair][nrings]
     float* vring = nullptr;      // [chunk][P][nrings] adjoint pair-mean term
     double* solve_ws = nullptr;  // [n_max][n_max] + vectors
-    int* d_err = nullptr;        // device error word
+    int* d_err = nullptr;        // device error words: [0] data path, [1] FP64 solve (Cholesky)
     size_t device_bytes = 0;
     size_t workspace_bytes = 0;
     std::vector<int> cubic_pair_ab_host, cubic_tiles_host;
@@ -162,6 +162,8 @@ modal_status cuda_check(cudaError_t e, const char* what);
 cudaError_t launch_lambda_table(const Plan& pl, const double* d_mu_north, const double* d_log2c,
                                 const double* d_a, const double* d_b, cudaStream_t st);
 cudaError_t build_tc_tables(Plan& pl, cudaStream_t st);      // allocates pl.tc
+size_t tc_table_bytes(const Plan& pl);                       // bytes build_tc_tables allocates for the table
+size_t tc_adj_table_bytes(const Plan& pl);                   // the same for build_tc_adj_tables
 size_t tc_b_workspace_bytes(const Plan& pl, int chunk);
 // k_legendre_tc_adj.cu
 cudaError_t build_tc_adj_tables(Plan& pl, cudaStream_t st);
