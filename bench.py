@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--prec", default="auto", help="fp32 | 3xtf32 | fp16x3 | bf16x3 | bf16 | auto")
     ap.add_argument("--no-baseline", action="store_true",
                     help="skip the plain FP32 comparison, the CPU baseline and the mixed-workload key")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="mixed workload: time the default launch shapes only (no modal_autotune)")
     ap.add_argument("--cpu-rings", type=int, default=8, help="rings in the CPU-baseline sample")
     ap.add_argument("--lmax", type=int, default=2000, help="smaller l_max for profiler captures only")
     ap.add_argument("--chunk", type=int, default=32, help="maps per internal pass of the library")
@@ -461,11 +463,15 @@ def run_gpu(args):
         # timed on the same GPU after the headline step's plan is released
         plan.close()
         try:
-            mv, mms, ml, mclk, mn = mixed_measure(M, dev, prec, args.chunk, max(2, K // 2), 2)
+            mx = mixed_measure(M, dev, prec, args.chunk, max(2, K // 2), 2)
             result["mixed_workload"] = {
                 "metric": "maps/s, mixed l_max 500/1000/2000 (2:1:1) coefficient pass with linear term, P=16",
-                "value": round(mv, 3), "unit": "maps/s", "ms_per_step": round(mms, 3), "maps_per_step": mn,
-                "steps": max(2, K // 2), "gpu_launches_per_step": int(ml), "clocks": mclk}
+                "value": round(mx["value"], 3), "unit": "maps/s", "ms_per_step": round(mx["ms"], 3),
+                "launch_shapes": "autotuned per plan (modal_autotune, untimed)",
+                "default_shapes_value": round(mx["default_value"], 3),
+                "default_shapes_ms_per_step": round(mx["default_ms"], 3),
+                "tuning": mx.get("tuning"), "maps_per_step": mx["maps_per_step"],
+                "steps": max(2, K // 2), "gpu_launches_per_step": int(mx["launches"]), "clocks": mx["clocks"]}
         except Exception as e:          # the headline line is printed whatever happens here
             result["mixed_workload"] = {"error": str(e)[:200]}
     if rank == 0 and world == 1 and not args.no_baseline and prec != "fp32":
@@ -611,11 +617,13 @@ def cpu_baseline(nring_sample, prec=None, beta_headline=None):
 MIXED = [(500, 256), (1000, 128), (2000, 128)]      # (l_max, maps per step): the 2:1:1 batched mix
 
 
-def mixed_measure(M, dev, prec, chunk, steps, warmup, rank=0, world=1, local=0):
+def mixed_measure(M, dev, prec, chunk, steps, warmup, rank=0, world=1, local=0, tune=True):
     """Batched Monte Carlo coefficient pass: 256 maps at l_max = 500, 128 at 1000 and 128 at
     2000 per step (P = 16, 20-degree band mask, linear term), one plan per l_max grouped in a
-    modal batch and replayed as one CUDA graph.  Returns (maps/s, ms per step, kernels per
-    step, clock summary, maps per step)."""
+    modal batch and replayed as one CUDA graph.  Timed first with the default launch shapes,
+    then (tune) after modal_autotune has tuned each plan on its own maps (untimed; the batch
+    graph is captured again).  Returns a dict: value / ms (tuned if tune, else default),
+    default_value / default_ms, tuning per l_max, kernels per step, clocks, maps per step."""
     import torch
     import simgen
 
@@ -633,36 +641,46 @@ def mixed_measure(M, dev, prec, chunk, steps, warmup, rank=0, world=1, local=0):
         alms.append(torch.from_numpy(simgen.gaussian_alm(cl, nb, seed=60 + i + 1000 * rank).astype(np.complex64)).to(dev))
     batch = M.Batch(plans)
     n_maps = sum(nb for _, nb in MIXED)
-    for _ in range(warmup):
-        batch.cubic(alms, use_linear=True, graph=True)
-    torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    for pl in plans:
-        M.modal_get_profile(pl.h)
     st = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clocks:
-        ev0.record(st)
-        for _ in range(steps):
+
+    def timed():
+        for _ in range(warmup):
             batch.cubic(alms, use_linear=True, graph=True)
-        ev1.record(st)
         torch.cuda.synchronize()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
-    value = job_throughput(n_maps, steps, world, ms)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clocks:
+            ev0.record(st)
+            for _ in range(steps):
+                batch.cubic(alms, use_linear=True, graph=True)
+            ev1.record(st)
+            torch.cuda.synchronize()
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+        return job_throughput(n_maps, steps, world, ms), ms / steps, clocks.summary()
+
+    out = {"maps_per_step": n_maps}
+    out["default_value"], out["default_ms"], clk = timed()
+    out["value"], out["ms"], out["clocks"] = out["default_value"], out["default_ms"], clk
+    if tune:
+        out["tuning"] = {}
+        for (L, nb), pl, a in zip(MIXED, plans, alms):
+            best, _ = pl.autotune(a, use_linear=True)
+            out["tuning"]["lmax%d" % L] = best
+        out["value"], out["ms"], out["clocks"] = timed()
     # kernels per step: one direct (uncaptured) pass, counted by the plans
     for pl in plans:
         M.modal_get_profile(pl.h)
     batch.cubic(alms, use_linear=True, graph=False)
     torch.cuda.synchronize()
-    launches = sum(sum(n for (_, n) in M.modal_get_profile(pl.h).values()) for pl in plans)
+    out["launches"] = sum(sum(n for (_, n) in M.modal_get_profile(pl.h).values()) for pl in plans)
     for pl in plans:
         pl.sync()
     batch.close()
     for pl in plans:
         pl.close()
-    return value, ms / steps, launches, clocks.summary(), n_maps
+    return out
 
 
 def run_mixed(args):
@@ -679,7 +697,8 @@ def run_mixed(args):
     dev = torch.device("cuda", local)
     prec = "fp16x3" if args.prec == "auto" else args.prec
     K, W = args.steps, args.warmup
-    value, ms, launches, clk, n_maps = mixed_measure(M, dev, prec, args.chunk, K, W, rank, world, local)
+    mx = mixed_measure(M, dev, prec, args.chunk, K, W, rank, world, local, tune=not args.no_tune)
+    value, ms, launches, clk, n_maps = mx["value"], mx["ms"], mx["launches"], mx["clocks"], mx["maps_per_step"]
     if rank == 0:
         print(json.dumps({
             "metric": "maps/s, mixed l_max 500/1000/2000 (2:1:1) coefficient pass with linear term, P=16",
@@ -690,7 +709,9 @@ def run_mixed(args):
             "config": {"workload": "batched Monte Carlo: 256 @ l_max 500, 128 @ 1000, 128 @ 2000 per step, "
                                    "P=16, band mask, one captured CUDA graph", "maps_per_step": n_maps,
                        "precision": prec, "l2": "inputs and intermediates > L2 (no flush)",
+                       "launch_shapes": "default" if args.no_tune else "autotuned per plan (modal_autotune, untimed)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
+            "default_shapes_value": round(mx["default_value"], 3), "tuning": mx.get("tuning"),
             "clocks": clk, "gpu_launches": int(launches) * K,
             "roofline": None, "e2e": None,
         }), flush=True)

@@ -262,6 +262,38 @@ modal_status modal_reset(modal_h h, int what);
  * plan has no workspace and the calls that run maps through it return MODAL_ESTATE
  * until a modal_set_chunk succeeds. */
 modal_status modal_set_chunk(modal_h h, int chunk);
+
+/* Launch shapes of a plan's kernels (not part of the method; every setting gives the same
+ * results up to the order of FP32/FP64 partial sums).
+ *   chunk          maps per internal pass (as modal_set_chunk), [1, 4096]
+ *   legendre_maps  maps per work item of the tensor-core Legendre contraction: the MMA
+ *                  tile is 128 ring pairs x N = 2 P legendre_maps columns, N a multiple of
+ *                  16 and at most 256, legendre_maps <= 32 (default 8; kept but unused by
+ *                  the FP32 plan)
+ *   cubic_ctas     CTAs per map of the cubic and quartic sums (split-K over pixels),
+ *                  [1, max(1, npix / 128)]
+ *   linear_ranges  pixel ranges (split-K) of the tensor-core linear-term product,
+ *                  [1, 8 x the device's SM count] (default: the SM count)
+ *   ms             output of modal_autotune: the winning coefficient-pass time (ignored
+ *                  by modal_set_tuning) */
+typedef struct modal_tuning {
+    int chunk, legendre_maps, cubic_ctas, linear_ranges;
+    float ms;
+} modal_tuning;
+modal_status modal_get_tuning(modal_h h, modal_tuning* t);
+/* Validates every field (MODAL_EINVAL, nothing changed) and reallocates the workspace
+ * (synchronises).  If that allocation fails: MODAL_ENOMEM with the previous tuning
+ * restored, or, if even that fails, no workspace (as modal_set_chunk). */
+modal_status modal_set_tuning(modal_h h, const modal_tuning* t);
+/* Autotuner: times modal_cubic(h, alm, B, use_linear, ...) (the coefficient pass: synthesis,
+ * cubic sums and the linear term) on the caller's maps for candidate settings of each
+ * field in turn (legendre_maps, cubic_ctas, linear_ranges, chunk), CUDA events on
+ * `stream`, one warm-up and the better of two timed calls per candidate, and keeps a
+ * candidate only if it is at least 1 % faster than the best so far.  Leaves the plan on
+ * the winning tuning and writes it to *best (best->ms = its time).  alm: dev [B][n_alm],
+ * B >= 1; a candidate whose workspace does not fit is skipped.  Synchronises; takes about
+ * 50 coefficient passes. */
+modal_status modal_autotune(modal_h h, const void* alm, int B, int use_linear, modal_tuning* best, void* stream);
 /* Synchronise `stream`, then report asynchronous faults (MODAL_ECUDA) or a device
  * wait that gave up (MODAL_ETIMEOUT, with the flag cleared). */
 modal_status modal_sync(modal_h h, void* stream);

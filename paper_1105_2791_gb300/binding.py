@@ -33,6 +33,7 @@ EXPORTS = [
     "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
     "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate", "modal_quartic",
     "modal_set_retain_maps", "modal_backward_retained", "modal_fnl_weights", "modal_peak_probe",
+    "modal_get_tuning", "modal_set_tuning", "modal_autotune",
 ]
 MODAL_NSTAGES = 15
 
@@ -54,6 +55,13 @@ class modal_info(ctypes.Structure):
                 ("n_lin", c_longlong), ("n_cov", c_longlong), ("lin_final", c_int), ("chunk", c_int),
                 ("device_bytes", c_size_t), ("n_quad", c_int)]
 
+
+class modal_tuning(ctypes.Structure):
+    _fields_ = [("chunk", c_int), ("legendre_maps", c_int), ("cubic_ctas", c_int), ("linear_ranges", c_int),
+                ("ms", c_float)]
+
+
+TUNING_FIELDS = ("chunk", "legendre_maps", "cubic_ctas", "linear_ranges")
 
 _LIB = None
 
@@ -82,6 +90,9 @@ def load_library():
         "modal_solve": [H, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
         "modal_fnl_weights": [H, c_void_p, c_void_p, c_void_p, c_void_p],
         "modal_peak_probe": [c_int, c_void_p, c_void_p],
+        "modal_get_tuning": [H, POINTER(modal_tuning)],
+        "modal_set_tuning": [H, POINTER(modal_tuning)],
+        "modal_autotune": [H, c_void_p, c_int, c_int, POINTER(modal_tuning), c_void_p],
         "modal_bivector_fit": [H, c_void_p, c_void_p, c_void_p, c_void_p],
         "modal_solve_bivector": [H, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
         "modal_bivector_rotate": [H, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p],
@@ -249,6 +260,31 @@ def modal_fnl_weights(h, alpha, w, stream=None):
 
 
 PEAK_KINDS = {"fp32_simt": 0, "fp64_simt": 1, "tf32_tensor": 2, "f16_tensor": 3, "tf32_tensor_n16": 4}
+
+
+def _tuning_dict(t):
+    return {"chunk": t.chunk, "legendre_maps": t.legendre_maps, "cubic_ctas": t.cubic_ctas,
+            "linear_ranges": t.linear_ranges, "ms": float(t.ms)}
+
+
+def modal_get_tuning(h):
+    """The plan's launch shapes as a dict (modal_tuning)."""
+    t = modal_tuning()
+    _check(load_library().modal_get_tuning(h, byref(t)))
+    return _tuning_dict(t)
+
+
+def modal_set_tuning(h, tuning):
+    """Set the launch shapes from a dict with the keys of TUNING_FIELDS."""
+    t = modal_tuning(*(int(tuning[k]) for k in TUNING_FIELDS), 0.0)
+    _check(load_library().modal_set_tuning(h, byref(t)))
+
+
+def modal_autotune(h, alm, B, use_linear=False, stream=None):
+    """Time candidate launch shapes on the caller's maps; returns the winner (dict, with ms)."""
+    t = modal_tuning()
+    _check(load_library().modal_autotune(h, _dev(alm), int(B), int(bool(use_linear)), byref(t), _stream(stream)))
+    return _tuning_dict(t)
 
 
 def modal_peak_probe(kind, stream=None):

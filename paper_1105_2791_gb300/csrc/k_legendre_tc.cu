@@ -90,12 +90,12 @@ __global__ void __launch_bounds__(256) k_alm_amax(int L, const float* __restrict
 }
 
 // ------------------------------------------------------------------ B operand blocks
-// Stage block (g, m, pi, kb) of the filtered a_lm for maps 8g .. 8g+7: [hi tile, lo tile],
-// each N = 16 P rows (b, p, re/im) x TC_KB bytes of K (KPS values l = m + pi + 2 (kb KPS + k)),
-// the same core-matrix layout the MMA reads.  Built once per chunk and shared by every
-// ring tile.
+// Stage block (g, m, pi, kb) of the filtered a_lm for maps G g .. G g + G - 1 (G maps per
+// group, the plan's tunable): [hi tile, lo tile], each N = 2 P G rows (b, p, re/im) x TC_KB
+// bytes of K (KPS values l = m + pi + 2 (kb KPS + k)), the same core-matrix layout the MMA
+// reads.  Built once per chunk and shared by every ring tile.
 struct PrepArgs {
-    int L, P, B, n_groups;
+    int L, P, B, G, n_groups;
     int64_t n_alm, total_bkb;      // stage blocks per map group
     const int64_t* bblk_base;      // [2 (L+1)] first stage block of (m, parity)
     const float* filt;             // [P][L+1]
@@ -111,17 +111,17 @@ __global__ void __launch_bounds__(256) k_tc_prep_b(PrepArgs a) {
     constexpr int KPS = TC_KB / S::E;
     constexpr int CM = 16 / S::E;
     constexpr int NKC = TC_KB / 16;
-    __shared__ float2 s_a[TC_MAPS * 64];
+    __shared__ float2 s_a[TC_MAX_MAPS * 32];
     __shared__ float s_f[64 * 16];
-    __shared__ float s_scale[TC_MAPS];
+    __shared__ float s_scale[TC_MAX_MAPS];
     __shared__ int s_dec[16 * 16];                              // per column n: (map row of s_a, p, Re/Im)
-    const int N = 16 * a.P;
+    const int N = 2 * a.P * a.G;
     const int b_tile = N * TC_KB;
     const int m = blockIdx.y >> 1, pi = blockIdx.y & 1, g = blockIdx.z;
     const int nkb = tc_nkb(a.L, m, pi, KPS);
     const int64_t base_m = d_alm_index(m, m, a.L);
-    if (threadIdx.x < TC_MAPS) {
-        const int b = g * TC_MAPS + threadIdx.x;
+    if (threadIdx.x < a.G) {
+        const int b = g * a.G + threadIdx.x;
         s_scale[threadIdx.x] = (b < a.B) ? exp2f((float)tc_scale_exp(a.amax[b])) : 0.f;
     }
     // column n = (map bl, p, Re/Im) = 2 (bl P + p) + comp, decoded once per CTA
@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(256) k_tc_prep_b(PrepArgs a) {
     for (int kb = blockIdx.x; kb < nkb; kb += gridDim.x) {
         const int l0 = m + pi + 2 * kb * KPS;                   // l of K index k: l0 + 2 k
         __syncthreads();
-        for (int i = threadIdx.x; i < TC_MAPS * KPS; i += blockDim.x) {
+        for (int i = threadIdx.x; i < a.G * KPS; i += blockDim.x) {
             const int bl = i / KPS, k = i % KPS;
-            const int b = g * TC_MAPS + bl, l = l0 + 2 * k;
+            const int b = g * a.G + bl, l = l0 + 2 * k;
             float2 v = make_float2(0.f, 0.f);
             if (b < a.B && l <= a.L) {
                 v = a.alm[(int64_t)b * a.n_alm + base_m + (l - m)];
@@ -199,7 +199,7 @@ __device__ __forceinline__ void tmem_ld16x4(uint32_t a0, uint32_t a1, uint32_t a
 #undef TC_LD16
 
 struct TcArgs {
-    int L, P, R, R_half, RH, n_rt, B, n_groups;
+    int L, P, R, R_half, RH, n_rt, B, G, n_groups;
     int64_t n_items, total_bkb;
     const char* table;             // pre-tiled A blocks
     const int64_t* blk_base;       // [2 (L+1)] first A block of (m, parity)
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
     constexpr bool TF32 = (PREC == MODAL_3XTF32);
     constexpr int KPS = TC_KB / S::E;     // K values per stage
     constexpr int NKC = TC_KB / 16;       // core matrices along K per stage
-    const int N = 16 * a.P;               // 2 (re, im) x P x 8 maps
+    const int N = 2 * a.P * a.G;          // 2 (re, im) x P x G maps
     const int b_tile = N * TC_KB;         // bytes of one B tile
     const uint32_t stage_tx = TC_A_STAGE + 2 * b_tile;
 
@@ -336,11 +336,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
     } else {
         // ---------------- epilogue (TC_PROD_WARPS warps): TMEM -> D1 + D2 -> E or O row
         // Columns are ordered (map bl, basis p, re/im); column pair cp = bl P + p maps to
-        // the delta row (8 g P + cp) (L+1) 2 RH + (2 m + pi) RH, so addresses advance by a
+        // the delta row (G g P + cp) (L+1) 2 RH + (2 m + pi) RH, so addresses advance by a
         // fixed stride per column pair.
         const int quarter = warp % 4;                       // TMEM lanes 32 quarter .. + 31
         const int half = (warp - 2) / 4;                    // column half
-        const int nblk = a.P;                               // 16-column blocks (N = 16 P)
+        const int nblk = N / 16;                            // 16-column blocks
         const int blk_lo = half ? (nblk + 1) / 2 : 0, blk_hi = half ? nblk : (nblk + 1) / 2;
         const int64_t row_stride = (int64_t)(a.L + 1) * 2 * a.RH;
         const float lam_inv = (S::E == 2) ? (1.f / TC_LAMBDA_SCALE) : 1.f;
@@ -348,10 +348,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
         for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x, ++nitem) {
             int m, pi, rt, g;
             tc_item(a, item, m, pi, rt, g);
-            // per-map unscale factors of this map group (lane bl holds map 8 g + bl)
+            // per-map unscale factors of this map group (lane bl holds map G g + bl)
             float inv_lane = 0.f;
-            if (lane < TC_MAPS && g * TC_MAPS + lane < a.B)
-                inv_lane = exp2f((float)-tc_scale_exp(a.amax[g * TC_MAPS + lane])) * lam_inv;
+            if (lane < a.G && g * a.G + lane < a.B)
+                inv_lane = exp2f((float)-tc_scale_exp(a.amax[g * a.G + lane])) * lam_inv;
             bool ok = !*abort_flag && mbar_wait(tmem_full, nitem & 1, abort_flag, a.err);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) {                                       // items left undone: never silent
@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_legendre_tc(TcArgs a) {
             tc_fence_after();
             const int jn = rt * 128 + quarter * 32 + lane;   // TMEM lane = ring pair within the tile
             const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-            const int cp_valid = (a.B - g * TC_MAPS) * a.P;   // column pairs that belong to real maps
-            float2* base = a.delta + ((int64_t)g * TC_MAPS * a.P) * row_stride + (int64_t)(2 * m + pi) * a.RH + jn;
+            const int cp_valid = (a.B - g * a.G) * a.P;       // column pairs that belong to real maps
+            float2* base = a.delta + ((int64_t)g * a.G * a.P) * row_stride + (int64_t)(2 * m + pi) * a.RH + jn;
             auto store_block = [&](int blk, const float* d) {
                 const int cp0 = blk * 8;
                 int bl = cp0 / a.P, p = cp0 - bl * a.P;
@@ -429,8 +429,13 @@ size_t tc_b_workspace_bytes(const Plan& pl, int chunk) {
     int64_t total = 0;
     for (int m = 0; m <= pl.lmax; ++m)
         for (int pi = 0; pi < 2; ++pi) total += tc_nkb(pl.lmax, m, pi, KPS);
-    const int groups = (chunk + TC_MAPS - 1) / TC_MAPS;
-    return (size_t)groups * total * 2 * (16 * pl.P) * TC_KB;
+    const int groups = (chunk + pl.tc_maps - 1) / pl.tc_maps;
+    return (size_t)groups * total * 2 * (2 * pl.P * pl.tc_maps) * TC_KB;
+}
+
+bool tc_maps_valid(int P, int G) {
+    const int n = 2 * P * G;
+    return G >= 1 && G <= TC_MAX_MAPS && n % 16 == 0 && n <= 256;
 }
 
 size_t tc_table_bytes(const Plan& pl) {
@@ -541,7 +546,7 @@ static cudaError_t launch_tc(const Plan& pl, const PrepArgs& pa, const TcArgs& a
 
 cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2* delta, int part, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
-    if (B > 4096 || B > pl.chunk) return cudaErrorInvalidValue;
+    if (B > 4096 || B > pl.chunk || !tc_maps_valid(pl.P, pl.tc_maps)) return cudaErrorInvalidValue;
     if (part & 1) {
         cudaError_t e = cudaMemsetAsync(pl.tc.d_amax, 0, B * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
@@ -554,7 +559,8 @@ cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2*
     pa.L = pl.lmax;
     pa.P = pl.P;
     pa.B = B;
-    pa.n_groups = (B + TC_MAPS - 1) / TC_MAPS;
+    pa.G = pl.tc_maps;
+    pa.n_groups = (B + pa.G - 1) / pa.G;
     pa.n_alm = pl.n_alm;
     pa.total_bkb = pl.tc.total_bkb;
     pa.bblk_base = pl.tc.d_bkb_off;
@@ -570,6 +576,7 @@ cudaError_t launch_legendre_tc(const Plan& pl, const float2* alm, int B, float2*
     a.RH = pl.RH;
     a.n_rt = pl.tc.n_rt;
     a.B = B;
+    a.G = pa.G;
     a.n_groups = pa.n_groups;
     a.n_items = (int64_t)(pl.lmax + 1) * 2 * a.n_rt * a.n_groups;
     a.total_bkb = pl.tc.total_bkb;

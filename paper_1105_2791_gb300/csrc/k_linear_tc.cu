@@ -317,11 +317,13 @@ __global__ void __launch_bounds__(LT_THREADS, 1) k_linear_tc(LinArgs a) {
     }
 }
 
-// One pixel range per SM: the n_mt * nsm items of equal size spread evenly over the nsm
-// persistent CTAs, n_mt each (the partial-sum buffer holds nsm ranges).
+// Pixel ranges: by default one per SM, so the n_mt * nsm items of equal size spread evenly
+// over the nsm persistent CTAs, n_mt each; the plan's tuning may choose another count (the
+// partial-sum buffer holds max(nsm, lt_ranges) ranges).
 int linear_tc_splits(const Plan& pl, int B) {
     (void)B;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(pl.nsm, pl.npix / LT_KPX));
+    const int r = pl.lt_ranges > 0 ? pl.lt_ranges : pl.nsm;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(r, pl.npix / LT_KPX));
 }
 
 size_t linear_presplit_bytes(const Plan& pl) {

@@ -182,7 +182,7 @@ static modal_status alloc_workspace_buffers(modal_plan* pl, int chunk) {
     CK(dalloc(pl, &pl->vring, (size_t)chunk * pl->P * pl->nrings), "workspace vring");
     // cubic partials: [chunk][cubic_ctas][n_max]; linear partials: [ksplit][n_pair][chunk*P]
     const size_t cub = (size_t)chunk * pl->cubic_ctas * pl->n_max;
-    const size_t lin = (size_t)std::max(pl->lin_ksplit, pl->nsm) * pl->n_pair * chunk * pl->P;
+    const size_t lin = (size_t)std::max(pl->lin_ksplit, std::max(pl->nsm, pl->lt_ranges)) * pl->n_pair * chunk * pl->P;
     pl->partial_elems = cub + lin;
     CK(dalloc(pl, &pl->partial, pl->partial_elems), "workspace partial");
     {
@@ -370,6 +370,8 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
         pl->lin_ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(ks, 128));
         cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, pl->dev);
         pl->nsm = std::max(pl->nsm, 1);
+        pl->lt_ranges = pl->nsm;
+        pl->tc_maps = 8;                                   // N = 16 P columns per Legendre item
     }
 
     auto fail = [&](modal_status s) { destroy_plan(pl); return s; };
@@ -551,6 +553,146 @@ modal_status modal_set_chunk(modal_h h, int chunk) {
     return set_error(s, why + " (the plan has no workspace until modal_set_chunk succeeds)");
 }
 
+modal_status modal_get_tuning(modal_h h, modal_tuning* t) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!t) return set_error(MODAL_EINVAL, "t is NULL");
+    t->chunk = h->chunk;
+    t->legendre_maps = h->tc_maps;
+    t->cubic_ctas = h->cubic_ctas;
+    t->linear_ranges = h->lt_ranges;
+    t->ms = 0.f;
+    return MODAL_OK;
+}
+
+modal_status modal_set_tuning(modal_h h, const modal_tuning* t) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (!t) return set_error(MODAL_EINVAL, "t is NULL");
+    if (t->chunk < 1 || t->chunk > 4096) return set_error(MODAL_EINVAL, "chunk must be in [1, 4096]");
+    if (!tc_maps_valid(h->P, t->legendre_maps))
+        return set_error(MODAL_EINVAL, "legendre_maps: 2 P legendre_maps must be a multiple of 16 and at most 256");
+    const int64_t max_ctas = std::max<int64_t>(1, h->npix / 128);
+    if (t->cubic_ctas < 1 || t->cubic_ctas > max_ctas)
+        return set_error(MODAL_EINVAL, "cubic_ctas must be in [1, max(1, npix / 128)]");
+    if (t->linear_ranges < 1 || t->linear_ranges > 8 * h->nsm)
+        return set_error(MODAL_EINVAL, "linear_ranges must be in [1, 8 x SM count]");
+    CK(cudaDeviceSynchronize(), "set_tuning sync");
+    const int old_chunk = h->chunk, old_maps = h->tc_maps, old_ctas = h->cubic_ctas, old_ranges = h->lt_ranges;
+    h->tc_maps = t->legendre_maps;
+    h->cubic_ctas = t->cubic_ctas;
+    h->lt_ranges = t->linear_ranges;
+    const modal_status s = alloc_workspace(h, t->chunk);
+    if (s == MODAL_OK) return MODAL_OK;
+    const std::string why = modal_last_error();
+    h->tc_maps = old_maps;
+    h->cubic_ctas = old_ctas;
+    h->lt_ranges = old_ranges;
+    if (old_chunk >= 1 && alloc_workspace(h, old_chunk) == MODAL_OK)
+        return set_error(s, why + " (the previous tuning is kept)");
+    free_workspace(h);
+    h->chunk = 0;
+    return set_error(s, why + " (the plan has no workspace until modal_set_chunk or modal_set_tuning succeeds)");
+}
+
+modal_status modal_autotune(modal_h h, const void* alm, int B, int use_linear, modal_tuning* best, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
+    if (!alm || !best || B < 1) return set_error(MODAL_EINVAL, "alm, best and B >= 1 are required");
+    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+    cudaStream_t st = as_stream(stream);
+    double* beta = nullptr;
+    CK(cudaMalloc(&beta, (size_t)B * h->n_max * sizeof(double)), "autotune beta");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // one warm-up call, then the better of two timed calls
+    auto time_pass = [&](float* ms) -> modal_status {
+        float bestv = 3.4e38f;
+        for (int r = 0; r < 3; ++r) {
+            CK(cudaEventRecord(e0, st), "autotune event");
+            const modal_status s = modal_cubic(h, alm, B, use_linear, beta, stream);
+            if (s != MODAL_OK) return s;
+            CK(cudaEventRecord(e1, st), "autotune event");
+            CK(cudaEventSynchronize(e1), "autotune sync");
+            float v = 0.f;
+            CK(cudaEventElapsedTime(&v, e0, e1), "autotune time");
+            if (r > 0) bestv = std::min(bestv, v);
+        }
+        *ms = bestv;
+        return MODAL_OK;
+    };
+    modal_tuning cur;
+    modal_get_tuning(h, &cur);
+    float cur_ms = 0.f;
+    modal_status s = time_pass(&cur_ms);
+    // a candidate replaces the incumbent only if it is at least 1 % faster; one that cannot
+    // be set (its workspace does not fit) is skipped
+    auto consider = [&](modal_tuning cand) -> modal_status {
+        if (cand.chunk == cur.chunk && cand.legendre_maps == cur.legendre_maps && cand.cubic_ctas == cur.cubic_ctas &&
+            cand.linear_ranges == cur.linear_ranges)
+            return MODAL_OK;
+        if (modal_set_tuning(h, &cand) != MODAL_OK) return modal_set_tuning(h, &cur);
+        float ms = 0.f;
+        const modal_status r = time_pass(&ms);
+        if (r != MODAL_OK) return r;
+        if (ms < 0.99f * cur_ms) {
+            cur = cand;
+            cur_ms = ms;
+            return MODAL_OK;
+        }
+        return modal_set_tuning(h, &cur);
+    };
+    const int nsm = h->nsm;
+    if (s == MODAL_OK && h->prec != MODAL_FP32) {
+        const int gs[] = {32, 28, 24, 20, 16, 14, 12, 10, 8, 6, 4, 2};
+        int tried = 0;
+        for (int g : gs) {
+            if (s != MODAL_OK || tried >= 6) break;
+            if (!tc_maps_valid(h->P, g) || g > std::max(8, B)) continue;
+            modal_tuning c = cur;
+            c.legendre_maps = g;
+            s = consider(c);
+            ++tried;
+        }
+    }
+    if (s == MODAL_OK) {
+        const int64_t max_ctas = std::max<int64_t>(1, h->npix / 128);
+        const int cs[] = {std::max(1, nsm / 4), std::max(1, nsm / 2), nsm, 2 * nsm, 4 * nsm, 8 * nsm};
+        for (int c : cs) {
+            if (s != MODAL_OK) break;
+            if (c > max_ctas) continue;
+            modal_tuning t = cur;
+            t.cubic_ctas = c;
+            s = consider(t);
+        }
+    }
+    if (s == MODAL_OK && use_linear && h->lin_mode == MODAL_LINEAR_PIXEL && h->prec != MODAL_FP32) {
+        const int rs[] = {std::max(1, nsm / 2), nsm, 2 * nsm, 4 * nsm};
+        for (int r : rs) {
+            if (s != MODAL_OK) break;
+            modal_tuning t = cur;
+            t.linear_ranges = r;
+            s = consider(t);
+        }
+    }
+    if (s == MODAL_OK) {
+        const int ks[] = {8, 16, 32, 64, 128};
+        for (int k : ks) {
+            if (s != MODAL_OK) break;
+            if (k > B) continue;
+            modal_tuning t = cur;
+            t.chunk = k;
+            s = consider(t);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(beta);
+    if (s != MODAL_OK) return s;
+    cur.ms = cur_ms;
+    *best = cur;
+    return MODAL_OK;
+}
+
 modal_status modal_synthesize(modal_h h, const void* alm, int B, float* maps, void* stream) {
     if (check_plan(h)) return MODAL_EINVAL;
     if (check_workspace(h)) return MODAL_ESTATE;
@@ -676,7 +818,7 @@ static modal_status ensure_quartic(modal_plan* h) {
         CK(dalloc(h, &h->qt.k3, (size_t)h->qt.n_quad), "quartic two-pair term");
         CK(dalloc(h, &h->qt.kmat, (size_t)std::max(h->lin_ksplit, 1) * h->n_pair * h->n_pair), "quartic two-pair sums");
     }
-    if (h->qt.chunk == h->chunk) return MODAL_OK;
+    if (h->qt.chunk == h->chunk && h->qt.ctas == h->cubic_ctas) return MODAL_OK;
     dfree(h->qt.partial); dfree(h->qt.rq); dfree(h->qt.h);
     h->qt.partial = h->qt.rq = h->qt.h = nullptr;
     h->qt.chunk = 0;
@@ -686,6 +828,7 @@ static modal_status ensure_quartic(modal_plan* h) {
     CK(dalloc(h, &h->qt.rq, ch * np * h->nrings), "quartic ring sums");
     CK(dalloc(h, &h->qt.h, std::max(hring, hpix)), "quartic single-pair term");
     h->qt.chunk = h->chunk;
+    h->qt.ctas = h->cubic_ctas;
     return MODAL_OK;
 }
 

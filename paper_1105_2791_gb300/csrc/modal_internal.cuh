@@ -69,6 +69,7 @@ struct QuarticState {
     double* kmat = nullptr;       // two-pair sums [ksplit or 1][n_pair][n_pair]
     double* k3 = nullptr;         // [n_quad] two-pair term
     int chunk = 0;                // maps the buffers were sized for
+    int ctas = 0;                 // cubic_ctas the partial sums were sized for
 };
 
 struct Plan {
@@ -111,8 +112,10 @@ struct Plan {
     float2* ut = nullptr;        // [chunk][P][lmax+1][2][RH] (adjoint)
     double* partial = nullptr;   // cubic / linear partial sums
     size_t partial_elems = 0;
-    int cubic_ctas = 0;          // CTAs per map in the cubic kernel
+    int cubic_ctas = 0;          // CTAs per map in the cubic and quartic kernels (tunable)
     int lin_ksplit = 0;          // K splits in the linear-term GEMM (SIMT)
+    int lt_ranges = 0;           // pixel ranges of the tensor-core linear-term GEMM (tunable)
+    int tc_maps = 8;             // maps per work item of the tensor-core Legendre kernel (tunable)
     int nsm = 0;                 // SMs of the plan's device
     // maps of the last modal_cubic call kept in `maps` for modal_backward_retained
     int retain_maps = 0;
@@ -163,6 +166,7 @@ cudaError_t launch_lambda_table(const Plan& pl, const double* d_mu_north, const 
                                 const double* d_a, const double* d_b, cudaStream_t st);
 cudaError_t build_tc_tables(Plan& pl, cudaStream_t st);      // allocates pl.tc
 size_t tc_table_bytes(const Plan& pl);                       // bytes build_tc_tables allocates for the table
+bool tc_maps_valid(int P, int G);                            // G maps per forward Legendre item: 2 P G % 16 == 0, <= 256
 size_t tc_adj_table_bytes(const Plan& pl);                   // the same for build_tc_adj_tables
 size_t tc_b_workspace_bytes(const Plan& pl, int chunk);
 // k_legendre_tc_adj.cu

@@ -10,7 +10,8 @@
 
 namespace modal {
 
-constexpr int TC_MAPS = 8;                 // maps per work item (N = 16 P)
+constexpr int TC_MAPS = 8;                 // maps per work item of the adjoint Legendre kernel (N = 16 P)
+constexpr int TC_MAX_MAPS = 32;            // most maps per work item of the forward kernel (tunable, N = 2 P G <= 256)
 constexpr int TC_PROD_WARPS = 8;           // epilogue warps
 constexpr int TC_THREADS = 32 * (2 + TC_PROD_WARPS);
 constexpr int TC_STAGES = 4;

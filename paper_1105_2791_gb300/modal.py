@@ -9,6 +9,7 @@ import numpy as np
 import torch
 
 from . import binding as B
+from . import tuning as T
 
 
 class Plan:
@@ -22,6 +23,7 @@ class Plan:
         self.n_quad = info.n_quad
         self.prec = info.prec
         self.linear_mode = "pixel"
+        self.masked = ring_mask is not None or pix_mask is not None
 
     # -- lifecycle
     def close(self):
@@ -152,6 +154,35 @@ class Plan:
 
     def sync(self):
         B.modal_sync(self.h)
+
+    # -- launch shapes
+    def tuning(self):
+        """The plan's launch shapes (modal_get_tuning) as a dict."""
+        return B.modal_get_tuning(self.h)
+
+    def set_tuning(self, tuning):
+        """Set launch shapes from a dict (modal_set_tuning; unspecified keys keep their value)."""
+        cur = B.modal_get_tuning(self.h)
+        cur.update({k: v for k, v in tuning.items() if k in B.TUNING_FIELDS})
+        B.modal_set_tuning(self.h, cur)
+
+    def autotune(self, alm, use_linear=False, cache=None):
+        """Tune the launch shapes for coefficient passes over batches like `alm` (dev
+        [B][n_alm]).  With `cache` (a JSON file path), a configuration tuned before is taken
+        from the file without timing, and a new result is added to it.  Returns
+        (tuning dict, "cache" or "measured")."""
+        key = None
+        if cache:
+            key = T.tuning_key(torch.cuda.get_device_name(alm.device), self.lmax, self.P, self.nrings, self.nphi,
+                               self.prec, alm.shape[0], use_linear, self.linear_mode, self.masked)
+            entry = T.load(cache).get(key)
+            if entry is not None and T.valid_entry(entry):
+                self.set_tuning(entry)
+                return dict(self.tuning(), ms=float(entry.get("ms", 0.0))), "cache"
+        best = B.modal_autotune(self.h, alm, alm.shape[0], use_linear)
+        if cache:
+            T.store(cache, key, best)
+        return best, "measured"
 
     def save_state(self, path):
         B.modal_save_state(self.h, path)
