@@ -167,8 +167,9 @@ STAGE_TRAFFIC_GB = {
 def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps, peaks, nsynth=3, probe=None):
     """Roofline of every timed stage: algorithmic work per step (flops or bytes) over the
     stage's live CUDA-event time, against its peak; sorted by time, largest first.
-    nsynth: syntheses per chunk (linear term, cubic, and the adjoint unless it reuses the
-    cubic's maps)."""
+    nsynth: syntheses per chunk per step (3: linear term, coefficient pass and adjoint each
+    synthesise; 2: the coefficient pass reads the linear-term pass's maps; 1: the adjoint
+    does too)."""
     R_half, L1, npix = (R + 1) // 2, L + 1, R * nphi
     n_alm = (L + 1) * (L + 2) // 2
     probe = probe or {}
@@ -222,12 +223,6 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
             src = fp32_src
         t = traffic.get(stage)
         extra = {}
-        if stage == "adjoint_pixel" and bound == "tensor" and probe.get("tf32_tensor_n16"):
-            # the same product against the tensor pipe's measured rate at its own instruction
-            # shape (M = 128, N = 16): the ceiling of a kernel that issues N = 16 MMAs
-            sp = probe["tf32_tensor_n16"] / 3.0
-            extra = {"shape_peak": round(sp, 1), "shape_frac": round(achieved / sp, 4),
-                     "shape_peak_source": "measured in this run: tcgen05 kind::tf32 probe (M128 N16) / 3 products"}
         if achieved > peak:
             # the peaks are a torch copy kernel and cuBLAS, not hard ceilings: a kernel that
             # streams well can exceed them slightly; flagged, not capped
@@ -268,10 +263,12 @@ def run_gpu(args):
     lin_sims = torch.from_numpy(simgen.gaussian_alm(cl, 2, seed=4 + 1000 * rank,
                                                     stream=simgen.STREAM_LINEAR).astype(np.complex64)).to(dev)
 
-    # The adjoint differentiates the cubic call of the same step and synthesises its maps
-    # again (recomputation, not storage).  --adjoint kept reuses the maps that call left in
-    # the plan's workspace instead (modal_backward_retained; the batch must fit one chunk);
-    # the default run times that variant too, in a short extra pass reported beside.
+    # The step's batch is a linear-term sample and the coefficient pass's input: its maps are
+    # synthesised once for both (modal_linear_term keeps them, modal_cubic_retained reads
+    # them; the batch must fit one chunk).  The adjoint differentiates the coefficient pass
+    # and synthesises the maps again (recomputation, not storage).  --adjoint kept reuses the
+    # kept maps for the adjoint too (modal_backward_retained); the default run times that
+    # variant as well, in a short extra pass reported beside.
     kept_ok = B <= args.chunk
     if args.adjoint == "kept" and not kept_ok:
         raise SystemExit("--adjoint kept needs --batch <= --chunk")
@@ -286,6 +283,7 @@ def run_gpu(args):
             raise
         plan.set_chunk(min(args.chunk, B))
         plan.set_retain_maps(kept_ok)
+        plan.reuse_maps = kept_ok                      # coefficient pass on the linear-term pass's maps
         if args.linear == "ring":
             plan.set_linear_mode("ring")
         plan.linear_term(lin_sims, finalize=True)      # a mean to subtract from the first step on
@@ -320,7 +318,10 @@ def run_gpu(args):
 
     def step(pl, a, overlap=True, kept=None):
         pl.linear_term(a)
-        pl.cubic(a, use_linear=True, out=beta)
+        if pl.reuse_maps:
+            pl.cubic_retained(a, use_linear=True, out=beta)
+        else:
+            pl.cubic(a, use_linear=True, out=beta)
         pl.cov_accumulate(beta)
         backward = pl.backward_retained if (retain if kept is None else kept) else pl.backward
         if not overlap:                                  # per-stage timing: one stream, stages in order
@@ -389,10 +390,9 @@ def run_gpu(args):
         return ms, prof
 
     # roofline denominators the driver does not measure: FP32 SIMT, FP64 SIMT, tcgen05 tf32
-    # and f16 rates (and tf32 at the adjoint's N = 16), each probed once on this GPU before
-    # the timed region
+    # and f16 rates, each probed once on this GPU before the timed region
     probe = {}
-    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor", "tf32_tensor_n16"):
+    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor"):
         try:
             probe[kind] = round(M.modal_peak_probe(kind), 2)
         except M.ModalError as e:
@@ -424,8 +424,9 @@ def run_gpu(args):
     n_prof_steps = max(1, K // 2)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    nsynth = (1 if retain else 2) if kept_ok else 3
     rooflines = stage_rooflines(prec, L, R, nphi, P, plan.n_max, plan.n_pair, min(B, args.chunk), B, prof,
-                                n_prof_steps, peaks, nsynth=2 if retain else 3, probe=probe)
+                                n_prof_steps, peaks, nsynth=nsynth, probe=probe)
     top = rooflines[0]
     roof = {k: top[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "peak_source")}
     if top["traffic"] is not None:
@@ -442,7 +443,10 @@ def run_gpu(args):
                        L, R, nphi, P, plan.n_max, B, prec),
                    "lmax": L, "nrings": R, "nphi": nphi, "P": P, "n_max": plan.n_max, "batch_per_gpu": B,
                    "precision": prec, "linear_means": args.linear,
+                   "coefficient_maps": ("kept from the step's linear-term synthesis" if kept_ok
+                                        else "synthesised again"),
                    "adjoint_maps": "kept from the step's cubic call" if retain else "synthesised again",
+                   "syntheses_per_map_per_step": nsynth,
                    "l2": "inputs and intermediates > L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk,
@@ -486,6 +490,7 @@ def run_gpu(args):
         # synthesising its maps again, as in the default step)
         try:
             plain.set_chunk(1)
+            plain.reuse_maps = False                   # one map per launch: every call synthesises
             oms, _ = timed(plain, alm, max(1, K // 2), 1, kept=False)
             result["plain_one_map_value"] = round(B * max(1, K // 2) / (oms / 1e3), 3)
             result["speedup_vs_plain_one_map"] = round(value / world / result["plain_one_map_value"], 3)
@@ -774,10 +779,9 @@ def run_trispectrum(args):
         return max_over_ranks(ev0.elapsed_time(ev1), dev), prof
 
     # roofline denominators the driver does not measure: FP32 SIMT, FP64 SIMT, tcgen05 tf32
-    # and f16 rates (and tf32 at the adjoint's N = 16), each probed once on this GPU before
-    # the timed region
+    # and f16 rates, each probed once on this GPU before the timed region
     probe = {}
-    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor", "tf32_tensor_n16"):
+    for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor"):
         try:
             probe[kind] = round(M.modal_peak_probe(kind), 2)
         except M.ModalError as e:

@@ -209,13 +209,24 @@ modal_status modal_bivector_rotate(modal_h h, const double* zeta0, const double*
 modal_status modal_backward(modal_h h, const void* alm, int B, const double* g, int use_linear,
                             void* grad_alm, void* stream);
 
-/* Keep the filtered maps of each modal_cubic call whose batch fits one chunk (B <= chunk;
- * no extra memory: they stay in the plan's map workspace), so that modal_backward_retained
- * can differentiate that call without synthesising them again.  on: 0 (default) or 1. */
+/* Keep the filtered maps of each modal_linear_term or modal_cubic call whose batch fits one
+ * chunk (B <= chunk; no extra memory: they stay in the plan's map workspace), so that
+ * modal_cubic_retained and modal_backward_retained can use them without synthesising them
+ * again.  on: 0 (default) or 1. */
 modal_status modal_set_retain_maps(modal_h h, int on);
 
-/* modal_backward at the a_lm of the plan's last modal_cubic call, from the maps that call
- * kept: the same result as modal_backward(h, alm, B, g, use_linear, grad_alm) without the
+/* modal_cubic (Eq. bbispect with the linear term of Eq. bispectrumest) at the a_lm of the
+ * plan's last modal_linear_term or modal_cubic call, from the maps that call kept (and, for
+ * the per-ring linear term, the Legendre sums still beside them): the same result as
+ * modal_cubic(h, alm, B, use_linear, beta) without the synthesis, so that a batch that is
+ * both a linear-term sample and a coefficient input is synthesised once.  alm and B must
+ * be the pointer and count given to that call (checked; the caller must not have changed
+ * the a_lm since), and this call must be ordered after it on the device.  The maps stay
+ * kept.  B = 0 does nothing; MODAL_ESTATE if no maps are kept for (alm, B). */
+modal_status modal_cubic_retained(modal_h h, const void* alm, int B, int use_linear, double* beta, void* stream);
+
+/* modal_backward at the a_lm of the plan's last modal_linear_term or modal_cubic call, from
+ * the maps that call kept: the same result as modal_backward(h, alm, B, g, use_linear, grad_alm) without the
  * synthesis.  alm and B must be the pointer and count given to that call (checked; the
  * caller must not have changed the a_lm since), and the call must be ordered after it on
  * the device (same stream, or an event).  B = 0 does nothing.  MODAL_ESTATE if no maps are

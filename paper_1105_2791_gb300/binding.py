@@ -33,7 +33,7 @@ EXPORTS = [
     "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
     "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate", "modal_quartic",
     "modal_set_retain_maps", "modal_backward_retained", "modal_fnl_weights", "modal_peak_probe",
-    "modal_get_tuning", "modal_set_tuning", "modal_autotune",
+    "modal_get_tuning", "modal_set_tuning", "modal_autotune", "modal_cubic_retained",
 ]
 MODAL_NSTAGES = 15
 
@@ -86,6 +86,7 @@ def load_library():
         "modal_analyze": [H, c_void_p, c_int, c_void_p, c_void_p],
         "modal_linear_term": [H, c_void_p, c_int, c_int, c_void_p],
         "modal_cubic": [H, c_void_p, c_int, c_int, c_void_p, c_void_p],
+        "modal_cubic_retained": [H, c_void_p, c_int, c_int, c_void_p, c_void_p],
         "modal_cov_accumulate": [H, c_void_p, c_int, c_void_p],
         "modal_solve": [H, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p],
         "modal_fnl_weights": [H, c_void_p, c_void_p, c_void_p, c_void_p],
@@ -200,6 +201,11 @@ def modal_linear_term(h, alm_sims, B, finalize, stream=None):
 
 def modal_cubic(h, alm, B, use_linear, beta, stream=None):
     _check(load_library().modal_cubic(h, _dev(alm), int(B), int(bool(use_linear)), _dev(beta), _stream(stream)))
+
+
+def modal_cubic_retained(h, alm, B, use_linear, beta, stream=None):
+    _check(load_library().modal_cubic_retained(h, _dev(alm), int(B), int(bool(use_linear)), _dev(beta),
+                                               _stream(stream)))
 
 
 def modal_quartic(h, alm, B, use_linear, tau, stream=None):

@@ -154,7 +154,7 @@ static size_t per_map_workspace(const modal_plan* pl) {
     const size_t maps = (size_t)pl->P * pl->npix * sizeof(float);
     const size_t ut = (size_t)pl->P * L1 * 2 * pl->RH * sizeof(float2);
     return delta + maps + ut + tc_b_workspace_bytes(*pl, 8) / 8 + tc_adj_workspace_bytes(*pl, 8) / 8 +
-           adjoint_tc_workspace_bytes(*pl, 1);
+           adjoint_v_workspace_bytes(*pl, 1) + adjoint_pm_workspace_bytes(*pl, 1);
 }
 
 static void free_workspace(modal_plan* pl) {
@@ -164,7 +164,8 @@ static void free_workspace(modal_plan* pl) {
     dfree(pl->ut); pl->ut = nullptr;
     dfree(pl->partial); pl->partial = nullptr;
     dfree(pl->hk); pl->hk = nullptr;
-    dfree(pl->adj_hops); pl->adj_hops = nullptr;
+    dfree(pl->adj_gops); pl->adj_gops = nullptr;
+    dfree(pl->adj_pmk); pl->adj_pmk = nullptr;
     dfree(pl->vring); pl->vring = nullptr;
     dfree(pl->tc.bops); pl->tc.bops = nullptr;
     dfree(pl->tca.bops); pl->tca.bops = nullptr;
@@ -178,7 +179,8 @@ static modal_status alloc_workspace_buffers(modal_plan* pl, int chunk) {
     CK(dalloc(pl, &pl->maps, (size_t)chunk * pl->P * pl->npix), "workspace maps");
     CK(dalloc(pl, &pl->ut, (size_t)chunk * pl->P * L1 * 2 * pl->RH), "workspace ut");
     CK(dalloc(pl, &pl->hk, (size_t)chunk * pl->P * pl->n_pair), "workspace hk");
-    CK(dalloc(pl, &pl->adj_hops, adjoint_tc_workspace_bytes(*pl, chunk)), "workspace adjoint operands");
+    CK(dalloc(pl, &pl->adj_gops, adjoint_v_workspace_bytes(*pl, chunk)), "workspace adjoint operands");
+    CK(dalloc(pl, &pl->adj_pmk, adjoint_pm_workspace_bytes(*pl, chunk) / sizeof(float)), "workspace adjoint pair-mean weights");
     CK(dalloc(pl, &pl->vring, (size_t)chunk * pl->P * pl->nrings), "workspace vring");
     // cubic partials: [chunk][cubic_ctas][n_max]; linear partials: [ksplit][n_pair][chunk*P]
     const size_t cub = (size_t)chunk * pl->cubic_ctas * pl->n_max;
@@ -246,7 +248,7 @@ static void destroy_plan(modal_plan* pl) {
     dfree(pl->modeidx); dfree(pl->tiles); dfree(pl->pair_ab);
     dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->lin_bsplit); dfree(pl->S1); dfree(pl->S2);
     dfree(pl->ring_sum); dfree(pl->ring_mean);
-    dfree(pl->solve_ws); dfree(pl->d_err);
+    dfree(pl->solve_ws); dfree(pl->d_err); dfree(pl->adj_pm); dfree(pl->adj_pm_blk);
     dfree(pl->qt.tiles); dfree(pl->qt.idx); dfree(pl->qt.modes); dfree(pl->qt.pa); dfree(pl->qt.pb);
     dfree(pl->qt.partial); dfree(pl->qt.rq); dfree(pl->qt.h); dfree(pl->qt.k3); dfree(pl->qt.kmat);
     free_tc_tables(*pl);
@@ -753,6 +755,10 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
         else CK(launch_pair_accumulate(*h, h->maps, nb, st), "pair accumulate");
     }
     h->n_lin += B;
+    if (h->retain_maps && B > 0 && B <= h->chunk) {      // the whole batch is in the map workspace
+        h->kept_alm = alm_sims;
+        h->kept_B = B;
+    }
     if (finalize) {
         if (h->n_lin < 1) return set_error(MODAL_ESTATE, "finalize with no linear-term simulations");
         STAGE(h, ST_PAIRS, st);
@@ -761,23 +767,21 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
         const modal_status ps = refresh_linear_presplit(h, st);
         if (ps != MODAL_OK) return ps;
         h->lin_final = 1;
+        h->adj_pm_ready = 0;
     }
     return MODAL_OK;
 }
 
-modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, double* beta, void* stream) {
-    if (check_plan(h)) return MODAL_EINVAL;
-    if (check_workspace(h)) return MODAL_ESTATE;
-    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
-    if (B > 0 && (!alm || !beta)) return set_error(MODAL_EINVAL, "null pointer");
-    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
-    cudaStream_t st = as_stream(stream);
+// The coefficient pass of B maps; kept: the maps (and, for the ring-mode linear term, their
+// Legendre sums) are already in the plan's workspace from an earlier call on the same a_lm.
+static modal_status cubic_impl(modal_h h, const void* alm, int B, int use_linear, double* beta, cudaStream_t st,
+                               bool kept) {
     const float2* a = static_cast<const float2*>(alm);
     double* cub = h->partial;
     double* lin = h->partial + (size_t)h->chunk * h->cubic_ctas * h->n_max;
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
-        CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "cubic synthesis");
+        if (!kept) CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "cubic synthesis");
         { STAGE(h, ST_CUBIC, st); CK(launch_cubic(*h, h->maps, nb, cub, st), "cubic"); }
         int splits = h->lin_ksplit;
         if (use_linear) {
@@ -800,6 +804,28 @@ modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, doub
         h->kept_B = B;
     }
     return MODAL_OK;
+}
+
+modal_status modal_cubic(modal_h h, const void* alm, int B, int use_linear, double* beta, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B > 0 && (!alm || !beta)) return set_error(MODAL_EINVAL, "null pointer");
+    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+    return cubic_impl(h, alm, B, use_linear, beta, as_stream(stream), false);
+}
+
+modal_status modal_cubic_retained(modal_h h, const void* alm, int B, int use_linear, double* beta, void* stream) {
+    if (check_plan(h)) return MODAL_EINVAL;
+    if (check_workspace(h)) return MODAL_ESTATE;
+    if (B < 0) return set_error(MODAL_EINVAL, "B < 0");
+    if (B == 0) return MODAL_OK;
+    if (!alm || !beta) return set_error(MODAL_EINVAL, "null pointer");
+    if (use_linear && !h->lin_final) return set_error(MODAL_ESTATE, "linear term requested before modal_linear_term(finalize)");
+    if (!h->kept_alm || h->kept_alm != alm || h->kept_B != B)
+        return set_error(MODAL_ESTATE, "no maps kept for this a_lm and batch (modal_set_retain_maps, B <= chunk, "
+                                       "no synthesis or adjoint since the call that kept them)");
+    return cubic_impl(h, alm, B, use_linear, beta, as_stream(stream), true);
 }
 
 modal_status modal_set_retain_maps(modal_h h, int on) {
@@ -1091,6 +1117,13 @@ static modal_status backward_impl(modal_h h, const void* alm, int B, const doubl
     float2* out = static_cast<float2*>(grad_alm);
     // ring mode: the pair-mean term is constant on each ring and enters only through m = 0
     const bool ring = use_linear && h->lin_mode == MODAL_LINEAR_RING;
+    // split plans, per-pixel means: the pair-mean term enters after the transposed Legendre
+    // sums, through the adjoint transform of each weighted pair-mean row (built once per mean)
+    const bool pm_late = use_linear && !ring && h->prec != MODAL_FP32;
+    if (pm_late && !h->adj_pm_ready) {
+        STAGE(h, ST_OTHER, st);
+        CK(build_adjoint_pm_table(*h, st), "adjoint pair-mean table");
+    }
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
         if (!kept) CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "backward synthesis");
@@ -1102,7 +1135,7 @@ static modal_status backward_impl(modal_h h, const void* alm, int B, const doubl
             if (h->prec == MODAL_FP32)
                 CK(launch_adjoint_u(*h, h->maps, nb, h->hk, use_linear && !ring, h->maps, st), "adjoint pixel");
             else
-                CK(launch_adjoint_tc(*h, nb, h->hk, use_linear && !ring, h->maps, st), "adjoint pixel");
+                CK(launch_adjoint_v(*h, nb, h->hk, h->maps, st), "adjoint pixel");
         }
         {
             // split precisions: the r2c kernel also records each map's max |U~| for the operand scale
@@ -1118,6 +1151,10 @@ static modal_status backward_impl(modal_h h, const void* alm, int B, const doubl
         } else {
             { STAGE(h, ST_LEGENDRE_ADJ_PREP, st); CK(launch_legendre_adjoint_tc(*h, h->ut, nb, out + (size_t)b0 * h->n_alm, true, 1, st), "adjoint legendre prep"); }
             { STAGE(h, ST_LEGENDRE_ADJ, st); CK(launch_legendre_adjoint_tc(*h, h->ut, nb, out + (size_t)b0 * h->n_alm, true, 2, st), "adjoint legendre"); }
+        }
+        if (pm_late) {
+            STAGE(h, ST_ADJ_PIXEL, st);
+            CK(launch_adjoint_pm(*h, nb, h->hk, out + (size_t)b0 * h->n_alm, st), "adjoint pair-mean term");
         }
     }
     return MODAL_OK;
@@ -1245,6 +1282,7 @@ modal_status modal_reset(modal_h h, int what) {
         if (h->ring_sum) CK(cudaMemset(h->ring_sum, 0, (size_t)h->n_pair * h->nrings * sizeof(double)), "reset ring sums");
         h->n_lin = 0;
         h->lin_final = 0;
+        h->adj_pm_ready = 0;
     }
     if (what & 2) {
         CK(cudaMemset(h->S1, 0, h->n_max * sizeof(double)), "reset S1");
@@ -1345,6 +1383,7 @@ modal_status modal_load_state(modal_h h, const char* path) {
     h->n_lin = hd.n_lin;
     h->n_cov = hd.n_cov;
     h->lin_final = 0;
+    h->adj_pm_ready = 0;
     if (hd.has_pairs && hd.lin_final && h->n_lin > 0) {
         if (hd.has_pairs == 2) CK(launch_ring_finalize(*h, 0), "ring pair means");
         else CK(launch_pair_finalize(*h, 0), "pair finalize");

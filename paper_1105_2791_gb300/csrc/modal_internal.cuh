@@ -122,7 +122,12 @@ struct Plan {
     const void* kept_alm = nullptr;   // a_lm they were synthesised from (nullptr: none kept)
     int kept_B = 0;
     float* hk = nullptr;         // [chunk][P][n_pair] adjoint weights
-    char* adj_hops = nullptr;    // [chunk] tf32 hi/lo B operands of the tensor-core adjoint pixel weights
+    char* adj_gops = nullptr;    // [chunk] tf32 hi/lo G operands of the tensor-core adjoint pixel weights
+    float* adj_pmk = nullptr;    // [lmax+1][chunk][n_pair] filter-weighted adjoint weights K (pair-mean part)
+    float2* adj_pm = nullptr;    // [n_pair][n_alm] (l-major) adjoint transform of each weighted pair-mean row
+    int adj_pm_ready = 0;        // adj_pm holds the current pair means
+    int* adj_pm_blk = nullptr;   // blocks of the pair-mean gradient kernel: l << 8 | m block, largest l first
+    int adj_pm_nblk = 0;
     // ring-only linear term (modal_set_linear_mode)
     int lin_mode = 0;            // MODAL_LINEAR_PIXEL or MODAL_LINEAR_RING
     int has_pix_mask = 0;        // W varies along rings: ring mode refused
@@ -209,8 +214,13 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
 cudaError_t launch_adjoint_u(Plan& pl, const float* maps, int B, const float* hk, int use_linear,
                              float* u, cudaStream_t st);
 // k_adjoint_tc.cu: the same pixel weights as a tcgen05 product (split plans); in place on maps
-size_t adjoint_tc_workspace_bytes(const Plan& pl, int chunk);
-cudaError_t launch_adjoint_tc(Plan& pl, int B, const float* hk, int use_linear, float* maps, cudaStream_t st);
+// k_adjoint_v.cu: the map part of the pixel weights (in place over the maps) and the
+// pair-mean part applied to the gradient after the transposed Legendre sums.
+size_t adjoint_v_workspace_bytes(const Plan& pl, int chunk);
+cudaError_t launch_adjoint_v(Plan& pl, int B, const float* hk, float* maps, cudaStream_t st);
+size_t adjoint_pm_workspace_bytes(const Plan& pl, int chunk);
+cudaError_t build_adjoint_pm_table(Plan& pl, cudaStream_t st);
+cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, cudaStream_t st);
 // k_ring_linear.cu
 cudaError_t launch_pair_ring(Plan& pl, const float* maps, int B, cudaStream_t st);
 cudaError_t launch_ring_finalize(Plan& pl, cudaStream_t st);

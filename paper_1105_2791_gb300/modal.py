@@ -72,6 +72,15 @@ class Plan:
         B.modal_cubic(self.h, alm, nb, use_linear, out)
         return out
 
+    def cubic_retained(self, alm, use_linear=False, out=None):
+        """cubic() of the batch whose maps the last linear_term() or cubic() call kept (same
+        alm tensor, set_retain_maps on): no second synthesis."""
+        nb = alm.shape[0]
+        if out is None:
+            out = torch.empty((nb, self.n_max), dtype=torch.float64, device=alm.device)
+        B.modal_cubic_retained(self.h, alm, nb, use_linear, out)
+        return out
+
     def quartic(self, alm, use_linear=False, out=None):
         """Trispectrum modal coefficients tau [B][n_quad] float64 (modal_quartic)."""
         nb = alm.shape[0]

@@ -126,18 +126,3 @@ def test_probed_peaks_replace_the_derived_ones():
     tf = _by_stage(bench.stage_rooflines("3xtf32", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,
                                          probe=probe))
     assert tf["legendre"]["peak"] == pytest.approx(300.0)
-
-
-def test_adjoint_pixel_reports_its_shape_peak():
-    """With the N = 16 tf32 probe, the tensor-core adjoint pixel stage also reports its
-    fraction of the tensor pipe's rate at its own instruction shape (a third of the probe)."""
-    probe = {"fp32_simt": 70.0, "tf32_tensor": 900.0, "tf32_tensor_n16": 240.0}
-    rows = _by_stage(bench.stage_rooflines("fp16x3", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,
-                                           probe=probe))
-    ap = rows["adjoint_pixel"]
-    assert ap["shape_peak"] == pytest.approx(80.0)
-    assert ap["shape_frac"] == pytest.approx(ap["achieved"] / 80.0, rel=1e-3)
-    assert "shape_peak" not in rows["linear_gemm"]
-    plain = _by_stage(bench.stage_rooflines("fp16x3", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,
-                                            probe={"tf32_tensor": 900.0}))
-    assert "shape_peak" not in plain["adjoint_pixel"]

@@ -1,7 +1,8 @@
-"""The adjoint from the maps kept by the preceding cubic call (modal_backward_retained).
+"""The adjoint and the coefficients from the maps kept by a preceding call
+(modal_backward_retained, modal_cubic_retained).
 
-It runs the same kernels on the same maps as modal_backward, so the gradients must agree
-bit for bit; they are also checked against the oracle's adjoint_grad (<= 1e-5 relative,
+They run the same kernels on the same maps as modal_backward and modal_cubic, so the
+results must agree bit for bit; they are also checked against the oracle's adjoint_grad (<= 1e-5 relative,
 as for modal_backward).  The state checks cover every call that reuses the map workspace.
 """
 import numpy as np
@@ -88,7 +89,7 @@ def test_backward_retained_needs_the_cubic_calls_maps():
     plan.cubic(a)
     refused(a[:1], g[:1])                            # another batch size
     refused(a.clone(), g)                            # another a_lm buffer
-    plan.linear_term(a)                              # linear-term synthesis reuses the workspace
+    plan.linear_term(a.clone())                      # linear-term synthesis of another buffer
     refused(a, g)
     plan.cubic(a)
     plan.quartic(a)                                  # so does the trispectrum
@@ -115,5 +116,67 @@ def test_backward_retained_needs_the_cubic_calls_maps():
     got = plan.backward_retained(a, g)
     assert torch.equal(got, ref)
     refused(a, g)                                    # the adjoint consumed the kept maps
+    plan.sync()
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
+@pytest.mark.parametrize("mode", ["pixel", "ring"])
+def test_cubic_retained_from_the_linear_term_maps(prec, mode):
+    """A batch that is both a linear-term sample and a coefficient input: linear_term(a) keeps
+    its maps, cubic_retained(a) gives cubic(a) bit for bit (and, in ring mode, reads the m = 0
+    Legendre sums left beside them), and backward_retained after it gives backward."""
+    M = _cuda_or_skip()
+    L, P, R, nphi, nb = 24, 6, 25, 64, 3
+    basis = simgen.shifted_legendre_basis(L, P)
+    cl = simgen.cl_model(L)
+    plan = M.Plan(L, P, basis, cl, R, nphi, prec=prec, ring_mask=simgen.band_mask(R, 20.0))
+    if mode == "ring":
+        plan.set_linear_mode("ring")
+    plan.set_retain_maps(True)
+    sims = simgen.gaussian_alm(cl, 6, seed=81, stream=simgen.STREAM_LINEAR).astype(np.complex64)
+    plan.linear_term(torch.from_numpy(sims).cuda(), finalize=True)
+    a = torch.from_numpy(simgen.gaussian_alm(cl, nb, seed=82).astype(np.complex64)).cuda()
+    g = torch.from_numpy(np.random.default_rng(83).standard_normal((nb, plan.n_max))).cuda()
+    plan.linear_term(a)                              # accumulate only: the mean in use is unchanged
+    kept = plan.cubic_retained(a, use_linear=True)
+    kept_plain = plan.cubic_retained(a)              # the maps stay kept
+    grad_kept = plan.backward_retained(a, g, use_linear=True)
+    again = plan.cubic(a, use_linear=True)
+    assert torch.equal(kept, again)
+    assert torch.equal(kept_plain, plan.cubic(a))
+    assert torch.equal(grad_kept, plan.backward(a, g, use_linear=True))
+    plan.sync()
+    plan.close()
+
+
+def test_cubic_retained_needs_kept_maps():
+    M = _cuda_or_skip()
+    L, P, R, nphi = 16, 3, 17, 64
+    basis = simgen.shifted_legendre_basis(L, P)
+    cl = simgen.cl_model(L)
+    plan = M.Plan(L, P, basis, cl, R, nphi, prec="fp32")
+    a = torch.from_numpy(simgen.gaussian_alm(cl, 2, seed=91).astype(np.complex64)).cuda()
+
+    def refused(x):
+        with pytest.raises(M.ModalError) as ei:
+            plan.cubic_retained(x)
+        assert ei.value.status == M.MODAL_ESTATE
+
+    plan.linear_term(a)
+    refused(a)                                       # retention off
+    plan.set_retain_maps(True)
+    plan.linear_term(a)
+    refused(a[:1])                                   # another batch size
+    refused(a.clone())                               # another a_lm buffer
+    ref = plan.cubic(a)
+    assert torch.equal(plan.cubic_retained(a), ref)  # kept by the cubic call itself
+    plan.backward(a, torch.ones((2, plan.n_max), dtype=torch.float64, device="cuda"))
+    refused(a)                                       # the adjoint overwrote the maps
+    plan.linear_term(a)
+    plan.set_chunk(1)                                # two maps in two chunks: nothing kept
+    plan.linear_term(a)
+    refused(a)
+    assert plan.cubic_retained(a[:0]).shape == (0, plan.n_max)
     plan.sync()
     plan.close()
