@@ -446,12 +446,13 @@ __global__ void k_adjpm_k(int L, int P, int n_pair, int B, const float* __restri
     }
 }
 
-// grad[b][lm] -= c_m sum_c K[l][b][c] F_c[lm] for up to AP_MAPS maps per block; block =
+// T[b][l (l+1)/2 + m] = c_m sum_c K[l][b][c] F_c[lm] for up to AP_MAPS maps per block; block =
 // (one l, AP_THREADS consecutive m), the largest l first so that the longest rows start early.
-// K[l] sits in shared memory as [c][b], read four maps per broadcast load.
-__global__ void __launch_bounds__(AP_THREADS) k_adjpm_grad(int L, int n_pair, int B, int64_t n_alm, const int* __restrict__ blk_l,
+// K[l] sits in shared memory as [c][b], read four maps per broadcast load; T is l-major like
+// F, so both the loads of F and the stores of T are contiguous in m.
+__global__ void __launch_bounds__(AP_THREADS) k_adjpm_grad(int n_pair, int B, int64_t n_alm, const int* __restrict__ blk_l,
                                                            const float* __restrict__ K, const float2* __restrict__ F,
-                                                           float2* __restrict__ grad) {
+                                                           float2* __restrict__ T) {
     __shared__ __align__(16) float sK[136 * AP_MAPS];
     const int code = blk_l[blockIdx.x];
     const int l = code >> 8, m = ((code & 0xff) * AP_THREADS) + threadIdx.x;
@@ -488,14 +489,37 @@ __global__ void __launch_bounds__(AP_THREADS) k_adjpm_grad(int L, int n_pair, in
         }
     }
     const float cm = (m == 0) ? 1.f : 2.f;
-    const int64_t idx = d_alm_index(l, m, L);
+    const int64_t li = av_lidx(l, m);
 #pragma unroll
-    for (int b = 0; b < AP_MAPS; ++b) {
-        if (b < nb) {
-            float2* o = grad + (int64_t)(bg + b) * n_alm + idx;
+    for (int b = 0; b < AP_MAPS; ++b)
+        if (b < nb) T[(int64_t)(bg + b) * n_alm + li] = make_float2(cm * acc[b].x, m > 0 ? cm * acc[b].y : 0.f);
+}
+
+// grad[b][alm index (l, m)] -= T[b][l (l+1)/2 + m], through 32 x 32 tiles of (l, m) in shared
+// memory so that T is read contiguous in m and grad written contiguous in l.
+__global__ void __launch_bounds__(256) k_adjpm_apply(int L, int64_t n_alm, const float2* __restrict__ T,
+                                                     float2* __restrict__ grad) {
+    __shared__ float2 tile[32][33];
+    const int nlb = (L + 32) / 32;
+    const int lb = blockIdx.x / nlb, mb = blockIdx.x % nlb;
+    if (mb > lb) return;
+    const int b = blockIdx.y;
+    const float2* tb = T + (int64_t)b * n_alm;
+    float2* gb = grad + (int64_t)b * n_alm;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    for (int i = ty; i < 32; i += 8) {                     // row l = 32 lb + i, column m = 32 mb + tx
+        const int l = 32 * lb + i, m = 32 * mb + tx;
+        tile[tx][i] = (l <= L && m <= l) ? tb[av_lidx(l, m)] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {                     // row m = 32 mb + j, column l = 32 lb + tx
+        const int m = 32 * mb + j, l = 32 * lb + tx;
+        if (l <= L && m <= l) {
+            float2* o = gb + d_alm_index(l, m, L);
+            const float2 d = tile[j][tx];
             float2 r = *o;
-            r.x -= cm * acc[b].x;
-            if (m > 0) r.y -= cm * acc[b].y;
+            r.x -= d.x;
+            r.y -= d.y;
             *o = r;
         }
     }
@@ -505,7 +529,7 @@ size_t adjoint_pm_workspace_bytes(const Plan& pl, int chunk) {
     return pl.prec == MODAL_FP32 ? 0 : (size_t)(pl.lmax + 1) * chunk * pl.n_pair * sizeof(float);
 }
 
-cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, cudaStream_t st) {
+cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, float2* scratch, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
     if (!pl.adj_pm_ready || !pl.adj_pmk || !pl.adj_pm_blk || B > pl.chunk || pl.n_pair > 136) return cudaErrorInvalidValue;
     const int64_t n = (int64_t)(pl.lmax + 1) * B * pl.n_pair;
@@ -515,7 +539,12 @@ cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, cu
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_adjpm_grad<<<dim3(pl.adj_pm_nblk, (B + AP_MAPS - 1) / AP_MAPS), AP_THREADS, 0, st>>>(
-        pl.lmax, pl.n_pair, B, pl.n_alm, pl.adj_pm_blk, pl.adj_pmk, pl.adj_pm, grad);
+        pl.n_pair, B, pl.n_alm, pl.adj_pm_blk, pl.adj_pmk, pl.adj_pm, scratch);
+    note_launch(pl);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nlb = (pl.lmax + 32) / 32;
+    k_adjpm_apply<<<dim3(nlb * nlb, B), 256, 0, st>>>(pl.lmax, pl.n_alm, scratch, grad);
     note_launch(pl);
     return cudaGetLastError();
 }

@@ -1154,7 +1154,8 @@ static modal_status backward_impl(modal_h h, const void* alm, int B, const doubl
         }
         if (pm_late) {
             STAGE(h, ST_ADJ_PIXEL, st);
-            CK(launch_adjoint_pm(*h, nb, h->hk, out + (size_t)b0 * h->n_alm, st), "adjoint pair-mean term");
+            // the Legendre sums' workspace is free once the transposed sums are done
+            CK(launch_adjoint_pm(*h, nb, h->hk, out + (size_t)b0 * h->n_alm, h->delta, st), "adjoint pair-mean term");
         }
     }
     return MODAL_OK;

@@ -220,7 +220,8 @@ size_t adjoint_v_workspace_bytes(const Plan& pl, int chunk);
 cudaError_t launch_adjoint_v(Plan& pl, int B, const float* hk, float* maps, cudaStream_t st);
 size_t adjoint_pm_workspace_bytes(const Plan& pl, int chunk);
 cudaError_t build_adjoint_pm_table(Plan& pl, cudaStream_t st);
-cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, cudaStream_t st);
+// scratch: B n_alm float2 (the correction in l-major order before it is subtracted)
+cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, float2* scratch, cudaStream_t st);
 // k_ring_linear.cu
 cudaError_t launch_pair_ring(Plan& pl, const float* maps, int B, cudaStream_t st);
 cudaError_t launch_ring_finalize(Plan& pl, cudaStream_t st);
