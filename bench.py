@@ -198,7 +198,11 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
         "ring_r2c": ("hbm", delta_bytes + map_bytes, launches),
         "adjoint_pixel": ("tensor" if tensor_peak else "alu", 2.0 * P * n_pair * npix * chunk, launches),
         "cubic": ("alu", 2.0 * n_max * npix * chunk, launches),
-        "linear_gemm": ("tensor" if tensor_peak else "alu", 2.0 * n_pair * P * npix * chunk, launches),
+        # linear term: split plans sum conj(F_c) a_lm in harmonic space (the pair-mean table of
+        # n_pair x n_alm complex64 read once per launch, the a_lm once); the FP32 plan runs the
+        # pixel-space product (one multiply-add per pair, basis function and pixel)
+        "linear_term": (("hbm", (n_pair + chunk) * n_alm * 8.0, launches) if tensor_peak
+                        else ("alu", 2.0 * n_pair * P * npix * chunk, launches)),
         "pair_means": ("hbm", map_bytes + 2.0 * n_pair * npix * 8, launches),
         "legendre_prep": ("hbm", chunk * n_alm * 8.0 + chunk * P * 2 * n_alm * 2 * 2.0, nsynth * launches),
         "legendre_adjoint_prep": ("hbm", 2.0 * delta_bytes, launches),
@@ -214,7 +218,7 @@ def stage_rooflines(prec, L, R, nphi, P, n_max, n_pair, chunk, B, prof, n_steps,
             peak, unit, achieved = hbm, "GB/s", total / (ms / 1e3) / 1e9
             src = "measured HBM copy"
         elif bound == "tensor":
-            tf32x3 = stage in ("linear_gemm", "adjoint_pixel") or prec == "3xtf32"   # these run 3xTF32
+            tf32x3 = stage == "adjoint_pixel" or prec == "3xtf32"   # these run 3xTF32
             tp = tf32 / 3.0 if tf32x3 else tensor_peak
             peak, unit, achieved = tp, "TFLOP/s", total / (ms / 1e3) / 1e12
             src = tf32_src if tf32x3 else "measured bf16 sustained / %g products per useful MAC" % split[prec]

@@ -283,12 +283,10 @@ modal_status modal_set_chunk(modal_h h, int chunk);
  *                  the FP32 plan)
  *   cubic_ctas     CTAs per map of the cubic and quartic sums (split-K over pixels),
  *                  [1, max(1, npix / 128)]
- *   linear_ranges  pixel ranges (split-K) of the tensor-core linear-term product,
- *                  [1, 8 x the device's SM count] (default: the SM count)
  *   ms             output of modal_autotune: the winning coefficient-pass time (ignored
  *                  by modal_set_tuning) */
 typedef struct modal_tuning {
-    int chunk, legendre_maps, cubic_ctas, linear_ranges;
+    int chunk, legendre_maps, cubic_ctas;
     float ms;
 } modal_tuning;
 modal_status modal_get_tuning(modal_h h, modal_tuning* t);
@@ -298,7 +296,7 @@ modal_status modal_get_tuning(modal_h h, modal_tuning* t);
 modal_status modal_set_tuning(modal_h h, const modal_tuning* t);
 /* Autotuner: times modal_cubic(h, alm, B, use_linear, ...) (the coefficient pass: synthesis,
  * cubic sums and the linear term) on the caller's maps for candidate settings of each
- * field in turn (legendre_maps, cubic_ctas, linear_ranges, chunk), CUDA events on
+ * field in turn (legendre_maps, cubic_ctas, chunk), CUDA events on
  * `stream`, one warm-up and the better of two timed calls per candidate, and keeps a
  * candidate only if it is at least 1 % faster than the best so far.  Leaves the plan on
  * the winning tuning and writes it to *best (best->ms = its time).  alm: dev [B][n_alm],

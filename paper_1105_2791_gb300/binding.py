@@ -57,11 +57,10 @@ class modal_info(ctypes.Structure):
 
 
 class modal_tuning(ctypes.Structure):
-    _fields_ = [("chunk", c_int), ("legendre_maps", c_int), ("cubic_ctas", c_int), ("linear_ranges", c_int),
-                ("ms", c_float)]
+    _fields_ = [("chunk", c_int), ("legendre_maps", c_int), ("cubic_ctas", c_int), ("ms", c_float)]
 
 
-TUNING_FIELDS = ("chunk", "legendre_maps", "cubic_ctas", "linear_ranges")
+TUNING_FIELDS = ("chunk", "legendre_maps", "cubic_ctas")
 
 _LIB = None
 
@@ -269,8 +268,7 @@ PEAK_KINDS = {"fp32_simt": 0, "fp64_simt": 1, "tf32_tensor": 2, "f16_tensor": 3,
 
 
 def _tuning_dict(t):
-    return {"chunk": t.chunk, "legendre_maps": t.legendre_maps, "cubic_ctas": t.cubic_ctas,
-            "linear_ranges": t.linear_ranges, "ms": float(t.ms)}
+    return {"chunk": t.chunk, "legendre_maps": t.legendre_maps, "cubic_ctas": t.cubic_ctas, "ms": float(t.ms)}
 
 
 def modal_get_tuning(h):

@@ -10,13 +10,9 @@
 //              MMAs per pixel tile (two K steps of 8 tf32, hi*hi + hi*lo + lo*hi) at the wide
 //              N where an MMA instruction is cheapest per flop; the epilogue forms U^M_t from
 //              V in FP32 and writes it over the maps.
-//   mean part  U^pm_t(x) = sum_c h_{t,c} W_x <c>_x depends on the map only through h.  The
-//              rest of the adjoint (ring r2c, transposed Legendre sums, filter) is linear, so
-//              its image is sum_c K_c(l) F_c[lm] with F_c the adjoint transform of the
-//              weighted pair-mean row W<c> (without the filter), built once per finalised
-//              mean, and K_c(l) = sum_t f_t(l) h_{t,c}: a 136-term sum per coefficient instead
-//              of a 2176-term sum per pixel.  launch_adjoint_pm subtracts it from the
-//              gradient after the transposed Legendre sums.
+//   mean part  U^pm_t(x) = sum_c h_{t,c} W_x <c>_x depends on the map only through h; it is
+//              applied in harmonic space after the transposed Legendre sums
+//              (k_pm_harmonic.cu: launch_adjoint_pm).
 //
 // Every wait is bounded as in the Legendre kernels; on expiry the kernel records
 // MODAL_DEVERR_TIMEOUT and its roles drain.
@@ -27,7 +23,6 @@
 #include <cuda.h>
 #include <algorithm>
 #include <mutex>
-#include <vector>
 
 namespace modal {
 
@@ -45,8 +40,6 @@ constexpr int AV_ABUF = 2 * AV_AT;                // A operand of one group: [hi
 constexpr int AV_STAGES = 6;                      // map tiles in flight (TMA ring)
 constexpr int AV_MT = AV_PM * 128 * 4;            // one map tile: 16 rows (p) x 128 pixels (8 KB)
 static_assert(AV_SBO == TC_SBO, "the operand tiles use the shared descriptor geometry");
-constexpr int AP_MAPS = 32;                       // maps per block of the pair-mean gradient kernel
-constexpr int AP_THREADS = 128;                   // m values per block of that kernel
 
 // Round-to-nearest tf32 (ties away from zero) by integer arithmetic on the float bits, and
 // the remainder rounded the same way: x ~ hi + lo with both exact in tf32.
@@ -352,201 +345,6 @@ cudaError_t launch_adjoint_v(Plan& pl, int B, const float* hk, float* maps, cuda
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
-}
-
-// ------------------------------------------------------------------ pair-mean part
-__host__ __device__ inline int64_t av_lidx(int64_t l, int64_t m) { return l * (l + 1) / 2 + m; }
-
-// in[c][x] = W_x <c>_x
-__global__ void k_adjpm_weighted(int64_t npix, int n_pair, const float* __restrict__ W, const float* __restrict__ pm,
-                                 float* __restrict__ out) {
-    const int64_t n = (int64_t)n_pair * npix;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = W[i % npix] * pm[i];
-}
-
-// F[c][l (l+1)/2 + m] = in[c][alm index (l, m)]: the l-major copy read by k_adjpm_grad
-__global__ void k_adjpm_lmajor(int L, int64_t n_alm, const float2* __restrict__ in, float2* __restrict__ F) {
-    const int c = blockIdx.y;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_alm; i += (int64_t)gridDim.x * blockDim.x) {
-        // i = m (2 L + 3 - m) / 2 + (l - m): recover m by the closed form, then correct by one
-        int m = (int)((2.0 * L + 3.0 - sqrt((2.0 * L + 3.0) * (2.0 * L + 3.0) - 8.0 * (double)i)) / 2.0);
-        m = max(0, min(L, m));
-        while (m > 0 && d_alm_index(m, m, L) > i) --m;
-        while (m < L && d_alm_index(m + 1, m + 1, L) <= i) ++m;
-        const int l = m + (int)(i - d_alm_index(m, m, L));
-        F[(int64_t)c * n_alm + av_lidx(l, m)] = in[(int64_t)c * n_alm + i];
-    }
-}
-
-cudaError_t build_adjoint_pm_table(Plan& pl, cudaStream_t st) {
-    if (!pl.pair_mean) return cudaErrorInvalidValue;
-    if (!pl.adj_pm) {
-        cudaError_t e = cudaMalloc(&pl.adj_pm, (size_t)pl.n_pair * pl.n_alm * sizeof(float2));
-        if (e != cudaSuccess) {
-            pl.adj_pm = nullptr;
-            return e;
-        }
-        pl.device_bytes += (size_t)pl.n_pair * pl.n_alm * sizeof(float2);
-        ++pl.generation;
-        // blocks of k_adjpm_grad: (l, m block) packed as l << 8 | block, largest l first
-        std::vector<int> blk;
-        for (int l = pl.lmax; l >= 0; --l)
-            for (int q = 0; q * AP_THREADS <= l; ++q) blk.push_back(l << 8 | q);
-        e = cudaMalloc(&pl.adj_pm_blk, blk.size() * sizeof(int));
-        if (e != cudaSuccess) {
-            pl.adj_pm_blk = nullptr;
-            return e;
-        }
-        pl.device_bytes += blk.size() * sizeof(int);
-        pl.adj_pm_nblk = (int)blk.size();
-        e = cudaMemcpy(pl.adj_pm_blk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return e;
-    }
-    const size_t L1 = pl.lmax + 1;
-    float* win = nullptr;
-    float2* ut = nullptr;
-    float2* fm = nullptr;
-    cudaError_t e = cudaMallocAsync(&win, (size_t)pl.n_pair * pl.npix * sizeof(float), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&ut, (size_t)pl.n_pair * L1 * 2 * pl.RH * sizeof(float2), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&fm, (size_t)pl.n_pair * pl.n_alm * sizeof(float2), st);
-    if (e == cudaSuccess) {
-        k_adjpm_weighted<<<pl.nsm * 8, 256, 0, st>>>(pl.npix, pl.n_pair, pl.W, pl.pair_mean, win);
-        note_launch(pl);
-        e = cudaGetLastError();
-    }
-    // the adjoint's own transforms without the filter: ring r2c (no ring weights: W is in
-    // the rows), then the transposed Legendre sums of each row
-    if (e == cudaSuccess) e = launch_ring_r2c(pl, win, pl.n_pair, nullptr, ut, nullptr, st);
-    if (e == cudaSuccess) e = launch_legendre_adjoint_simt(pl, ut, pl.n_pair, nullptr, 1, fm, st);
-    if (e == cudaSuccess) {
-        k_adjpm_lmajor<<<dim3(std::max(1, std::min(pl.nsm * 2, (int)((pl.n_alm + 255) / 256))), pl.n_pair), 256, 0, st>>>(
-            pl.lmax, pl.n_alm, fm, pl.adj_pm);
-        note_launch(pl);
-        e = cudaGetLastError();
-    }
-    if (win) cudaFreeAsync(win, st);
-    if (ut) cudaFreeAsync(ut, st);
-    if (fm) cudaFreeAsync(fm, st);
-    if (e == cudaSuccess) pl.adj_pm_ready = 1;
-    return e;
-}
-
-// K[l][b][c] = sum_t f_t(l) h_{b,t,c}
-__global__ void k_adjpm_k(int L, int P, int n_pair, int B, const float* __restrict__ filt, const float* __restrict__ hk,
-                          float* __restrict__ K) {
-    const int64_t n = (int64_t)(L + 1) * B * n_pair;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % n_pair);
-        const int b = (int)((i / n_pair) % B);
-        const int l = (int)(i / ((int64_t)n_pair * B));
-        float s = 0.f;
-        for (int t = 0; t < P; ++t) s = fmaf(filt[(int64_t)t * (L + 1) + l], hk[((int64_t)b * P + t) * n_pair + c], s);
-        K[i] = s;
-    }
-}
-
-// T[b][l (l+1)/2 + m] = c_m sum_c K[l][b][c] F_c[lm] for up to AP_MAPS maps per block; block =
-// (one l, AP_THREADS consecutive m), the largest l first so that the longest rows start early.
-// K[l] sits in shared memory as [c][b], read four maps per broadcast load; T is l-major like
-// F, so both the loads of F and the stores of T are contiguous in m.
-__global__ void __launch_bounds__(AP_THREADS) k_adjpm_grad(int n_pair, int B, int64_t n_alm, const int* __restrict__ blk_l,
-                                                           const float* __restrict__ K, const float2* __restrict__ F,
-                                                           float2* __restrict__ T) {
-    __shared__ __align__(16) float sK[136 * AP_MAPS];
-    const int code = blk_l[blockIdx.x];
-    const int l = code >> 8, m = ((code & 0xff) * AP_THREADS) + threadIdx.x;
-    const int bg = blockIdx.y * AP_MAPS;
-    const int nb = min(AP_MAPS, B - bg);
-    for (int i = threadIdx.x; i < n_pair * AP_MAPS; i += blockDim.x) {
-        const int c = i / AP_MAPS, b = i % AP_MAPS;
-        sK[i] = (b < nb) ? K[((int64_t)l * B + bg + b) * n_pair + c] : 0.f;
-    }
-    __syncthreads();
-    if (m > l) return;
-    float2 acc[AP_MAPS];
-#pragma unroll
-    for (int b = 0; b < AP_MAPS; ++b) acc[b] = make_float2(0.f, 0.f);
-    const float2* f = F + av_lidx(l, m);
-    // eight pair rows per round: their loads are all in flight before the first is used
-    for (int c0 = 0; c0 < n_pair; c0 += 8) {
-        float2 v8[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v8[i] = (c0 + i < n_pair) ? f[(int64_t)(c0 + i) * n_alm] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int c = min(c0 + i, n_pair - 1);       // a row past the end carries v = 0
-            const float2 v = v8[i];
-            const float4* k4 = reinterpret_cast<const float4*>(sK + c * AP_MAPS);
-#pragma unroll
-            for (int q = 0; q < AP_MAPS / 4; ++q) {
-                const float4 k = k4[q];
-                acc[4 * q + 0].x = fmaf(k.x, v.x, acc[4 * q + 0].x); acc[4 * q + 0].y = fmaf(k.x, v.y, acc[4 * q + 0].y);
-                acc[4 * q + 1].x = fmaf(k.y, v.x, acc[4 * q + 1].x); acc[4 * q + 1].y = fmaf(k.y, v.y, acc[4 * q + 1].y);
-                acc[4 * q + 2].x = fmaf(k.z, v.x, acc[4 * q + 2].x); acc[4 * q + 2].y = fmaf(k.z, v.y, acc[4 * q + 2].y);
-                acc[4 * q + 3].x = fmaf(k.w, v.x, acc[4 * q + 3].x); acc[4 * q + 3].y = fmaf(k.w, v.y, acc[4 * q + 3].y);
-            }
-        }
-    }
-    const float cm = (m == 0) ? 1.f : 2.f;
-    const int64_t li = av_lidx(l, m);
-#pragma unroll
-    for (int b = 0; b < AP_MAPS; ++b)
-        if (b < nb) T[(int64_t)(bg + b) * n_alm + li] = make_float2(cm * acc[b].x, m > 0 ? cm * acc[b].y : 0.f);
-}
-
-// grad[b][alm index (l, m)] -= T[b][l (l+1)/2 + m], through 32 x 32 tiles of (l, m) in shared
-// memory so that T is read contiguous in m and grad written contiguous in l.
-__global__ void __launch_bounds__(256) k_adjpm_apply(int L, int64_t n_alm, const float2* __restrict__ T,
-                                                     float2* __restrict__ grad) {
-    __shared__ float2 tile[32][33];
-    const int nlb = (L + 32) / 32;
-    const int lb = blockIdx.x / nlb, mb = blockIdx.x % nlb;
-    if (mb > lb) return;
-    const int b = blockIdx.y;
-    const float2* tb = T + (int64_t)b * n_alm;
-    float2* gb = grad + (int64_t)b * n_alm;
-    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-    for (int i = ty; i < 32; i += 8) {                     // row l = 32 lb + i, column m = 32 mb + tx
-        const int l = 32 * lb + i, m = 32 * mb + tx;
-        tile[tx][i] = (l <= L && m <= l) ? tb[av_lidx(l, m)] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    for (int j = ty; j < 32; j += 8) {                     // row m = 32 mb + j, column l = 32 lb + tx
-        const int m = 32 * mb + j, l = 32 * lb + tx;
-        if (l <= L && m <= l) {
-            float2* o = gb + d_alm_index(l, m, L);
-            const float2 d = tile[j][tx];
-            float2 r = *o;
-            r.x -= d.x;
-            r.y -= d.y;
-            *o = r;
-        }
-    }
-}
-
-size_t adjoint_pm_workspace_bytes(const Plan& pl, int chunk) {
-    return pl.prec == MODAL_FP32 ? 0 : (size_t)(pl.lmax + 1) * chunk * pl.n_pair * sizeof(float);
-}
-
-cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, float2* scratch, cudaStream_t st) {
-    if (B == 0) return cudaSuccess;
-    if (!pl.adj_pm_ready || !pl.adj_pmk || !pl.adj_pm_blk || B > pl.chunk || pl.n_pair > 136) return cudaErrorInvalidValue;
-    const int64_t n = (int64_t)(pl.lmax + 1) * B * pl.n_pair;
-    k_adjpm_k<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, st>>>(pl.lmax, pl.P, pl.n_pair, B, pl.filt, hk,
-                                                                                  pl.adj_pmk);
-    note_launch(pl);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_adjpm_grad<<<dim3(pl.adj_pm_nblk, (B + AP_MAPS - 1) / AP_MAPS), AP_THREADS, 0, st>>>(
-        pl.n_pair, B, pl.n_alm, pl.adj_pm_blk, pl.adj_pmk, pl.adj_pm, scratch);
-    note_launch(pl);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int nlb = (pl.lmax + 32) / 32;
-    k_adjpm_apply<<<dim3(nlb * nlb, B), 256, 0, st>>>(pl.lmax, pl.n_alm, scratch, grad);
-    note_launch(pl);
-    return cudaGetLastError();
 }
 
 }  // namespace modal

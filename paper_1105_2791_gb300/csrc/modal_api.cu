@@ -184,7 +184,7 @@ static modal_status alloc_workspace_buffers(modal_plan* pl, int chunk) {
     CK(dalloc(pl, &pl->vring, (size_t)chunk * pl->P * pl->nrings), "workspace vring");
     // cubic partials: [chunk][cubic_ctas][n_max]; linear partials: [ksplit][n_pair][chunk*P]
     const size_t cub = (size_t)chunk * pl->cubic_ctas * pl->n_max;
-    const size_t lin = (size_t)std::max(pl->lin_ksplit, std::max(pl->nsm, pl->lt_ranges)) * pl->n_pair * chunk * pl->P;
+    const size_t lin = (size_t)std::max(pl->lin_ksplit, 1) * pl->n_pair * chunk * pl->P;
     pl->partial_elems = cub + lin;
     CK(dalloc(pl, &pl->partial, pl->partial_elems), "workspace partial");
     {
@@ -246,7 +246,7 @@ static void destroy_plan(modal_plan* pl) {
     free_workspace(pl);
     dfree(pl->lam); dfree(pl->filt); dfree(pl->W); dfree(pl->wring); dfree(pl->twiddle);
     dfree(pl->modeidx); dfree(pl->tiles); dfree(pl->pair_ab);
-    dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->lin_bsplit); dfree(pl->S1); dfree(pl->S2);
+    dfree(pl->pair_sum); dfree(pl->pair_mean); dfree(pl->S1); dfree(pl->S2);
     dfree(pl->ring_sum); dfree(pl->ring_mean);
     dfree(pl->solve_ws); dfree(pl->d_err); dfree(pl->adj_pm); dfree(pl->adj_pm_blk);
     dfree(pl->qt.tiles); dfree(pl->qt.idx); dfree(pl->qt.modes); dfree(pl->qt.pa); dfree(pl->qt.pb);
@@ -372,7 +372,6 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
         pl->lin_ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(ks, 128));
         cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, pl->dev);
         pl->nsm = std::max(pl->nsm, 1);
-        pl->lt_ranges = pl->nsm;
         pl->tc_maps = 8;                                   // N = 16 P columns per Legendre item
     }
 
@@ -561,7 +560,6 @@ modal_status modal_get_tuning(modal_h h, modal_tuning* t) {
     t->chunk = h->chunk;
     t->legendre_maps = h->tc_maps;
     t->cubic_ctas = h->cubic_ctas;
-    t->linear_ranges = h->lt_ranges;
     t->ms = 0.f;
     return MODAL_OK;
 }
@@ -575,19 +573,15 @@ modal_status modal_set_tuning(modal_h h, const modal_tuning* t) {
     const int64_t max_ctas = std::max<int64_t>(1, h->npix / 128);
     if (t->cubic_ctas < 1 || t->cubic_ctas > max_ctas)
         return set_error(MODAL_EINVAL, "cubic_ctas must be in [1, max(1, npix / 128)]");
-    if (t->linear_ranges < 1 || t->linear_ranges > 8 * h->nsm)
-        return set_error(MODAL_EINVAL, "linear_ranges must be in [1, 8 x SM count]");
     CK(cudaDeviceSynchronize(), "set_tuning sync");
-    const int old_chunk = h->chunk, old_maps = h->tc_maps, old_ctas = h->cubic_ctas, old_ranges = h->lt_ranges;
+    const int old_chunk = h->chunk, old_maps = h->tc_maps, old_ctas = h->cubic_ctas;
     h->tc_maps = t->legendre_maps;
     h->cubic_ctas = t->cubic_ctas;
-    h->lt_ranges = t->linear_ranges;
     const modal_status s = alloc_workspace(h, t->chunk);
     if (s == MODAL_OK) return MODAL_OK;
     const std::string why = modal_last_error();
     h->tc_maps = old_maps;
     h->cubic_ctas = old_ctas;
-    h->lt_ranges = old_ranges;
     if (old_chunk >= 1 && alloc_workspace(h, old_chunk) == MODAL_OK)
         return set_error(s, why + " (the previous tuning is kept)");
     free_workspace(h);
@@ -629,8 +623,7 @@ modal_status modal_autotune(modal_h h, const void* alm, int B, int use_linear, m
     // a candidate replaces the incumbent only if it is at least 1 % faster; one that cannot
     // be set (its workspace does not fit) is skipped
     auto consider = [&](modal_tuning cand) -> modal_status {
-        if (cand.chunk == cur.chunk && cand.legendre_maps == cur.legendre_maps && cand.cubic_ctas == cur.cubic_ctas &&
-            cand.linear_ranges == cur.linear_ranges)
+        if (cand.chunk == cur.chunk && cand.legendre_maps == cur.legendre_maps && cand.cubic_ctas == cur.cubic_ctas)
             return MODAL_OK;
         if (modal_set_tuning(h, &cand) != MODAL_OK) return modal_set_tuning(h, &cur);
         float ms = 0.f;
@@ -664,15 +657,6 @@ modal_status modal_autotune(modal_h h, const void* alm, int B, int use_linear, m
             if (c > max_ctas) continue;
             modal_tuning t = cur;
             t.cubic_ctas = c;
-            s = consider(t);
-        }
-    }
-    if (s == MODAL_OK && use_linear && h->lin_mode == MODAL_LINEAR_PIXEL && h->prec != MODAL_FP32) {
-        const int rs[] = {std::max(1, nsm / 2), nsm, 2 * nsm, 4 * nsm};
-        for (int r : rs) {
-            if (s != MODAL_OK) break;
-            modal_tuning t = cur;
-            t.linear_ranges = r;
             s = consider(t);
         }
     }
@@ -725,15 +709,13 @@ modal_status modal_analyze(modal_h h, const float* maps, int B, void* alm, void*
     return MODAL_OK;
 }
 
-// The tensor-core linear term reads W <pair> pre-split into tf32 hi/lo; rebuilt whenever
+// Split plans with per-pixel means take the linear term and the adjoint's pair-mean part in
+// harmonic space, from the adjoint transforms of the weighted pair-mean rows; rebuilt whenever
 // the per-pixel mean is finalised.
-static modal_status refresh_linear_presplit(modal_plan* h, cudaStream_t st) {
+static modal_status refresh_pm_table(modal_plan* h, cudaStream_t st) {
+    h->adj_pm_ready = 0;
     if (h->prec == MODAL_FP32 || h->lin_mode == MODAL_LINEAR_RING) return MODAL_OK;
-    if (!h->lin_bsplit) {
-        ++h->generation;
-        CK(dalloc(h, &h->lin_bsplit, linear_presplit_bytes(*h)), "pre-split pair-mean panel");
-    }
-    CK(launch_linear_presplit(*h, st), "pair-mean panel split");
+    CK(build_pm_table(*h, st), "pair-mean harmonic table");
     return MODAL_OK;
 }
 
@@ -764,10 +746,9 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
         STAGE(h, ST_PAIRS, st);
         if (ring) CK(launch_ring_finalize(*h, st), "ring pair means");
         else CK(launch_pair_finalize(*h, st), "pair finalize");
-        const modal_status ps = refresh_linear_presplit(h, st);
+        const modal_status ps = refresh_pm_table(h, st);
         if (ps != MODAL_OK) return ps;
         h->lin_final = 1;
-        h->adj_pm_ready = 0;
     }
     return MODAL_OK;
 }
@@ -793,8 +774,9 @@ static modal_status cubic_impl(modal_h h, const void* alm, int B, int use_linear
             } else if (h->prec == MODAL_FP32) {
                 CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm");
             } else {
-                CK(launch_linear_tc(*h, h->maps, nb, lin, st), "linear gemm");
-                splits = linear_tc_splits(*h, nb);
+                // from the a_lm and the harmonic pair-mean table (the same finite sums)
+                CK(launch_linear_harmonic(*h, a + (size_t)b0 * h->n_alm, nb, lin, st), "linear term (harmonic)");
+                splits = 1;
             }
         }
         { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, splits, beta + (size_t)b0 * h->n_max, st), "beta finalize"); }
@@ -1122,7 +1104,7 @@ static modal_status backward_impl(modal_h h, const void* alm, int B, const doubl
     const bool pm_late = use_linear && !ring && h->prec != MODAL_FP32;
     if (pm_late && !h->adj_pm_ready) {
         STAGE(h, ST_OTHER, st);
-        CK(build_adjoint_pm_table(*h, st), "adjoint pair-mean table");
+        CK(build_pm_table(*h, st), "pair-mean harmonic table");
     }
     for (int b0 = 0; b0 < B; b0 += h->chunk) {
         const int nb = std::min(h->chunk, B - b0);
@@ -1388,7 +1370,7 @@ modal_status modal_load_state(modal_h h, const char* path) {
     if (hd.has_pairs && hd.lin_final && h->n_lin > 0) {
         if (hd.has_pairs == 2) CK(launch_ring_finalize(*h, 0), "ring pair means");
         else CK(launch_pair_finalize(*h, 0), "pair finalize");
-        const modal_status ps = refresh_linear_presplit(h, 0);
+        const modal_status ps = refresh_pm_table(h, 0);
         if (ps != MODAL_OK) return ps;
         CK(cudaDeviceSynchronize(), "load sync");
         h->lin_final = 1;
@@ -1397,7 +1379,7 @@ modal_status modal_load_state(modal_h h, const char* path) {
 }
 
 static const char* kStageNames[MODAL_NSTAGES] = {
-    "legendre", "ring_c2r", "cubic", "linear_gemm", "beta_finalize", "pair_means",
+    "legendre", "ring_c2r", "cubic", "linear_term", "beta_finalize", "pair_means",
     "cov_accumulate", "solve", "adjoint_pixel", "ring_r2c", "legendre_adjoint", "other",
     "legendre_prep", "legendre_adjoint_prep", "quartic"};
 

@@ -99,7 +99,6 @@ struct Plan {
     // Monte Carlo accumulators
     double* pair_sum = nullptr;  // [n_pair][npix]
     float* pair_mean = nullptr;  // [n_pair][npix]
-    char* lin_bsplit = nullptr;  // W <pair> split into tf32 hi/lo per 32-pixel stage (tensor-core linear term)
     long long n_lin = 0;
     int lin_final = 0;
     double* S1 = nullptr;        // [n_max]
@@ -114,7 +113,6 @@ struct Plan {
     size_t partial_elems = 0;
     int cubic_ctas = 0;          // CTAs per map in the cubic and quartic kernels (tunable)
     int lin_ksplit = 0;          // K splits in the linear-term GEMM (SIMT)
-    int lt_ranges = 0;           // pixel ranges of the tensor-core linear-term GEMM (tunable)
     int tc_maps = 8;             // maps per work item of the tensor-core Legendre kernel (tunable)
     int nsm = 0;                 // SMs of the plan's device
     // maps of the last modal_cubic call kept in `maps` for modal_backward_retained
@@ -123,7 +121,7 @@ struct Plan {
     int kept_B = 0;
     float* hk = nullptr;         // [chunk][P][n_pair] adjoint weights
     char* adj_gops = nullptr;    // [chunk] tf32 hi/lo G operands of the tensor-core adjoint pixel weights
-    float* adj_pmk = nullptr;    // [lmax+1][chunk][n_pair] filter-weighted adjoint weights K (pair-mean part)
+    float* adj_pmk = nullptr;    // per chunk: K of the adjoint's pair-mean part or S of the harmonic linear term
     float2* adj_pm = nullptr;    // [n_pair][n_alm] (l-major) adjoint transform of each weighted pair-mean row
     int adj_pm_ready = 0;        // adj_pm holds the current pair means
     int* adj_pm_blk = nullptr;   // blocks of the pair-mean gradient kernel: l << 8 | m block, largest l first
@@ -199,10 +197,6 @@ cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmaps_p, cons
 // k_cubic.cu
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
-cudaError_t launch_linear_tc(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);   // k_linear_tc.cu
-size_t linear_presplit_bytes(const Plan& pl);
-int linear_tc_splits(const Plan& pl, int B);   // K splits of the tensor-core linear term for B maps
-cudaError_t launch_linear_presplit(Plan& pl, cudaStream_t st);   // after each finalised pixel mean
 // lin_splits: K splits summed from lin_partial ([lin_splits][n_pair][B P])
 cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* cub_partial,
                                  const double* lin_partial, int lin_splits, double* beta, cudaStream_t st);
@@ -214,13 +208,15 @@ cudaError_t launch_adjoint_weights(Plan& pl, const double* g, int B, float* hk, 
 cudaError_t launch_adjoint_u(Plan& pl, const float* maps, int B, const float* hk, int use_linear,
                              float* u, cudaStream_t st);
 // k_adjoint_tc.cu: the same pixel weights as a tcgen05 product (split plans); in place on maps
-// k_adjoint_v.cu: the map part of the pixel weights (in place over the maps) and the
-// pair-mean part applied to the gradient after the transposed Legendre sums.
+// k_adjoint_v.cu: the map part of the pixel weights (in place over the maps).
 size_t adjoint_v_workspace_bytes(const Plan& pl, int chunk);
 cudaError_t launch_adjoint_v(Plan& pl, int B, const float* hk, float* maps, cudaStream_t st);
+// k_pm_harmonic.cu: the pair means in harmonic space (split plans, per-pixel means): the table
+// of adjoint-transformed weighted pair-mean rows (after each finalised mean), the linear term
+// from a_lm, and the adjoint's pair-mean part applied to the gradient.
 size_t adjoint_pm_workspace_bytes(const Plan& pl, int chunk);
-cudaError_t build_adjoint_pm_table(Plan& pl, cudaStream_t st);
-// scratch: B n_alm float2 (the correction in l-major order before it is subtracted)
+cudaError_t build_pm_table(Plan& pl, cudaStream_t st);
+cudaError_t launch_linear_harmonic(Plan& pl, const float2* alm, int B, double* lin, cudaStream_t st);
 cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, float2* scratch, cudaStream_t st);
 // k_ring_linear.cu
 cudaError_t launch_pair_ring(Plan& pl, const float* maps, int B, cudaStream_t st);

@@ -3,9 +3,8 @@
 The library's autotuner (include/modal.h: modal_autotune) times candidate launch shapes of
 a plan on the caller's maps; this module keys the winner by everything that decides
 which shape wins (device name, l_max, P, grid, precision, batch size, linear-term mode)
-and stores it in a JSON object {key: {"chunk", "legendre_maps", "cubic_ctas",
-"linear_ranges", "ms"}}, so that later plans of the same configuration take the tuned
-shapes without timing.  Host-side bookkeeping only: no part of the method runs here.
+and stores it in a JSON object {key: {"chunk", "legendre_maps", "cubic_ctas", "ms"}}, so
+that later plans of the same configuration take the tuned shapes without timing.  Host-side bookkeeping only: no part of the method runs here.
 """
 from __future__ import annotations
 

@@ -15,7 +15,7 @@ PEAKS = {"hbm_gbs": 6683.8, "bf16_tflops_sustained": 1710.9}
 
 
 def _prof(ms=10.0):
-    stages = ["legendre", "legendre_adjoint", "ring_c2r", "ring_r2c", "adjoint_pixel", "cubic", "linear_gemm",
+    stages = ["legendre", "legendre_adjoint", "ring_c2r", "ring_r2c", "adjoint_pixel", "cubic", "linear_term",
               "pair_means", "legendre_prep", "legendre_adjoint_prep"]
     return {s: (ms, 1) for s in stages}
 
@@ -38,10 +38,16 @@ def test_algorithmic_work_per_launch_at_the_bench_workload():
     assert float(rows["ring_c2r"]["per_launch"].split()[0]) == pytest.approx(c2r, rel=1e-3)
     assert float(rows["ring_r2c"]["per_launch"].split()[0]) == pytest.approx(c2r, rel=1e-3)
     assert c2r == pytest.approx(33.19, abs=0.01)
-    # cubic: one multiply-add per mode and pixel; linear term and adjoint: per pair, basis function, pixel
+    # cubic: one multiply-add per mode and pixel; adjoint: per pair, basis function, pixel
     assert float(rows["cubic"]["per_launch"].split()[0]) == pytest.approx(2 * N_MAX * npix * CHUNK, rel=1e-3)
-    assert float(rows["linear_gemm"]["per_launch"].split()[0]) == pytest.approx(2 * N_PAIR * P * npix * CHUNK,
-                                                                               rel=1e-3)
+    # linear term of a split plan: the pair-mean table (complex64 per pair and a_lm) and the a_lm
+    lin = (N_PAIR + CHUNK) * n_alm * 8 / 1e9
+    assert rows["linear_term"]["bound"] == "hbm"
+    assert float(rows["linear_term"]["per_launch"].split()[0]) == pytest.approx(lin, rel=1e-3)
+    # the FP32 plan's pixel-space product: one multiply-add per pair, basis function and pixel
+    f32 = _by_stage(bench.stage_rooflines("fp32", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS))
+    assert float(f32["linear_term"]["per_launch"].split()[0]) == pytest.approx(2 * N_PAIR * P * npix * CHUNK,
+                                                                              rel=1e-3)
     assert float(rows["adjoint_pixel"]["per_launch"].split()[0]) == pytest.approx(2 * P * N_PAIR * npix * CHUNK,
                                                                                  rel=1e-3)
     # pair sums: the maps once, the FP64 sums read and written
@@ -71,7 +77,7 @@ def test_launches_per_step_and_achieved_rates():
     assert c2r["peak"] == pytest.approx(6683.8) and c2r["frac"] == pytest.approx(c2r["achieved"] / 6683.8, rel=1e-3)
     # split FP16 runs three products per useful multiply-add; 3xTF32 at half the bf16 rate, three products
     assert three["legendre"]["peak"] == pytest.approx(1710.9 / 3, rel=1e-3)
-    assert three["linear_gemm"]["peak"] == pytest.approx(1710.9 / 6, rel=1e-3)
+    assert three["adjoint_pixel"]["peak"] == pytest.approx(1710.9 / 6, rel=1e-3)
     assert three["cubic"]["peak"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12, rel=1e-3)
     # rows come largest time first, and stages that did not run are left out
     prof2 = dict(prof)
@@ -84,7 +90,7 @@ def test_launches_per_step_and_achieved_rates():
 def test_traffic_only_for_the_captured_workload():
     rows = _by_stage(bench.stage_rooflines("fp16x3", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS))
     assert rows["ring_c2r"]["traffic"] == pytest.approx(16.53 + 16.74, abs=0.01)
-    assert rows["linear_gemm"]["traffic"] is None              # not captured at this workload
+    assert rows["linear_term"]["traffic"] is None              # not captured at this workload
     small = _by_stage(bench.stage_rooflines("fp16x3", 1000, 1001, 2048, P, N_MAX, N_PAIR, 8, 8, _prof(), 1, PEAKS))
     assert all(r["traffic"] is None for r in small.values())
 
@@ -120,7 +126,7 @@ def test_probed_peaks_replace_the_derived_ones():
     rows = _by_stage(bench.stage_rooflines("fp16x3", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,
                                            probe=probe))
     assert rows["cubic"]["peak"] == pytest.approx(70.0)
-    assert rows["linear_gemm"]["peak"] == pytest.approx(300.0) and rows["adjoint_pixel"]["peak"] == pytest.approx(300.0)
+    assert rows["adjoint_pixel"]["peak"] == pytest.approx(300.0)
     assert rows["legendre"]["peak"] == pytest.approx(1710.9 / 3, rel=1e-3)
     assert "measured in this run" in rows["cubic"]["peak_source"]
     tf = _by_stage(bench.stage_rooflines("3xtf32", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,

@@ -51,16 +51,16 @@ def test_every_legendre_tile_and_split_gives_the_same_beta(P):
     L, nb = 64, 12
     plan, a, sims, basis, cl, R, nphi = _setup(M, L, P, "fp16x3", nb, seed=400 + P)
     base = plan.tuning()
-    assert base["legendre_maps"] == 8 and base["linear_ranges"] >= 1
+    assert base["legendre_maps"] == 8 and base["cubic_ctas"] >= 1
     ref = plan.cubic(a, use_linear=True)
     gs = [g for g in range(1, 33) if (2 * P * g) % 16 == 0 and 2 * P * g <= 256]
     for g in gs:
         plan.set_tuning({"legendre_maps": g})
         assert plan.tuning()["legendre_maps"] == g
         assert _rel(plan.cubic(a, use_linear=True), ref) <= 5e-6, (P, g)
-    for ctas, ranges, chunk in [(1, 1, 5), (7, 3, 12), (64, 300, 3), (plan.npix // 128, 19, 8)]:
-        plan.set_tuning({"legendre_maps": gs[-1], "cubic_ctas": ctas, "linear_ranges": ranges, "chunk": chunk})
-        assert _rel(plan.cubic(a, use_linear=True), ref) <= 5e-6, (P, ctas, ranges, chunk)
+    for ctas, chunk in [(1, 5), (7, 12), (64, 3), (plan.npix // 128, 8)]:
+        plan.set_tuning({"legendre_maps": gs[-1], "cubic_ctas": ctas, "chunk": chunk})
+        assert _rel(plan.cubic(a, use_linear=True), ref) <= 5e-6, (P, ctas, chunk)
     # the largest Legendre tile against the FP64 oracle
     beta = plan.cubic(a, use_linear=True).cpu().numpy()
     mu, w = osh.gl_nodes(R)
@@ -82,7 +82,7 @@ def test_illegal_settings_are_refused_and_change_nothing():
     bad = [{"legendre_maps": 6},                  # 2 P G = 120: not a multiple of 16
            {"legendre_maps": 16},                 # 320 columns > 256
            {"legendre_maps": 0}, {"cubic_ctas": 0}, {"cubic_ctas": plan.npix // 128 + 1},
-           {"linear_ranges": 0}, {"linear_ranges": 10 ** 6}, {"chunk": 0}, {"chunk": 5000}]
+           {"chunk": 0}, {"chunk": 5000}]
     for t in bad:
         with pytest.raises(M.ModalError) as ei:
             plan.set_tuning(t)
@@ -126,7 +126,7 @@ def test_autotune_keeps_results_and_caches(tmp_path):
     best, how = plan.autotune(a, use_linear=True, cache=cache)
     assert how == "measured" and best["ms"] > 0
     cur = plan.tuning()
-    for k in ("chunk", "legendre_maps", "cubic_ctas", "linear_ranges"):
+    for k in ("chunk", "legendre_maps", "cubic_ctas"):
         assert cur[k] == best[k]
     assert best["chunk"] in (8, 16, chunk0) and 1 <= best["legendre_maps"] <= 8
     tuned = plan.cubic(a, use_linear=True)
@@ -143,7 +143,7 @@ def test_autotune_keeps_results_and_caches(tmp_path):
     plan2, a2, *_ = _setup(M, 200, 16, "fp16x3", 16, seed=460)
     best2, how2 = plan2.autotune(a2, use_linear=True, cache=cache)
     assert how2 == "cache"
-    for k in ("chunk", "legendre_maps", "cubic_ctas", "linear_ranges"):
+    for k in ("chunk", "legendre_maps", "cubic_ctas"):
         assert best2[k] == best[k] and plan2.tuning()[k] == best[k]
     assert torch.equal(plan2.cubic(a2, use_linear=True), plan.cubic(a, use_linear=True))
     plan.sync()

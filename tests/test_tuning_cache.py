@@ -10,7 +10,7 @@ from paper_1105_2791_gb300 import tuning as T
 
 
 def _entry(**kw):
-    e = {"chunk": 32, "legendre_maps": 8, "cubic_ctas": 512, "linear_ranges": 152, "ms": 51.25}
+    e = {"chunk": 32, "legendre_maps": 8, "cubic_ctas": 512, "ms": 51.25}
     e.update(kw)
     return e
 
@@ -42,7 +42,7 @@ def test_invalid_entries_are_not_used(tmp_path):
     assert T.valid_entry(_entry())
     assert not T.valid_entry({"chunk": 8})
     assert not T.valid_entry(_entry(cubic_ctas=0))
-    assert not T.valid_entry(_entry(linear_ranges="x"))
+    assert not T.valid_entry(_entry(legendre_maps="x"))
     bad = tmp_path / "bad.json"
     bad.write_text("[1, 2]")
     with pytest.raises(ValueError):
