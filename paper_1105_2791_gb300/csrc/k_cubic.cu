@@ -17,165 +17,211 @@ namespace modal {
 // panel against the map panel, one map per CTA row of the grid, the panel built in
 // shared memory tile by tile and never written to HBM.
 //
+// Tiles: 8 colex pairs (a pair group pg, pairs sorted by r, then p) x 4 values of s (a quad
+// sq); tiles entirely below the diagonal s < r are absent from the tile list.  A compute
+// item holds two tiles, either of one pair group and two quads (kind A: 8 pair values and
+// 2 x 4 map values per pixel for 32 packed FMAs) or of two pair groups and one quad (kind B:
+// 16 + 4 values); a tile left alone is paired with a quad of zeros.  The two halves of a
+// warp (16 lanes each) take one item each, of the same kind, so that a warp runs one path.
+//
 // Warp roles (named barriers, two shared-memory stages of CUB_TX pixels each):
-//   fill warps     one pixel per thread: the map values and W are prefetched two tiles
+//   fill warps     two pixels per thread: the map values and W are prefetched one tile
 //                  ahead in registers, the pair products of all colex pairs are formed
-//                  in registers and stored as float4 rows of the panel;
-//   compute warps  one register tile of 8 pairs x 4 values of s per thread and one of
-//                  `nl` pixel lanes; pairs in colex order (by r, then p), so that tiles
-//                  entirely below the diagonal s < r are absent from the tile list.
-// Panel row layout: [half][pair group][4] so that the two float4 of a tile sit in two
-// contiguous 16-byte runs across the warp; row stride 8 n_pg + 4 floats keeps the
-// per-thread float4 stores of the fill warps free of bank conflicts.  Per-CTA partial
-// sums go to `partial` (FP64) and are summed in a fixed order by k_beta_finalize.
-constexpr int CUB_TX = 128;                 // pixels per stage (= fill threads)
-constexpr int CUB_MS = 20;                  // row stride of the staged map values
-constexpr int CUB_MAXCOMP = 288;            // compute threads at most
-constexpr int CUB_THREADS = CUB_MAXCOMP + CUB_TX;
+//                  in registers and stored as float4 slots of the panel;
+//   compute warps  16 lanes per item, 8 pixels per lane per stage.
+// Stage layout, pixel fastest: [2 n_pg slots of 4 pairs][CUB_TX] float4, then
+// [n_sq + 1 quads of 4 map values][CUB_TX] float4 (the last quad is zero), so that the
+// fill threads' stores and the half-warps' loads are runs of consecutive float4.  Per-CTA
+// partial sums go to `partial` (FP64) and are summed in a fixed order by k_beta_finalize.
+constexpr int CUB_TX = 128;                 // pixels per stage
+constexpr int CUB_FILL = 64;                // fill threads (two pixels each)
+constexpr int CUB_MAXCOMP = 288;            // compute threads at most (18 items x 16 lanes)
+constexpr int CUB_THREADS = CUB_MAXCOMP + CUB_FILL;   // 11 warps: at most 3 per SM sub-partition
+constexpr int CUB_LANES = 16;               // lanes per item
 
 __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ __forceinline__ void named_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
+// items: [nslots] int2 (tile a, tile b); tile a < 0: idle slot; tile b < 0: tile a alone.
 template <int PM>
 __global__ void __launch_bounds__(CUB_THREADS, 1)
-k_cubic(int P, int n_pg, int ntiles, int nl, int ncomp, const int* __restrict__ tiles,
+k_cubic(int P, int n_pg, int n_sq, int ntiles, int ncomp, const int* __restrict__ tiles, const int2* __restrict__ items,
         const int* __restrict__ modeidx, int64_t npix, int64_t px_per_cta, const float* __restrict__ maps,
         const float* __restrict__ W, double* __restrict__ partial, int n_max) {
     extern __shared__ __align__(16) float smem[];
-    const int SU = 8 * n_pg + 4;
-    const int stage_floats = CUB_TX * (SU + CUB_MS);
+    const int nslot = 2 * n_pg;
+    const int stage_f4 = (nslot + n_sq + 1) * CUB_TX;              // float4 per stage
     const int b = blockIdx.y;
     const int tid = threadIdx.x;
-    const int nthr = ncomp + CUB_TX;
+    const int nthr = ncomp + CUB_FILL;
     const int64_t x_begin = (int64_t)blockIdx.x * px_per_cta;
     const int64_t x_end = min(npix, x_begin + px_per_cta);
     const int nch = (x_end > x_begin) ? (int)((x_end - x_begin + CUB_TX - 1) / CUB_TX) : 0;
     const float* mb = maps + (int64_t)b * P * npix;
+    float4* s4 = reinterpret_cast<float4*>(smem);
 
-    float acc[32];
+    // the zero quad of both stages
+    for (int i = tid; i < 2 * CUB_TX; i += nthr)
+        s4[(i / CUB_TX) * stage_f4 + (nslot + n_sq) * CUB_TX + i % CUB_TX] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+
+    float accA[32], accB[32];
 #pragma unroll
-    for (int e = 0; e < 32; ++e) acc[e] = 0.f;
-    const int tile = tid % ntiles, lane = tid / ntiles;
+    for (int e = 0; e < 32; ++e) accA[e] = accB[e] = 0.f;
+    const int lane16 = (tid % 32) % CUB_LANES;
+    const int slot_item = tid / CUB_LANES;
+    int2 it = make_int2(-1, -1);
 
     if (tid >= ncomp) {
         // ------------------------------------------------ fill warps
-        const int xl = tid - ncomp;
-        float cur[PM + 1], n1[PM + 1], n2[PM + 1];
-        auto load = [&](float* v, int k) {
-            const int64_t x = x_begin + (int64_t)k * CUB_TX + xl;
-            const bool in = k < nch && x < x_end;
+        const int xl = tid - ncomp;                                  // pixels xl and xl + CUB_FILL
+        float cur[2][PM + 1], n1[2][PM + 1];
+        auto load = [&](float (&v)[2][PM + 1], int k) {
 #pragma unroll
-            for (int p = 0; p < PM; ++p) v[p] = (in && p < P) ? mb[(int64_t)p * npix + x] : 0.f;
-            v[PM] = in ? W[x] : 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int64_t x = x_begin + (int64_t)k * CUB_TX + xl + h * CUB_FILL;
+                const bool in = k < nch && x < x_end;
+#pragma unroll
+                for (int p = 0; p < PM; ++p) v[h][p] = (in && p < P) ? mb[(int64_t)p * npix + x] : 0.f;
+                v[h][PM] = in ? W[x] : 0.f;
+            }
         };
         load(cur, 0);
-        load(n1, 1);
-        const int hoff = 4 * n_pg;
         for (int k = 0; k < nch; ++k) {
-            load(n2, k + 2);
+            load(n1, k + 1);
             const int s = k & 1;
             if (k >= 2) named_sync(3 + s, nthr);
-            float* sU = smem + s * stage_floats + xl * SU;
-            float* sMs = smem + s * stage_floats + CUB_TX * SU + xl * CUB_MS;
-            float wm[PM];
 #pragma unroll
-            for (int p = 0; p < PM; ++p) wm[p] = cur[PM] * cur[p];
-            float st[4];
+            for (int h = 0; h < 2; ++h) {
+                float4* sU = s4 + s * stage_f4 + xl + h * CUB_FILL;
+                float4* sM = sU + nslot * CUB_TX;
+                const float* cv = cur[h];
+                float wm[PM];
 #pragma unroll
-            for (int r = 0; r < PM; ++r)
+                for (int p = 0; p < PM; ++p) wm[p] = cv[PM] * cv[p];
+                float st[4];
 #pragma unroll
-                for (int p = 0; p <= r; ++p) {
-                    const int c = r * (r + 1) / 2 + p;           // colex pair index
-                    st[c & 3] = wm[p] * cur[r];
-                    if ((c & 3) == 3 && c < 8 * n_pg) {
-                        const int k4 = c >> 2;
-                        *reinterpret_cast<float4*>(sU + (k4 & 1) * hoff + (k4 >> 1) * 4) =
-                            make_float4(st[0], st[1], st[2], st[3]);
+                for (int r = 0; r < PM; ++r)
+#pragma unroll
+                    for (int p = 0; p <= r; ++p) {
+                        const int c = r * (r + 1) / 2 + p;           // colex pair index
+                        st[c & 3] = wm[p] * cv[r];
+                        if ((c & 3) == 3 && c < 8 * n_pg) sU[(c >> 2) * CUB_TX] = make_float4(st[0], st[1], st[2], st[3]);
                     }
-                }
-            constexpr int NPR = PM * (PM + 1) / 2;
-            if ((NPR & 3) != 0) {                                // tail of a partial float4
-                const int c0 = NPR & ~3;
+                constexpr int NPR = PM * (PM + 1) / 2;
+                if ((NPR & 3) != 0) {                                // tail of a partial float4
+                    const int c0 = NPR & ~3;
 #pragma unroll
-                for (int i = (NPR & 3); i < 4; ++i) st[i] = 0.f;
-                if (c0 < 8 * n_pg) {
-                    const int k4 = c0 >> 2;
-                    *reinterpret_cast<float4*>(sU + (k4 & 1) * hoff + (k4 >> 1) * 4) =
-                        make_float4(st[0], st[1], st[2], st[3]);
+                    for (int i = (NPR & 3); i < 4; ++i) st[i] = 0.f;
+                    if (c0 < 8 * n_pg) sU[(c0 >> 2) * CUB_TX] = make_float4(st[0], st[1], st[2], st[3]);
                 }
-            }
-            // pair slots past the colex pairs of PM modes (8 n_pg > NPR) are zero
-            for (int c0 = (NPR + 3) & ~3; c0 < 8 * n_pg; c0 += 4) {
-                const int k4 = c0 >> 2;
-                *reinterpret_cast<float4*>(sU + (k4 & 1) * hoff + (k4 >> 1) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+                // pair slots past the colex pairs of PM modes (8 n_pg > NPR) are zero
+                for (int c0 = (NPR + 3) & ~3; c0 < 8 * n_pg; c0 += 4)
+                    sU[(c0 >> 2) * CUB_TX] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<float4*>(sMs + 4 * q) =
-                    make_float4(q * 4 + 0 < PM ? cur[q * 4 + 0] : 0.f, q * 4 + 1 < PM ? cur[q * 4 + 1] : 0.f,
-                                q * 4 + 2 < PM ? cur[q * 4 + 2] : 0.f, q * 4 + 3 < PM ? cur[q * 4 + 3] : 0.f);
+                for (int q = 0; q < (PM + 3) / 4; ++q)
+                    if (q < n_sq)
+                        sM[q * CUB_TX] = make_float4(q * 4 + 0 < PM ? cv[q * 4 + 0] : 0.f, q * 4 + 1 < PM ? cv[q * 4 + 1] : 0.f,
+                                                     q * 4 + 2 < PM ? cv[q * 4 + 2] : 0.f, q * 4 + 3 < PM ? cv[q * 4 + 3] : 0.f);
+            }
             named_arrive(1 + s, nthr);
 #pragma unroll
-            for (int p = 0; p <= PM; ++p) {
-                cur[p] = n1[p];
-                n1[p] = n2[p];
-            }
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int p = 0; p <= PM; ++p) cur[h][p] = n1[h][p];
         }
     } else {
         // ------------------------------------------------ compute warps
-        const bool computes = lane < nl;
-        const int tpk = computes ? tiles[tile] : 0;
-        const int pg = tpk & 0xff, sq = tpk >> 8;
-        const int hoff = 4 * n_pg;
+        it = items[slot_item];
+        const bool active = it.x >= 0;
+        const int ta = active ? tiles[it.x] : 0;
+        const int tb = (active && it.y >= 0) ? tiles[it.y] : -1;
+        const int pga = ta & 0xff, sqa = ta >> 8;
+        // kind A: one pair group, quads a and b (the zero quad for a lone tile); kind B: two pair groups, one quad
+        const bool kindB = tb >= 0 && (tb & 0xff) != pga;
+        const int pgb = kindB ? (tb & 0xff) : pga;
+        const int sqb = kindB ? sqa : (tb >= 0 ? (tb >> 8) : n_sq);
         for (int k = 0; k < nch; ++k) {
             const int s = k & 1;
             named_sync(1 + s, nthr);
-            if (computes) {
-                const float* sU = smem + s * stage_floats;
-                const float* sMs = sU + CUB_TX * SU;
-                // packed FP32 pairs (one rounding per lane, as fmaf): tmp2[ip][q] holds the
-                // sums of pairs 2 ip and 2 ip + 1 against s = 4 sq + q
-                float2 tmp2[4][4];
+            if (active) {
+                const float4* sU = s4 + s * stage_f4;
+                const float4* sM = sU + nslot * CUB_TX;
+                // packed FP32 pairs (one rounding per lane, as fmaf): tA[ip][q], tB[ip][q] hold the
+                // sums of pairs 2 ip, 2 ip + 1 of the two tiles against their s = 4 sq + q
+                float2 tA[4][4], tB[4][4];
 #pragma unroll
                 for (int ip = 0; ip < 4; ++ip)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) tmp2[ip][q] = make_float2(0.f, 0.f);
-#pragma unroll 2
-                for (int xi = lane; xi < CUB_TX; xi += nl) {
-                    const float4 u0 = *reinterpret_cast<const float4*>(sU + xi * SU + pg * 4);
-                    const float4 u1 = *reinterpret_cast<const float4*>(sU + xi * SU + hoff + pg * 4);
-                    const float4 mv = *reinterpret_cast<const float4*>(sMs + xi * CUB_MS + sq * 4);
-                    const float2 u2[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
-                                          make_float2(u1.z, u1.w)};
-                    const float2 m2[4] = {make_float2(mv.x, mv.x), make_float2(mv.y, mv.y), make_float2(mv.z, mv.z),
-                                          make_float2(mv.w, mv.w)};
+                    for (int q = 0; q < 4; ++q) tA[ip][q] = tB[ip][q] = make_float2(0.f, 0.f);
+                if (!kindB) {
+#pragma unroll 1
+                    for (int xi = lane16; xi < CUB_TX; xi += CUB_LANES) {
+                        const float4 u0 = sU[(2 * pga) * CUB_TX + xi], u1 = sU[(2 * pga + 1) * CUB_TX + xi];
+                        const float4 ma = sM[sqa * CUB_TX + xi], mbv = sM[sqb * CUB_TX + xi];
+                        const float2 u2[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                                              make_float2(u1.z, u1.w)};
+                        const float2 a2[4] = {make_float2(ma.x, ma.x), make_float2(ma.y, ma.y), make_float2(ma.z, ma.z),
+                                              make_float2(ma.w, ma.w)};
+                        const float2 b2[4] = {make_float2(mbv.x, mbv.x), make_float2(mbv.y, mbv.y),
+                                              make_float2(mbv.z, mbv.z), make_float2(mbv.w, mbv.w)};
 #pragma unroll
-                    for (int ip = 0; ip < 4; ++ip)
+                        for (int ip = 0; ip < 4; ++ip)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) tmp2[ip][q] = __ffma2_rn(u2[ip], m2[q], tmp2[ip][q]);
+                            for (int q = 0; q < 4; ++q) {
+                                tA[ip][q] = __ffma2_rn(u2[ip], a2[q], tA[ip][q]);
+                                tB[ip][q] = __ffma2_rn(u2[ip], b2[q], tB[ip][q]);
+                            }
+                    }
+                } else {
+#pragma unroll 1
+                    for (int xi = lane16; xi < CUB_TX; xi += CUB_LANES) {
+                        const float4 u0 = sU[(2 * pga) * CUB_TX + xi], u1 = sU[(2 * pga + 1) * CUB_TX + xi];
+                        const float4 v0 = sU[(2 * pgb) * CUB_TX + xi], v1 = sU[(2 * pgb + 1) * CUB_TX + xi];
+                        const float4 mv = sM[sqa * CUB_TX + xi];
+                        const float2 u2[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w), make_float2(u1.x, u1.y),
+                                              make_float2(u1.z, u1.w)};
+                        const float2 v2[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                              make_float2(v1.z, v1.w)};
+                        const float2 m2[4] = {make_float2(mv.x, mv.x), make_float2(mv.y, mv.y), make_float2(mv.z, mv.z),
+                                              make_float2(mv.w, mv.w)};
+#pragma unroll
+                        for (int ip = 0; ip < 4; ++ip)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                tA[ip][q] = __ffma2_rn(u2[ip], m2[q], tA[ip][q]);
+                                tB[ip][q] = __ffma2_rn(v2[ip], m2[q], tB[ip][q]);
+                            }
+                    }
                 }
 #pragma unroll
                 for (int ip = 0; ip < 4; ++ip)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        acc[(2 * ip) * 4 + q] += tmp2[ip][q].x;
-                        acc[(2 * ip + 1) * 4 + q] += tmp2[ip][q].y;
+                        accA[(2 * ip) * 4 + q] += tA[ip][q].x;
+                        accA[(2 * ip + 1) * 4 + q] += tA[ip][q].y;
+                        accB[(2 * ip) * 4 + q] += tB[ip][q].x;
+                        accB[(2 * ip + 1) * 4 + q] += tB[ip][q].y;
                     }
             }
             if (k + 2 < nch) named_arrive(3 + s, nthr);
         }
     }
     __syncthreads();
-    float* red = smem;   // [nl][ntiles][32]
-    if (tid < ncomp && lane < nl) {
+    float* red = smem;   // [CUB_LANES][ntiles][32]
+    if (tid < ncomp && it.x >= 0) {
 #pragma unroll
-        for (int e = 0; e < 32; ++e) red[(lane * ntiles + tile) * 32 + e] = acc[e];
+        for (int e = 0; e < 32; ++e) red[(lane16 * ntiles + it.x) * 32 + e] = accA[e];
+        if (it.y >= 0) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) red[(lane16 * ntiles + it.y) * 32 + e] = accB[e];
+        }
     }
     __syncthreads();
     for (int i = tid; i < ntiles * 32; i += nthr) {
         const int t = i / 32, e = i % 32;
         float v = 0.f;
-        for (int ln = 0; ln < nl; ++ln) v += red[(ln * ntiles + t) * 32 + e];
+        for (int ln = 0; ln < CUB_LANES; ++ln) v += red[(ln * ntiles + t) * 32 + e];
         const int tp = tiles[t];
         const int c = (tp & 0xff) * 8 + e / 4, sv = (tp >> 8) * 4 + e % 4;
         const int n = modeidx[c * 16 + sv];
@@ -183,25 +229,22 @@ k_cubic(int P, int n_pg, int ntiles, int nl, int ncomp, const int* __restrict__ 
     }
 }
 
-static int cubic_lanes(const Plan& pl) { return std::max(1, std::min(8, CUB_MAXCOMP / pl.n_tiles)); }
-
 static size_t cubic_smem(const Plan& pl) {
-    const size_t SU = 8 * (size_t)pl.n_pg + 4;
-    const size_t tilebuf = 2 * (size_t)CUB_TX * (SU + CUB_MS) * 4;
-    const size_t redbuf = (size_t)cubic_lanes(pl) * pl.n_tiles * 32 * 4;
+    const size_t tilebuf = 2 * (size_t)CUB_TX * (2 * pl.n_pg + pl.n_sq + 1) * 16;
+    const size_t redbuf = (size_t)CUB_LANES * pl.n_tiles * 32 * 4;
     return tilebuf > redbuf ? tilebuf : redbuf;
 }
 
 template <int PM>
 static cudaError_t launch_cubic_pm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st) {
-    const int nl = cubic_lanes(pl);
-    const int ncomp = ((pl.n_tiles * nl + 31) / 32) * 32;
+    const int ncomp = pl.cubic_nslots * CUB_LANES;
     const size_t smem = cubic_smem(pl);
     cudaError_t e = cudaFuncSetAttribute(k_cubic<PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t ppc = ((pl.npix + pl.cubic_ctas - 1) / pl.cubic_ctas + CUB_TX - 1) / CUB_TX * CUB_TX;
     dim3 grid(pl.cubic_ctas, B);
-    k_cubic<PM><<<grid, ncomp + CUB_TX, smem, st>>>(pl.P, pl.n_pg, pl.n_tiles, nl, ncomp, pl.tiles, pl.modeidx,
+    k_cubic<PM><<<grid, ncomp + CUB_FILL, smem, st>>>(pl.P, pl.n_pg, pl.n_sq, pl.n_tiles, ncomp, pl.tiles,
+                                                    reinterpret_cast<const int2*>(pl.tiles + ((pl.n_tiles + 1) & ~1)), pl.modeidx,
                                                     pl.npix, ppc, maps, pl.W, partial, pl.n_max);
     note_launch(pl);
     return cudaGetLastError();
@@ -209,7 +252,7 @@ static cudaError_t launch_cubic_pm(Plan& pl, const float* maps, int B, double* p
 
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st) {
     if (B == 0) return cudaSuccess;
-    if (pl.n_tiles > CUB_MAXCOMP) return cudaErrorInvalidValue;
+    if (pl.cubic_nslots * CUB_LANES > CUB_MAXCOMP || pl.cubic_nslots % 2 != 0) return cudaErrorInvalidValue;
     if (pl.P <= 4) return launch_cubic_pm<4>(pl, maps, B, partial, st);
     if (pl.P <= 8) return launch_cubic_pm<8>(pl, maps, B, partial, st);
     return launch_cubic_pm<16>(pl, maps, B, partial, st);

@@ -143,6 +143,33 @@ static void build_mode_tables(modal_plan* pl, std::vector<int>& mi) {
             if (any) tiles.push_back(pg | (sq << 8));
         }
     pl->n_tiles = (int)tiles.size();
+    // compute items of the cubic kernel: two tiles of one pair group (two quads), else two
+    // pair groups of one quad, else a tile alone; items of the first kind first, each kind
+    // padded to an even count with idle slots so that the two half-warps of a warp run the
+    // same path.  Appended after the tile codes (from an even offset) as (tile a, tile b).
+    {
+        std::vector<std::vector<int>> by_pg(pl->n_pg);
+        for (int t = 0; t < pl->n_tiles; ++t) by_pg[tiles[t] & 0xff].push_back(t);
+        std::vector<std::pair<int, int>> kind_a, kind_b;
+        std::vector<std::vector<int>> pool(pl->n_sq);
+        for (int pg = 0; pg < pl->n_pg; ++pg) {
+            const std::vector<int>& ts = by_pg[pg];            // quads ascending
+            size_t i = 0;
+            for (; i + 1 < ts.size(); i += 2) kind_a.push_back({ts[i], ts[i + 1]});
+            if (i < ts.size()) pool[tiles[ts[i]] >> 8].push_back(ts[i]);
+        }
+        for (int sq = 0; sq < pl->n_sq; ++sq) {
+            size_t i = 0;
+            for (; i + 1 < pool[sq].size(); i += 2) kind_b.push_back({pool[sq][i], pool[sq][i + 1]});
+            if (i < pool[sq].size()) kind_a.push_back({pool[sq][i], -1});
+        }
+        if (kind_a.size() % 2) kind_a.push_back({-1, -1});
+        if (kind_b.size() % 2) kind_b.push_back({-1, -1});
+        if (tiles.size() % 2) tiles.push_back(0);
+        for (const auto& it : kind_a) { tiles.push_back(it.first); tiles.push_back(it.second); }
+        for (const auto& it : kind_b) { tiles.push_back(it.first); tiles.push_back(it.second); }
+        pl->cubic_nslots = (int)(kind_a.size() + kind_b.size());
+    }
     pl->cubic_pair_ab_host = pair_ab;
     pl->cubic_tiles_host = tiles;
 }

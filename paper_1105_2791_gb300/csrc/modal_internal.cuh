@@ -92,6 +92,7 @@ struct Plan {
     int* modeidx = nullptr;      // [n_pair_colex_pad][16] -> mode index or -1 (cubic tiles)
     int* tiles = nullptr;        // [n_tiles] packed (pair group, s quad)
     int n_tiles = 0, n_pg = 0, n_sq = 0;
+    int cubic_nslots = 0;        // compute items (half-warps) of the cubic kernel, stored after the tile codes
     int* pair_ab = nullptr;      // colex pair c -> (p | r << 8), padded entries = -1
     TcTable tc;
     TcAdjTable tca;
