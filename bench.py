@@ -151,15 +151,17 @@ def legendre_flops(P, lmax, nrings):
     return 4.0 * P * n_alm * ((nrings + 1) // 2)
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each stage's
-# kernel, from one-pass ncu captures at this workload (profiles/launches_l2000_b32_fp16x3.md
-# and profiles/legendre_tc_fp16x3_l1000_b8.md).  Keyed by (precision, lmax, nphi, P, maps
-# per launch); an entry is removed whenever its kernel changes until it is captured again.
+# DRAM traffic per launch (GB, dram__bytes_read + dram__bytes_write) of each stage's main
+# kernel, from one-pass ncu captures (dram__bytes_*, gpu__time_duration) of one bench step at
+# this workload; adjoint_pixel is the tensor-core map part (k_adjoint_v) and linear_term the
+# harmonic sums (k_linh_s).  Keyed by (precision, lmax, nphi, P, maps per launch); an entry is
+# removed whenever its kernel changes until it is captured again.
 STAGE_TRAFFIC_GB = {
     ("fp16x3", 2000, 4096, 16, 32): {
-        "legendre": 19.67 + 16.39, "pair_means": 25.71 + 8.88, "ring_c2r": 16.53 + 16.74,
-        "ring_r2c": 17.45 + 16.82, "legendre_adjoint": 26.19 + 0.52,
-        "legendre_prep": 0.51 + 8.40, "cubic": 17.84 + 0.11,
+        "legendre": 17.02 + 16.39, "pair_means": 25.71 + 8.88, "ring_c2r": 16.52 + 16.74,
+        "ring_r2c": 17.20 + 16.61, "legendre_adjoint": 27.06 + 0.57, "legendre_adjoint_prep": 16.56 + 16.73,
+        "legendre_prep": 0.515 + 8.394, "cubic": 17.84 + 0.11, "adjoint_pixel": 16.82 + 16.72,
+        "linear_term": 2.77 + 0.03,
     },
 }
 
