@@ -507,3 +507,29 @@ def test_backward_few_maps_with_pixel_means(prec, nb):
         err = _rel(grad[b], ref)
         print("adjoint lmax=%d P=%d %s %d maps, map %d: grad rel err %.3g" % (L, P, prec, nb, b, err))
         assert err <= 1e-5
+
+
+def test_cubic_every_number_of_basis_functions():
+    """The cubic kernel pairs its register tiles (one pair group with two s quads, two pair
+    groups with one quad, or a tile alone against a zero quad), and the pairing depends on P:
+    beta without the linear term against the oracle for every P from 1 to 16 (l_max = 20,
+    exact-cubic grid), FP32 and FP16X3 plans."""
+    M = _cuda_or_skip()
+    L, R, nphi = 20, 31, 64
+    cl = simgen.cl_model(L)
+    mu, w = osh.gl_nodes(R)
+    W = om.pixel_weights(w, nphi)
+    alm = simgen.gaussian_alm(cl, 2, seed=97).astype(np.complex64)
+    a = torch.from_numpy(alm).cuda()
+    for P in range(1, 17):
+        basis = simgen.shifted_legendre_basis(L, P)
+        filt = osh.filter_table(basis, cl)
+        refs = [om.cubic_beta(osh.synthesize(alm[b].astype(np.complex128), L, filt, mu, nphi), W) for b in range(2)]
+        for prec in ("fp32", "fp16x3"):
+            plan = _plan(M, L, P, basis, cl, R, nphi, prec)
+            got = plan.cubic(a).cpu().numpy()
+            plan.sync()
+            plan.close()
+            for b in range(2):
+                err = float(np.linalg.norm(got[b] - refs[b]) / np.linalg.norm(refs[b]))
+                assert err <= 1e-5, (P, prec, b, err)
