@@ -480,6 +480,7 @@ def run_gpu(args):
                 "launch_shapes": "autotuned per plan (modal_autotune, untimed)",
                 "default_shapes_value": round(mx["default_value"], 3),
                 "default_shapes_ms_per_step": round(mx["default_ms"], 3),
+                "shared_cubic_schedule_value": round(mx["shared_cubic_value"], 3),
                 "tuning": mx.get("tuning"), "maps_per_step": mx["maps_per_step"],
                 "steps": max(2, K // 2), "gpu_launches_per_step": int(mx["launches"]), "clocks": mx["clocks"]}
         except Exception as e:          # the headline line is printed whatever happens here
@@ -631,10 +632,12 @@ MIXED = [(500, 256), (1000, 128), (2000, 128)]      # (l_max, maps per step): th
 def mixed_measure(M, dev, prec, chunk, steps, warmup, rank=0, world=1, local=0, tune=True):
     """Batched Monte Carlo coefficient pass: 256 maps at l_max = 500, 128 at 1000 and 128 at
     2000 per step (P = 16, 20-degree band mask, linear term), one plan per l_max grouped in a
-    modal batch and replayed as one CUDA graph.  Timed first with the default launch shapes,
-    then (tune) after modal_autotune has tuned each plan on its own maps (untimed; the batch
-    graph is captured again).  Returns a dict: value / ms (tuned if tune, else default),
-    default_value / default_ms, tuning per l_max, kernels per step, clocks, maps per step."""
+    modal batch and replayed as one CUDA graph.  Timed first with the default launch shapes
+    (per-plan streams, then the shared-cubic schedule), then (tune) after modal_autotune has
+    tuned each plan on its own maps (untimed; the batch graph is captured again).  Returns a
+    dict: value / ms (tuned if tune, else default), default_value / default_ms,
+    shared_cubic_value / shared_cubic_ms, tuning per l_max, kernels per step, clocks, maps
+    per step."""
     import torch
     import simgen
 
@@ -674,6 +677,10 @@ def mixed_measure(M, dev, prec, chunk, steps, warmup, rank=0, world=1, local=0, 
     out = {"maps_per_step": n_maps}
     out["default_value"], out["default_ms"], clk = timed()
     out["value"], out["ms"], out["clocks"] = out["default_value"], out["default_ms"], clk
+    # the lockstep schedule with one persistent cubic launch per chunk pass (same betas)
+    batch.set_schedule("shared_cubic")
+    out["shared_cubic_value"], out["shared_cubic_ms"], _ = timed()
+    batch.set_schedule("streams")
     if tune:
         out["tuning"] = {}
         for (L, nb), pl, a in zip(MIXED, plans, alms):
@@ -723,6 +730,7 @@ def run_mixed(args):
                        "launch_shapes": "default" if args.no_tune else "autotuned per plan (modal_autotune, untimed)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "default_shapes_value": round(mx["default_value"], 3), "tuning": mx.get("tuning"),
+            "shared_cubic_schedule_value": round(mx["shared_cubic_value"], 3),
             "clocks": clk, "gpu_launches": int(launches) * K,
             "roofline": None, "e2e": None,
         }), flush=True)

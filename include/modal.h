@@ -375,6 +375,22 @@ typedef struct modal_batch* modal_batch_h;
 modal_status modal_batch_create(const modal_h* plans, int nplans, modal_batch_h* out);
 modal_status modal_batch_cubic(modal_batch_h bh, const void* const* alm, const int* B, int use_linear,
                                double* const* beta, int use_graph, void* stream);
+
+/* How modal_batch_cubic schedules its plans (Sec. 4's cubic sums, Eq. 41, for every plan):
+ *   MODAL_BATCH_STREAMS (default): each plan's whole pass (synthesis, cubic sums, linear
+ *     term, beta) runs chunk by chunk on its own stream, the streams concurrently.
+ *   MODAL_BATCH_SHARED_CUBIC: the plans' chunks go in lockstep passes; in pass k every plan
+ *     synthesizes its k-th chunk on its stream, then ONE persistent launch computes the
+ *     cubic sums of all of them from a work queue of (plan, map, pixel range) items, plans
+ *     with the longest pixel ranges first, before each plan's linear term and beta.  It
+ *     applies to calls whose plans with maps share one P (at most 8 of them, at least 2);
+ *     other calls run as MODAL_BATCH_STREAMS.  Every item is the one the plan's own launch
+ *     computes, so beta is bit-identical under either schedule.
+ * A change of schedule re-captures the batch graph.  Errors: MODAL_EINVAL (null batch,
+ * unknown schedule). */
+#define MODAL_BATCH_STREAMS 0
+#define MODAL_BATCH_SHARED_CUBIC 1
+modal_status modal_batch_set_schedule(modal_batch_h bh, int schedule);
 void modal_batch_destroy(modal_batch_h bh);
 
 void modal_destroy(modal_h h);

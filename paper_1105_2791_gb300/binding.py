@@ -33,7 +33,7 @@ EXPORTS = [
     "modal_batch_create", "modal_batch_cubic", "modal_batch_destroy", "modal_set_linear_mode",
     "modal_bivector_fit", "modal_solve_bivector", "modal_bivector_rotate", "modal_quartic",
     "modal_set_retain_maps", "modal_backward_retained", "modal_fnl_weights", "modal_peak_probe",
-    "modal_get_tuning", "modal_set_tuning", "modal_autotune", "modal_cubic_retained",
+    "modal_get_tuning", "modal_set_tuning", "modal_autotune", "modal_cubic_retained", "modal_batch_set_schedule",
 ]
 MODAL_NSTAGES = 15
 
@@ -117,13 +117,9 @@ def load_library():
         "modal_batch_create": [c_void_p, c_int, POINTER(c_void_p)],
         "modal_set_linear_mode": [H, c_int],
         "modal_batch_cubic": [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p],
+        "modal_batch_set_schedule": [c_void_p, c_int],
     }
     for name, args in sig.items():
-        if name == "modal_cubic_static":
-            fn = getattr(lib, name)
-            fn.argtypes = args
-            fn.restype = c_int
-            continue
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = c_int
@@ -235,6 +231,14 @@ def modal_batch_cubic(bh, alms, Bs, use_linear, betas, use_graph=True, stream=No
     o = (c_void_p * n)(*[_dev(x) for x in betas])
     _check(load_library().modal_batch_cubic(bh, a, b, int(bool(use_linear)), o, int(bool(use_graph)),
                                             _stream(stream)))
+
+
+BATCH_SCHEDULES = {"streams": 0, "shared_cubic": 1}
+
+
+def modal_batch_set_schedule(bh, schedule):
+    _check(load_library().modal_batch_set_schedule(bh, BATCH_SCHEDULES[schedule]
+                                                   if isinstance(schedule, str) else int(schedule)))
 
 
 def modal_batch_destroy(bh):

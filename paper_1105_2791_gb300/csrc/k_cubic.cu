@@ -43,18 +43,33 @@ __device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sy
 __device__ __forceinline__ void named_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // items: [nslots] int2 (tile a, tile b); tile a < 0: idle slot; tile b < 0: tile a alone.
+struct CubicJob {
+    const float* maps;
+    const float* W;
+    double* partial;
+    int64_t npix, ppc;
+    int nctas;
+};
+struct CubicJobs {
+    CubicJob job[CUBIC_MAX_JOBS];
+    int64_t item_end[CUBIC_MAX_JOBS];   // cumulative item counts
+    int n;
+};
+
+// One work item: map b of `maps`, pixel range `cta` of `nctas` ranges of px_per_cta pixels;
+// the CTA's sums of every mode go to partial[(b nctas + cta) n_max + n].  Ends with the CTA
+// synchronised, so that a persistent caller can run the next item on the same shared memory.
 template <int PM>
-__global__ void __launch_bounds__(CUB_THREADS, 1)
-k_cubic(int P, int n_pg, int n_sq, int ntiles, int ncomp, const int* __restrict__ tiles, const int2* __restrict__ items,
-        const int* __restrict__ modeidx, int64_t npix, int64_t px_per_cta, const float* __restrict__ maps,
-        const float* __restrict__ W, double* __restrict__ partial, int n_max) {
-    extern __shared__ __align__(16) float smem[];
+__device__ __forceinline__ void cubic_item(float* smem, int P, int n_pg, int n_sq, int ntiles, int ncomp,
+                                           const int* __restrict__ tiles, const int2* __restrict__ items,
+                                           const int* __restrict__ modeidx, int64_t npix, int64_t px_per_cta,
+                                           const float* __restrict__ maps, const float* __restrict__ W,
+                                           double* __restrict__ partial, int n_max, int b, int cta, int nctas) {
     const int nslot = 2 * n_pg;
     const int stage_f4 = (nslot + n_sq + 1) * CUB_TX;              // float4 per stage
-    const int b = blockIdx.y;
     const int tid = threadIdx.x;
     const int nthr = ncomp + CUB_FILL;
-    const int64_t x_begin = (int64_t)blockIdx.x * px_per_cta;
+    const int64_t x_begin = (int64_t)cta * px_per_cta;
     const int64_t x_end = min(npix, x_begin + px_per_cta);
     const int nch = (x_end > x_begin) ? (int)((x_end - x_begin + CUB_TX - 1) / CUB_TX) : 0;
     const float* mb = maps + (int64_t)b * P * npix;
@@ -225,7 +240,43 @@ k_cubic(int P, int n_pg, int n_sq, int ntiles, int ncomp, const int* __restrict_
         const int tp = tiles[t];
         const int c = (tp & 0xff) * 8 + e / 4, sv = (tp >> 8) * 4 + e % 4;
         const int n = modeidx[c * 16 + sv];
-        if (n >= 0) partial[((int64_t)b * gridDim.x + blockIdx.x) * n_max + n] = (double)v;
+        if (n >= 0) partial[((int64_t)b * nctas + cta) * n_max + n] = (double)v;
+    }
+    __syncthreads();
+}
+
+template <int PM>
+__global__ void __launch_bounds__(CUB_THREADS, 1)
+k_cubic(int P, int n_pg, int n_sq, int ntiles, int ncomp, const int* __restrict__ tiles, const int2* __restrict__ items,
+        const int* __restrict__ modeidx, int64_t npix, int64_t px_per_cta, const float* __restrict__ maps,
+        const float* __restrict__ W, double* __restrict__ partial, int n_max) {
+    extern __shared__ __align__(16) float smem[];
+    cubic_item<PM>(smem, P, n_pg, n_sq, ntiles, ncomp, tiles, items, modeidx, npix, px_per_cta, maps, W, partial, n_max,
+                   blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// The cubic sums of several plans (one pass of a mixed-l_max batch, the same P) as one
+// persistent launch: CTAs take (job, map, pixel range) items from a device counter, jobs in
+// the order given (the host puts the plans with the longest items first); every item is the
+// one the plan's own launch would compute, so the partial sums are identical.
+template <int PM>
+__global__ void __launch_bounds__(CUB_THREADS, 1)
+k_cubic_multi(CubicJobs jobs, int P, int n_pg, int n_sq, int ntiles, int ncomp, const int* __restrict__ tiles,
+              const int2* __restrict__ items, const int* __restrict__ modeidx, int n_max, int* __restrict__ counter) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t item = s_item;
+        __syncthreads();
+        if (item >= jobs.item_end[jobs.n - 1]) break;
+        int j = 0;
+        while (item >= jobs.item_end[j]) ++j;
+        const int64_t local = item - (j > 0 ? jobs.item_end[j - 1] : 0);
+        const CubicJob& jb = jobs.job[j];
+        cubic_item<PM>(smem, P, n_pg, n_sq, ntiles, ncomp, tiles, items, modeidx, jb.npix, jb.ppc, jb.maps, jb.W,
+                       jb.partial, n_max, (int)(local / jb.nctas), (int)(local % jb.nctas), jb.nctas);
     }
 }
 
@@ -248,6 +299,49 @@ static cudaError_t launch_cubic_pm(Plan& pl, const float* maps, int B, double* p
                                                     pl.npix, ppc, maps, pl.W, partial, pl.n_max);
     note_launch(pl);
     return cudaGetLastError();
+}
+
+template <int PM>
+static cudaError_t launch_cubic_multi_pm(const Plan& p0, const CubicJobs& jobs, int* counter, int nctas_grid,
+                                        cudaStream_t st) {
+    const int ncomp = p0.cubic_nslots * CUB_LANES;
+    const size_t smem = cubic_smem(p0);
+    cudaError_t e = cudaFuncSetAttribute(k_cubic_multi<PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_cubic_multi<PM><<<nctas_grid, ncomp + CUB_FILL, smem, st>>>(jobs, p0.P, p0.n_pg, p0.n_sq, p0.n_tiles, ncomp, p0.tiles,
+                                                                   reinterpret_cast<const int2*>(p0.tiles + ((p0.n_tiles + 1) & ~1)),
+                                                                   p0.modeidx, p0.n_max, counter);
+    note_launch(p0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cubic_multi(Plan* const* plans, const float* const* maps, const int* B, int n, int* counter,
+                               cudaStream_t st) {
+    if (n < 1 || n > CUBIC_MAX_JOBS) return cudaErrorInvalidValue;
+    const Plan& p0 = *plans[0];
+    if (p0.cubic_nslots * CUB_LANES > CUB_MAXCOMP || p0.cubic_nslots % 2 != 0) return cudaErrorInvalidValue;
+    CubicJobs jobs = {};
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const Plan& pl = *plans[i];
+        if (pl.P != p0.P || B[i] < 1 || B[i] > pl.chunk) return cudaErrorInvalidValue;
+        CubicJob& jb = jobs.job[i];
+        jb.maps = maps[i];
+        jb.W = pl.W;
+        jb.partial = pl.partial;
+        jb.npix = pl.npix;
+        jb.nctas = pl.cubic_ctas;
+        jb.ppc = ((pl.npix + pl.cubic_ctas - 1) / pl.cubic_ctas + CUB_TX - 1) / CUB_TX * CUB_TX;
+        total += (int64_t)B[i] * pl.cubic_ctas;
+        jobs.item_end[i] = total;
+    }
+    jobs.n = n;
+    const int grid = (int)std::min<int64_t>(total, (int64_t)std::max(p0.nsm, 1));
+    if (p0.P <= 4) return launch_cubic_multi_pm<4>(p0, jobs, counter, grid, st);
+    if (p0.P <= 8) return launch_cubic_multi_pm<8>(p0, jobs, counter, grid, st);
+    return launch_cubic_multi_pm<16>(p0, jobs, counter, grid, st);
 }
 
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st) {

@@ -782,36 +782,60 @@ modal_status modal_linear_term(modal_h h, const void* alm_sims, int B, int final
 
 // The coefficient pass of B maps; kept: the maps (and, for the ring-mode linear term, their
 // Legendre sums) are already in the plan's workspace from an earlier call on the same a_lm.
-static modal_status cubic_impl(modal_h h, const void* alm, int B, int use_linear, double* beta, cudaStream_t st,
-                               bool kept) {
-    const float2* a = static_cast<const float2*>(alm);
-    double* cub = h->partial;
-    double* lin = h->partial + (size_t)h->chunk * h->cubic_ctas * h->n_max;
-    for (int b0 = 0; b0 < B; b0 += h->chunk) {
-        const int nb = std::min(h->chunk, B - b0);
-        if (!kept) CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "cubic synthesis");
-        { STAGE(h, ST_CUBIC, st); CK(launch_cubic(*h, h->maps, nb, cub, st), "cubic"); }
-        int splits = h->lin_ksplit;
-        if (use_linear) {
-            STAGE(h, ST_LINEAR, st);
-            if (h->lin_mode == MODAL_LINEAR_RING) {
-                // ring sums of the maps from the m = 0 Legendre sums still in h->delta
-                CK(launch_linear_ring(*h, nb, lin, st), "linear term (ring)");
-                splits = 1;
-            } else if (h->prec == MODAL_FP32) {
-                CK(launch_linear_gemm(*h, h->maps, nb, lin, st), "linear gemm");
-            } else {
-                // from the a_lm and the harmonic pair-mean table (the same finite sums)
-                CK(launch_linear_harmonic(*h, a + (size_t)b0 * h->n_alm, nb, lin, st), "linear term (harmonic)");
-                splits = 1;
-            }
-        }
-        { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, cub, lin, splits, beta + (size_t)b0 * h->n_max, st), "beta finalize"); }
+// The linear-term partial sums of one chunk of nb maps (a: their a_lm, maps: their maps, the
+// m = 0 Legendre sums of the same synthesis in h->delta) into lin; returns through *splits
+// the number of partial-sum slices beta's finalisation adds.
+static modal_status linear_chunk(modal_h h, const float2* a, const float* maps, int nb, double* lin, int* splits,
+                                 cudaStream_t st) {
+    STAGE(h, ST_LINEAR, st);
+    *splits = h->lin_ksplit;
+    if (h->lin_mode == MODAL_LINEAR_RING) {
+        // ring sums of the maps from the m = 0 Legendre sums still in h->delta
+        CK(launch_linear_ring(*h, nb, lin, st), "linear term (ring)");
+        *splits = 1;
+    } else if (h->prec == MODAL_FP32) {
+        CK(launch_linear_gemm(*h, maps, nb, lin, st), "linear gemm");
+    } else {
+        // from the a_lm and the harmonic pair-mean table (the same finite sums)
+        CK(launch_linear_harmonic(*h, a, nb, lin, st), "linear term (harmonic)");
+        *splits = 1;
     }
+    return MODAL_OK;
+}
+
+static double* linear_partial(modal_h h) { return h->partial + (size_t)h->chunk * h->cubic_ctas * h->n_max; }
+
+// After the cubic sums of one chunk of nb maps (a: their a_lm, beta: their rows): the linear
+// term (if asked) and beta.
+static modal_status cubic_chunk_tail(modal_h h, const float2* a, int nb, int use_linear, double* beta, cudaStream_t st) {
+    double* lin = linear_partial(h);
+    int splits = h->lin_ksplit;
+    if (use_linear) {
+        const modal_status r = linear_chunk(h, a, h->maps, nb, lin, &splits, st);
+        if (r != MODAL_OK) return r;
+    }
+    { STAGE(h, ST_BETA, st); CK(launch_beta_finalize(*h, nb, use_linear, h->partial, lin, splits, beta, st), "beta finalize"); }
+    return MODAL_OK;
+}
+
+static void keep_maps_if_whole(modal_h h, const void* alm, int B) {
     if (h->retain_maps && B > 0 && B <= h->chunk) {      // the whole batch is in the map workspace
         h->kept_alm = alm;
         h->kept_B = B;
     }
+}
+
+static modal_status cubic_impl(modal_h h, const void* alm, int B, int use_linear, double* beta, cudaStream_t st,
+                               bool kept) {
+    const float2* a = static_cast<const float2*>(alm);
+    for (int b0 = 0; b0 < B; b0 += h->chunk) {
+        const int nb = std::min(h->chunk, B - b0);
+        if (!kept) CK(synth_chunk(h, a + (size_t)b0 * h->n_alm, nb, h->maps, st), "cubic synthesis");
+        { STAGE(h, ST_CUBIC, st); CK(launch_cubic(*h, h->maps, nb, h->partial, st), "cubic"); }
+        const modal_status r = cubic_chunk_tail(h, a + (size_t)b0 * h->n_alm, nb, use_linear, beta + (size_t)b0 * h->n_max, st);
+        if (r != MODAL_OK) return r;
+    }
+    keep_maps_if_whole(h, alm, B);
     return MODAL_OK;
 }
 
@@ -1459,6 +1483,9 @@ struct modal_batch {
     std::vector<double*> key_beta;
     std::vector<unsigned long long> key_gen;      // the plans' generations at capture
     int key_linear = -1;
+    int schedule = MODAL_BATCH_STREAMS;
+    cudaEvent_t cubic_done = nullptr;             // the shared cubic launch of one chunk pass
+    int* counter = nullptr;                       // its work-queue counter (device)
 };
 
 static void batch_drop_graph(modal_batch* bh) {
@@ -1469,9 +1496,89 @@ static void batch_drop_graph(modal_batch* bh) {
     bh->key_linear = -1;
 }
 
+// True if the plans' cubic sums can share one launch: the same P (so the same mode tables
+// and kernel instance) and at most CUBIC_MAX_JOBS plans with maps in the call.
+static bool batch_shares_cubic(const modal_batch* bh, const int* B) {
+    if (bh->schedule != MODAL_BATCH_SHARED_CUBIC) return false;
+    int n = 0;
+    const modal_plan* p0 = nullptr;
+    for (size_t i = 0; i < bh->plans.size(); ++i) {
+        if (B[i] == 0) continue;
+        const modal_plan* p = bh->plans[i];
+        if (!p0) p0 = p;
+        if (p->P != p0->P || p->n_max != p0->n_max || p->n_tiles != p0->n_tiles || p->cubic_nslots != p0->cubic_nslots)
+            return false;
+        ++n;
+    }
+    return n >= 2 && n <= CUBIC_MAX_JOBS;
+}
+
+// Chunk passes over the plans with maps in the call.  Pass k: each plan synthesizes its k-th
+// chunk on its own stream; one persistent cubic launch on bh->main takes the (plan, map,
+// pixel range) items of every plan's chunk k from a work queue, plans with the longest pixel
+// ranges first; then each plan's linear term and beta follow on its stream, and its next
+// synthesis after them.  Every item is the one the plan's own launch computes, so beta is
+// identical to modal_cubic's.
+static modal_status batch_run_shared(modal_batch* bh, const void* const* alm, const int* B, int use_linear,
+                                     double* const* beta) {
+    const size_t n = bh->plans.size();
+    std::vector<size_t> order;
+    int passes = 0;
+    for (size_t i = 0; i < n; ++i)
+        if (B[i] > 0) {
+            order.push_back(i);
+            passes = std::max(passes, (B[i] + bh->plans[i]->chunk - 1) / bh->plans[i]->chunk);
+        }
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        const modal_plan *px = bh->plans[x], *py = bh->plans[y];
+        return (px->npix + px->cubic_ctas - 1) / px->cubic_ctas > (py->npix + py->cubic_ctas - 1) / py->cubic_ctas;
+    });
+    CK(cudaEventRecord(bh->fork, bh->main), "batch fork");
+    for (size_t i : order) CK(cudaStreamWaitEvent(bh->side[i], bh->fork, 0), "batch fork wait");
+    for (int k = 0; k < passes; ++k) {
+        std::vector<Plan*> pl;
+        std::vector<const float*> mp;
+        std::vector<int> nb;
+        for (size_t i : order) {
+            modal_plan* h = bh->plans[i];
+            const int b0 = k * h->chunk;
+            if (b0 >= B[i]) continue;
+            pl.push_back(h);
+            mp.push_back(h->maps);
+            nb.push_back(std::min(h->chunk, B[i] - b0));
+            const float2* a = static_cast<const float2*>(alm[i]) + (size_t)b0 * h->n_alm;
+            CK(synth_chunk(h, a, nb.back(), h->maps, bh->side[i]), "cubic synthesis");
+            CK(cudaEventRecord(bh->done[i], bh->side[i]), "batch pass join");
+            CK(cudaStreamWaitEvent(bh->main, bh->done[i], 0), "batch pass join wait");
+        }
+        {
+            STAGE(static_cast<modal_plan*>(pl[0]), ST_CUBIC, bh->main);
+            CK(launch_cubic_multi(pl.data(), mp.data(), nb.data(), (int)pl.size(), bh->counter, bh->main), "shared cubic");
+        }
+        CK(cudaEventRecord(bh->cubic_done, bh->main), "batch pass fork");
+        for (size_t i : order) {
+            modal_plan* h = bh->plans[i];
+            const int b0 = k * h->chunk;
+            if (b0 >= B[i]) continue;
+            CK(cudaStreamWaitEvent(bh->side[i], bh->cubic_done, 0), "batch pass fork wait");
+            const float2* a = static_cast<const float2*>(alm[i]) + (size_t)b0 * h->n_alm;
+            const modal_status r = cubic_chunk_tail(h, a, std::min(h->chunk, B[i] - b0), use_linear,
+                                                    beta[i] + (size_t)b0 * h->n_max, bh->side[i]);
+            if (r != MODAL_OK) return r;
+        }
+    }
+    for (size_t i : order) {
+        keep_maps_if_whole(bh->plans[i], alm[i], B[i]);
+        CK(cudaEventRecord(bh->done[i], bh->side[i]), "batch join");
+        CK(cudaStreamWaitEvent(bh->main, bh->done[i], 0), "batch join wait");
+    }
+    return MODAL_OK;
+}
+
 // Fork to the plans' streams, run every plan's coefficient pass, join back on bh->main.
 static modal_status batch_run(modal_batch* bh, const void* const* alm, const int* B, int use_linear,
                               double* const* beta) {
+    if (batch_shares_cubic(bh, B)) return batch_run_shared(bh, alm, B, use_linear, beta);
     CK(cudaEventRecord(bh->fork, bh->main), "batch fork");
     for (size_t i = 0; i < bh->plans.size(); ++i) {
         CK(cudaStreamWaitEvent(bh->side[i], bh->fork, 0), "batch fork wait");
@@ -1500,7 +1607,9 @@ modal_status modal_batch_create(const modal_h* plans, int nplans, modal_batch_h*
     bool ok = cudaStreamCreateWithFlags(&bh->main, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&bh->fork, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&bh->in, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&bh->out, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&bh->out, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&bh->cubic_done, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMalloc(&bh->counter, sizeof(int)) == cudaSuccess;
     for (int i = 0; ok && i < nplans; ++i) {
         cudaStream_t s = nullptr;
         cudaEvent_t e = nullptr;
@@ -1581,6 +1690,15 @@ modal_status modal_batch_cubic(modal_batch_h bh, const void* const* alm, const i
     return MODAL_OK;
 }
 
+modal_status modal_batch_set_schedule(modal_batch_h bh, int schedule) {
+    if (!bh) return set_error(MODAL_EINVAL, "null batch");
+    if (schedule != MODAL_BATCH_STREAMS && schedule != MODAL_BATCH_SHARED_CUBIC)
+        return set_error(MODAL_EINVAL, "unknown batch schedule");
+    if (schedule != bh->schedule) batch_drop_graph(bh);
+    bh->schedule = schedule;
+    return MODAL_OK;
+}
+
 void modal_batch_destroy(modal_batch_h bh) {
     if (!bh) return;
     if (bh->main) cudaStreamSynchronize(bh->main);
@@ -1590,6 +1708,8 @@ void modal_batch_destroy(modal_batch_h bh) {
     if (bh->fork) cudaEventDestroy(bh->fork);
     if (bh->in) cudaEventDestroy(bh->in);
     if (bh->out) cudaEventDestroy(bh->out);
+    if (bh->cubic_done) cudaEventDestroy(bh->cubic_done);
+    if (bh->counter) cudaFree(bh->counter);
     if (bh->main) cudaStreamDestroy(bh->main);
     delete bh;
 }

@@ -197,6 +197,11 @@ cudaError_t launch_ring_r2c(const Plan& pl, const float* maps, int nmaps_p, cons
                             float2* ut, unsigned* amax, cudaStream_t st);
 // k_cubic.cu
 cudaError_t launch_cubic(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
+// The cubic sums of B[i] maps (one chunk, at maps[i], partial sums into plan i's partial
+// buffer) of n plans with the same P as one persistent launch; counter: device int.
+constexpr int CUBIC_MAX_JOBS = 8;
+cudaError_t launch_cubic_multi(Plan* const* plans, const float* const* maps, const int* B, int n, int* counter,
+                               cudaStream_t st);
 cudaError_t launch_linear_gemm(Plan& pl, const float* maps, int B, double* partial, cudaStream_t st);
 // lin_splits: K splits summed from lin_partial ([lin_splits][n_pair][B P])
 cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* cub_partial,

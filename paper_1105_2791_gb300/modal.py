@@ -253,14 +253,20 @@ def modal_fnl(alm, plan, alpha, use_linear=True):
 class Batch:
     """Plans of different l_max run as one coefficient pass (modal_batch_cubic).
 
-    The output tensors are owned by the batch and reused while the map counts stay the
-    same, so that with graph=True the captured CUDA graph is replayed; copy a result to
-    keep it past the next call."""
+    schedule: "streams" (each plan on its own stream) or "shared_cubic" (lockstep chunk
+    passes with one persistent cubic launch over every plan's maps); see
+    modal_batch_set_schedule.  The output tensors are owned by the batch and reused while
+    the map counts stay the same, so that with graph=True the captured CUDA graph is
+    replayed; copy a result to keep it past the next call."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, schedule="streams"):
         self.plans = list(plans)
         self.h = B.modal_batch_create([p.h for p in self.plans])
         self._out = None
+        self.set_schedule(schedule)
+
+    def set_schedule(self, schedule):
+        B.modal_batch_set_schedule(self.h, schedule)
 
     def close(self):
         if getattr(self, "h", None) is not None:
