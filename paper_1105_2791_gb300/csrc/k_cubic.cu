@@ -459,15 +459,20 @@ cudaError_t launch_beta_finalize(Plan& pl, int B, int use_linear, const double* 
 // through a PA_STAGES-deep ring in shared memory by cp.async: the two threads of a
 // pixel copy alternate rows of its column (each map value is fetched once) and read the
 // whole column after a CTA barrier; a second barrier keeps a stage from being refilled
-// while it is read.  The FP64 sums are read, updated and written once per launch.
+// while it is read.  The FP64 sums are read, updated and written once per launch: the
+// tile's FP32 sums go to shared memory by pair, each thread updates the pairs of its parity
+// at its pixel, PA_RMW loads in flight at a time (more spill at the 128-register cap that
+// keeps four CTAs per SM), their lines sent to L2 a few maps before the update.
 constexpr int PA_THREADS = 128;             // 64 pixels x 2 row parities
 constexpr int PA_PIX = PA_THREADS / 2;
 constexpr int PA_STAGES = 5;
+constexpr int PA_RMW = 8;                   // FP64 read-modify-writes in flight per thread (68 per thread at P = 16)
+constexpr int PA_PREFETCH = 4;              // maps before the end of a tile at which its FP64 sums go to L2
 
 template <int PM>
 constexpr size_t pa_smem_floats() {
     constexpr size_t ring = (size_t)PA_STAGES * PM * PA_PIX;
-    constexpr size_t sums = (size_t)((PM / 2) * (PM / 2 + 1)) * PA_THREADS;
+    constexpr size_t sums = (size_t)(PM * (PM + 1) / 2) * PA_PIX;
     return ring > sums ? ring : sums;
 }
 
@@ -477,10 +482,10 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 }
 
 template <int PM>
-__global__ void __launch_bounds__(PA_THREADS)
+__global__ void __launch_bounds__(PA_THREADS, 4)
 k_pair_accumulate(int P, int B, int64_t npix, const float* __restrict__ maps, double* __restrict__ sums) {
     constexpr int NACC = (PM / 2) * (PM / 2 + 1);                // sum over k of (PM - 2k)
-    extern __shared__ __align__(16) float pa_ring[];            // [PA_STAGES][PM][PA_PIX]; then [NACC][PA_THREADS]
+    extern __shared__ __align__(16) float pa_ring[];            // [PA_STAGES][PM][PA_PIX]; then [n_pair][PA_PIX]
     const int tid = threadIdx.x;
     const int h = tid / PA_PIX, xl = tid % PA_PIX;
     const int nv = P - h;                                       // shifted values that exist
@@ -511,6 +516,18 @@ k_pair_accumulate(int P, int B, int64_t npix, const float* __restrict__ maps, do
             issue(b + PA_STAGES - 1);
             asm volatile("cp.async.wait_group %0;" ::"n"(PA_STAGES - 1) : "memory");   // this thread's rows of map b
             __syncthreads();                                          // ... and the partner's
+            if (b == (B > PA_PREFETCH ? B - PA_PREFETCH : 0)) {
+                // the FP64 sums of this tile into L2 a few maps before their update: one
+                // 128-byte line per thread and step (PA_PIX doubles of a pair = 4 lines)
+                const int npair = P * (P + 1) / 2;
+                for (int i = tid; i < npair * (PA_PIX / 16); i += PA_THREADS) {
+                    const int64_t xs = x0 + (i % (PA_PIX / 16)) * 16;
+                    if (xs < npix) {
+                        const double* line = sums + (int64_t)(i / (PA_PIX / 16)) * npix + xs;
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+                    }
+                }
+            }
             const float* col = pa_ring + ((b % PA_STAGES) * PM + h) * PA_PIX + xl;
             float v[PM];
 #pragma unroll
@@ -526,23 +543,31 @@ k_pair_accumulate(int P, int B, int64_t npix, const float* __restrict__ maps, do
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();                                              // the ring is free
-        // the sums pass through shared memory ([NACC][PA_THREADS]) so that the FP64 update
-        // below is a plain loop
-        float* mine = pa_ring + tid;
+        // the sums pass through shared memory, one row of PA_PIX pixels per pair (lexicographic),
+        // so that the FP64 update below runs over pairs h, h + 2, ... with one stride
 #pragma unroll
-        for (int c = 0; c < NACC; ++c) mine[c * PA_THREADS] = acc[c];
+        for (int k = 0, c = 0; k < PM / 2; ++k) {
+            const int pa = 2 * k + h, q0 = pair_lex(pa, pa, P);
+#pragma unroll
+            for (int j = 0; j < PM - 2 * k; ++j, ++c)
+                if (pa + j < P) pa_ring[(q0 + j) * PA_PIX + xl] = acc[c];
+        }
+        __syncthreads();
         if (in) {
-            int c = 0;
+            // PA_RMW old values are loaded before the first of their stores, so that those
+            // loads are in flight together
+            const int nq = (P * (P + 1) / 2 - h + 1) / 2;
+            double* row = sums + (int64_t)h * npix + x;
+            const float* add = pa_ring + h * PA_PIX + xl;
 #pragma unroll 1
-            for (int k = 0; k < PM / 2; ++k) {
-                const int pa = 2 * k + h;
-                double* dst = sums + (int64_t)pair_lex(pa, pa, P) * npix + x;       // (pa, pa)
-                // rows hold an even number (PM - 2k) of sums: 8 read-modify-writes in flight
-#pragma unroll 4
-                for (int r = 2 * k; r < PM; r += 2, c += 2, dst += 2 * npix) {
-                    if (r + h < P) dst[0] += (double)mine[c * PA_THREADS];
-                    if (r + 1 + h < P) dst[npix] += (double)mine[(c + 1) * PA_THREADS];
-                }
+            for (int i0 = 0; i0 < nq; i0 += PA_RMW) {
+                double old[PA_RMW];
+#pragma unroll
+                for (int u = 0; u < PA_RMW; ++u)
+                    if (i0 + u < nq) old[u] = row[(int64_t)(2 * (i0 + u)) * npix];
+#pragma unroll
+                for (int u = 0; u < PA_RMW; ++u)
+                    if (i0 + u < nq) row[(int64_t)(2 * (i0 + u)) * npix] = old[u] + (double)add[2 * (i0 + u) * PA_PIX];
             }
         }
     }
