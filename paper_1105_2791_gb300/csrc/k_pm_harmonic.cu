@@ -34,6 +34,8 @@ constexpr int AP_THREADS = 128;                   // m values per block of that 
 constexpr int LH_MC = 32;                         // m values per shared-memory chunk of the linear term
 constexpr int LH_MAPS = 32;                       // maps per block of the linear term
 constexpr int LH_THREADS = 288;                   // (maps / 4) x (pairs / 4) register tiles, 8 x 34 at most
+constexpr int LH_FPT = (136 * LH_MC + LH_THREADS - 1) / LH_THREADS;     // table values a thread loads per block
+constexpr int LH_APT = (LH_MAPS * LH_MC + LH_THREADS - 1) / LH_THREADS;  // a_lm values a thread loads per block
 
 __host__ __device__ inline int64_t av_lidx(int64_t l, int64_t m) { return l * (l + 1) / 2 + m; }
 
@@ -232,12 +234,16 @@ cudaError_t launch_adjoint_pm(Plan& pl, int B, const float* hk, float2* grad, fl
 
 // ------------------------------------------------------------------ linear term
 // S[b][c][l] = sum_m c_m Re(conj(F_c[lm]) a_b[lm]) (only Re a at m = 0), one block per l (the
-// largest first) and up to LH_MAPS maps; thread = register tile of 4 maps x 4 pairs; chunks of
-// LH_MC values of m staged in shared memory; the per-chunk FP32 sums are added with
-// compensation (sums of up to l_max + 1 terms of both signs).
+// largest first) and up to LH_MAPS maps; thread = register tile of 4 maps x 4 pairs (pairs
+// ct + q n_pair/4, so that a warp reads consecutive rows of the staged table); chunks of
+// LH_MC values of m staged in shared memory, each thread's loads of a chunk issued together;
+// the per-chunk FP32 sums are added with compensation (sums of up to l_max + 1 terms of
+// both signs).
 __global__ void __launch_bounds__(LH_THREADS) k_linh_s(int L, int n_pair, int B, int64_t n_alm, const float2* __restrict__ F,
                                                        const float2* __restrict__ alm, float* __restrict__ S) {
-    __shared__ __align__(16) float2 sF[LH_MC][136];
+    // sF[c][j]: pair c at order m0 + j (a row per pair, as in F; the odd row length keeps the
+    // compute reads of 32 different rows on distinct banks)
+    __shared__ __align__(16) float2 sF[136][LH_MC + 1];
     __shared__ float2 sA[LH_MAPS][LH_MC + 1];
     const int l = L - (int)blockIdx.x;
     const int bg = blockIdx.y * LH_MAPS;
@@ -251,21 +257,40 @@ __global__ void __launch_bounds__(LH_THREADS) k_linh_s(int L, int n_pair, int B,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) sum[i][j] = comp[i][j] = 0.f;
-    for (int m0 = 0; m0 <= l; m0 += LH_MC) {
-        __syncthreads();
-        for (int i = tid; i < 136 * LH_MC; i += blockDim.x) {
-            const int c = i / LH_MC, j = i % LH_MC, m = m0 + j;
-            sF[j][c] = (c < n_pair && m <= l) ? F[(int64_t)c * n_alm + (int64_t)l * (l + 1) / 2 + m] : make_float2(0.f, 0.f);
+    // the table rows and a_lm of the next block of orders are loaded into registers while
+    // the current block is summed (LH_FPT + LH_APT loads in flight per thread)
+    float2 pf[LH_FPT], pa[LH_APT];
+    auto fetch = [&](int m0) {
+#pragma unroll
+        for (int u = 0; u < LH_FPT; ++u) {
+            const int i = tid + u * LH_THREADS, c = i / LH_MC, m = m0 + i % LH_MC;
+            pf[u] = (i < 136 * LH_MC && c < n_pair && m <= l) ? F[(int64_t)c * n_alm + (int64_t)l * (l + 1) / 2 + m]
+                                                            : make_float2(0.f, 0.f);
         }
-        for (int i = tid; i < LH_MAPS * LH_MC; i += blockDim.x) {
-            const int b = i / LH_MC, j = i % LH_MC, m = m0 + j;
+#pragma unroll
+        for (int u = 0; u < LH_APT; ++u) {
+            const int i = tid + u * LH_THREADS, b = i / LH_MC, m = m0 + i % LH_MC;
             float2 v = make_float2(0.f, 0.f);
-            if (b < nb && m <= l) {
+            if (i < LH_MAPS * LH_MC && b < nb && m <= l) {
                 v = alm[(int64_t)(bg + b) * n_alm + d_alm_index(l, m, L)];
                 if (m == 0) v.y = 0.f;
                 else { v.x *= 2.f; v.y *= 2.f; }
             }
-            sA[b][j] = v;
+            pa[u] = v;
+        }
+    };
+    for (int m0 = 0; m0 <= l; m0 += LH_MC) {
+        fetch(m0);
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < LH_FPT; ++u) {
+            const int i = tid + u * LH_THREADS;
+            if (i < 136 * LH_MC) sF[i / LH_MC][i % LH_MC] = pf[u];
+        }
+#pragma unroll
+        for (int u = 0; u < LH_APT; ++u) {
+            const int i = tid + u * LH_THREADS;
+            if (i < LH_MAPS * LH_MC) sA[i / LH_MC][i % LH_MC] = pa[u];
         }
         __syncthreads();
         if (active) {
@@ -276,10 +301,9 @@ __global__ void __launch_bounds__(LH_THREADS) k_linh_s(int L, int n_pair, int B,
                 for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
 #pragma unroll 4
             for (int j = 0; j < LH_MC; ++j) {
-                const float4 f01 = *reinterpret_cast<const float4*>(&sF[j][4 * ct]);
-                const float4 f23 = *reinterpret_cast<const float4*>(&sF[j][4 * ct + 2]);
-                const float2 fv[4] = {make_float2(f01.x, f01.y), make_float2(f01.z, f01.w), make_float2(f23.x, f23.y),
-                                      make_float2(f23.z, f23.w)};
+                float2 fv[4];
+#pragma unroll
+                for (int qc = 0; qc < 4; ++qc) fv[qc] = sF[ct + qc * nct][j];
 #pragma unroll
                 for (int qb = 0; qb < 4; ++qb) {
                     const float2 av = sA[4 * bt + qb][j];
@@ -303,7 +327,7 @@ __global__ void __launch_bounds__(LH_THREADS) k_linh_s(int L, int n_pair, int B,
     for (int qb = 0; qb < 4; ++qb)
 #pragma unroll
         for (int qc = 0; qc < 4; ++qc) {
-            const int b = 4 * bt + qb, c = 4 * ct + qc;
+            const int b = 4 * bt + qb, c = ct + qc * nct;
             if (b < nb && c < n_pair) S[((int64_t)(bg + b) * n_pair + c) * (L + 1) + l] = sum[qb][qc];
         }
 }
