@@ -90,7 +90,7 @@ def test_launches_per_step_and_achieved_rates():
 def test_traffic_only_for_the_captured_workload():
     rows = _by_stage(bench.stage_rooflines("fp16x3", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS))
     assert rows["ring_c2r"]["traffic"] == pytest.approx(16.52 + 16.74, abs=0.01)
-    assert rows["linear_term"]["traffic"] == pytest.approx(2.80, abs=0.01)
+    assert rows["linear_term"]["traffic"] == pytest.approx(2.815, abs=0.01)
     small = _by_stage(bench.stage_rooflines("fp16x3", 1000, 1001, 2048, P, N_MAX, N_PAIR, 8, 8, _prof(), 1, PEAKS))
     assert all(r["traffic"] is None for r in small.values())
 
