@@ -414,7 +414,7 @@ def run_gpu(args):
     launches = sum(n for (_, n) in prof_plain_timing.values())
     # end to end through the public API from pinned host memory
     a_e2e = [torch.empty_like(alm), torch.empty_like(alm)]
-    e2e_ms, _ = timed(plan, a_e2e, K, 1, e2e=True)
+    e2e_ms, _ = timed(plan, a_e2e, K, max(W, 2), e2e=True)
     # the same step with the adjoint on the cubic call's kept maps (or, under --adjoint kept,
     # with the maps synthesised again), device-timed
     other = None
