@@ -132,3 +132,28 @@ def test_probed_peaks_replace_the_derived_ones():
     tf = _by_stage(bench.stage_rooflines("3xtf32", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,
                                          probe=probe))
     assert tf["legendre"]["peak"] == pytest.approx(300.0)
+
+
+def test_no_function_reads_an_undefined_global():
+    """Every global name a function of bench.py or of the Python package reads is defined at
+    module level or built in (a stray name fails only when its workload runs on a GPU)."""
+    import builtins
+    import os
+    import symtable
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for rel in ("bench.py", "__graft_entry__.py", "paper_1105_2791_gb300/modal.py",
+                "paper_1105_2791_gb300/binding.py", "paper_1105_2791_gb300/tuning.py"):
+        top = symtable.symtable(open(os.path.join(root, rel)).read(), rel, "exec")
+        defined = set(top.get_identifiers())
+        bad = []
+
+        def walk(t):
+            for sym in t.get_symbols():
+                name = sym.get_name()
+                if sym.is_global() and sym.is_referenced() and name not in defined and not hasattr(builtins, name):
+                    bad.append((t.get_name(), name))
+            for child in t.get_children():
+                walk(child)
+
+        walk(top)
+        assert not bad, (rel, bad)
