@@ -414,7 +414,8 @@ def run_gpu(args):
     launches = sum(n for (_, n) in prof_plain_timing.values())
     # end to end through the public API from pinned host memory
     a_e2e = [torch.empty_like(alm), torch.empty_like(alm)]
-    e2e_ms, _ = timed(plan, a_e2e, K, max(W, 2), e2e=True)
+    with ClockSampler(local) as e2e_clocks:
+        e2e_ms, _ = timed(plan, a_e2e, K, max(W, 2), e2e=True)
     # the same step with the adjoint on the cubic call's kept maps (or, under --adjoint kept,
     # with the maps synthesised again), device-timed
     other = None
@@ -458,7 +459,8 @@ def run_gpu(args):
         "clocks": clk,
         "gpu_launches": int(launches),
         "e2e": {"value": round(e2e_value, 3), "unit": "maps/s",
-                "h2d_bytes_per_step": int(alm.numel() * 8), "d2h_bytes_per_step": int(B * 8 + 8)},
+                "h2d_bytes_per_step": int(alm.numel() * 8), "d2h_bytes_per_step": int(B * 8 + 8),
+                "clocks": e2e_clocks.summary()},
         "roofline": roof,
         "rooflines": rooflines,
         "peak_probes_tflops": probe,
