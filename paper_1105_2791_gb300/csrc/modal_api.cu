@@ -393,12 +393,15 @@ modal_status modal_init(int lmax, int P, const double* basis, const double* C_l,
 
     // kernel geometry
     {
-        int64_t ctas = pl->npix / 8192;
-        pl->cubic_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, 512));
-        int64_t ks = pl->npix / 16384;
-        pl->lin_ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(ks, 128));
         cudaDeviceGetAttribute(&pl->nsm, cudaDevAttrMultiProcessorCount, pl->dev);
         pl->nsm = std::max(pl->nsm, 1);
+        // pixel ranges of the cubic and quartic sums per map: one per 8192 pixels, at most one
+        // per SM (a 32-map launch at l_max = 2000 then runs 4864 CTAs: 18.09 ms, against 18.53
+        // with 512 ranges per map, whose per-CTA reductions and partial sums cost more)
+        int64_t ctas = pl->npix / 8192;
+        pl->cubic_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, pl->nsm));
+        int64_t ks = pl->npix / 16384;
+        pl->lin_ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(ks, 128));
         pl->tc_maps = 8;                                   // N = 16 P columns per Legendre item
     }
 
