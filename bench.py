@@ -395,7 +395,7 @@ def run_gpu(args):
         ms = max_over_ranks(ms, dev)
         return ms, prof
 
-    # roofline denominators the driver does not measure: FP32 SIMT, FP64 SIMT, tcgen05 tf32
+    # roofline denominators the measured-peaks file does not hold: FP32 SIMT, FP64 SIMT, tcgen05 tf32
     # and f16 rates, each probed once on this GPU before the timed region
     probe = {}
     for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor"):
@@ -794,7 +794,7 @@ def run_trispectrum(args):
         M.modal_set_profiling(plan.h, False)
         return max_over_ranks(ev0.elapsed_time(ev1), dev), prof
 
-    # roofline denominators the driver does not measure: FP32 SIMT, FP64 SIMT, tcgen05 tf32
+    # roofline denominators the measured-peaks file does not hold: FP32 SIMT, FP64 SIMT, tcgen05 tf32
     # and f16 rates, each probed once on this GPU before the timed region
     probe = {}
     for kind in ("fp32_simt", "fp64_simt", "tf32_tensor", "f16_tensor"):

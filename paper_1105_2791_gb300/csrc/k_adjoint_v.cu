@@ -281,7 +281,7 @@ size_t adjoint_v_workspace_bytes(const Plan& pl, int chunk) {
     return pl.prec == MODAL_FP32 ? 0 : (size_t)chunk * AV_BMAP;
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+// cuTensorMapEncodeTiled from the CUDA driver API, looked up once through the runtime.
 typedef CUresult (*AvEncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);

@@ -121,7 +121,7 @@ def test_job_throughput_is_whole_job_maps_per_second():
 def test_probed_peaks_replace_the_derived_ones():
     """With the library's throughput probes of this run, the FP32-SIMT stages use the probed
     FP32 rate and the 3xTF32 stages a third of the probed tf32 tensor rate; the split-FP16
-    stages keep the driver's sustained bf16 figure."""
+    stages keep the sustained bf16 figure of the measured-peaks file."""
     probe = {"fp32_simt": 70.0, "tf32_tensor": 900.0}
     rows = _by_stage(bench.stage_rooflines("fp16x3", L, R, NPHI, P, N_MAX, N_PAIR, CHUNK, CHUNK, _prof(), 1, PEAKS,
                                            probe=probe))
